@@ -1,0 +1,417 @@
+"""Benchmark of the EbV solver on one GB300 (or N replicas under torchrun).
+
+Workload: dense, unit-diagonal, strictly row-diagonally-dominant A, n=16384,
+off-diagonals U[-0.9, 0.9]/(n-1), 32 planted right-hand sides (b = A x_true),
+seeded.  One step = mixed-precision EbV factorisation (bfloat16 trailing
+updates on the tensor cores, FP32 factors) + FP64 iterative refinement of the
+32 solutions until the relative residual max_c ||b_c - A x_c|| / ||b_c|| is
+<= 1e-12.  The plain FP64 EbV path on the same GPU is measured beside it.
+
+Metric: nominal factor+solve GFLOP/s, 2n^3/3 + 2 n^2 nrhs flops per step (the
+HPL convention: refinement work is not credited), and solves/s.
+
+Output: one JSON line (rank 0).  --impl reference runs the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+solve GFLOP/s & solves/s, mixed vs FP64 EbV at rel. resid ≤1e-12"
+N_FULL, NRHS_FULL = 16384, 32
+TOL = 1e-12
+
+
+def nominal_flops(n, nrhs):
+    return 2.0 * n ** 3 / 3.0 + 2.0 * n * n * nrhs
+
+
+def oracle_sample_flops(n, kstop):
+    k = np.arange(kstop, dtype=np.float64)
+    m = n - k - 1
+    return float(np.sum(m + 2.0 * m * m))
+
+
+def workload_desc(n, nrhs):
+    return (f"dense DD n={n}, {nrhs} RHS, offdiag U[-0.9,0.9]/(n-1); EbV factor with bf16 tensor-core Schur "
+            f"updates + FP64 iterative refinement to rel. resid <= {TOL:g}")
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline
+# ----------------------------------------------------------------------------
+
+def cpu_oracle_rate(a: np.ndarray, kstop: int, threads: int = 0):
+    """Time the oracle's FP64 Doolittle on the first kstop elimination steps of
+    the full workload matrix; returns (GFLOP/s, seconds, threads)."""
+    import oracle
+    used = oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    oracle.lu(a, kstop=kstop)
+    dt = time.perf_counter() - t0
+    return oracle_sample_flops(a.shape[0], kstop) / dt / 1e9, dt, used
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, dist):
+    import torch
+
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, nrhs = args.n, args.nrhs
+    prec = args.prec
+
+    t_gen = time.perf_counter()
+    a_np, x_true, b_np = synthetic.config2(n, nrhs)
+    t_gen = time.perf_counter() - t_gen
+
+    a = torch.from_numpy(a_np).to(dev)
+    b0 = torch.from_numpy(b_np).to(dev)
+    lowp = torch.empty((n, n), dtype=torch.float32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ebv.workspace(n, prec, nrhs, dev)
+    rep = torch.zeros(3, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b0)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        x.copy_(b0)
+        ebv.ebv_factor(a, prec, lowp=lowp, info=info, ws=ws)
+        ebv.ebv_solve(lowp, x, prec, a_orig=a, refine=(TOL, args.max_iter), report=rep, ws=ws, ld=n)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    rep_np = ebv.read_report(rep)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ebv.launch_count()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = ebv.launch_count() - launches0
+    ms_total = e0.elapsed_time(e1)
+    ms = ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rep_np = ebv.read_report(rep)
+    info_v = int(info.item())
+
+    # accuracy of the last step against the planted solution and by the oracle residual (sampled rows)
+    import oracle
+    xs = x.cpu().numpy()
+    rows = synthetic.pick_indices(7, 256, [n])[:, 0]
+    r_s = oracle.residual(a_np, xs, b_np, rows=rows)
+    rel_resid_sampled = float((np.abs(r_s).max(axis=0) / np.abs(b_np).max(axis=0)).max())
+    err_true = float(np.abs(xs - x_true).max() / np.abs(x_true).max())
+
+    flops = nominal_flops(n, nrhs)
+    value = world * flops / (ms / 1e3) / 1e9
+
+    # per-kernel-class device times of one more (profiled) step
+    ebv.profile(True)
+    step()
+    torch.cuda.synchronize()
+    prof = ebv.profile_read()
+    ebv.profile(False)
+
+    # end to end through the C ABI from pinned host buffers
+    a_host = torch.from_numpy(a_np).pin_memory()
+    b_host = torch.from_numpy(b_np).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    a_dev2 = torch.empty_like(a)
+
+    def e2e_step():
+        a_dev2.copy_(a_host, non_blocking=True)
+        x.copy_(b_host, non_blocking=True)
+        ebv.ebv_factor(a_dev2, prec, lowp=lowp, info=info, ws=ws)
+        ebv.ebv_solve(lowp, x, prec, a_orig=a_dev2, refine=(TOL, args.max_iter), report=rep, ws=ws, ld=n)
+        x_host.copy_(x, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
+    e2e_val = world * flops / (e2e_ms / 1e3) / 1e9
+    del a_dev2
+
+    # plain FP64 EbV on the same GPU (same matrix and right-hand sides)
+    fp64 = None
+    if args.fp64_steps > 0:
+        lu64 = torch.empty_like(a)
+        x64 = torch.empty_like(b0)
+        ws64 = ebv.workspace(n, "fp64", nrhs, dev)
+
+        def step64():
+            lu64.copy_(a)
+            x64.copy_(b0)
+            ebv.ebv_factor(lu64, "fp64", info=info, ws=ws64)
+            ebv.ebv_solve(lu64, x64, "fp64", ws=ws64)
+
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.fp64_steps):
+            step64()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = g0.elapsed_time(g1) / args.fp64_steps
+        x64n = x64.cpu().numpy()
+        r64 = oracle.residual(a_np, x64n, b_np, rows=rows)
+        fp64 = {"gflops": flops / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
+                "rel_resid_sampled": float((np.abs(r64).max(axis=0) / np.abs(b_np).max(axis=0)).max()),
+                "speedup_mixed_vs_fp64": ms64 / ms}
+        del lu64, x64, ws64
+
+    # roofline of the dominant kernel class
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_work, dom_cnt) = dom
+    roofline = roofline_for(dom_name, dom_ms, dom_work, dom_cnt, peaks, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_kstop > 0:
+        rate, secs, used = cpu_oracle_rate(a_np, args.cpu_kstop)
+        cpu = {"value": rate, "unit": "GFLOP/s", "cores": used, "kind": "oracle",
+               "sample": f"oracle FP64 Doolittle (kij, OpenMP rows) on the first {args.cpu_kstop} elimination "
+                         f"steps of the n={n} workload matrix ({secs:.1f} s, {cpu_model()}); GFLOP/s of those steps",
+               "est_solve_s": flops / (rate * 1e9)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (tensor-core updates) / fp32 (factors) / fp64 (refinement)",
+        "data": "synthetic (seeded, planted solutions)",
+        "config": {"workload": workload_desc(n, nrhs), "n": n, "nrhs": nrhs, "precision": prec,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (A is %.2f GB FP64)" % (n * n * 8 / 1e9)},
+        "solves_per_s": world * 1e3 / ms, "rhs_per_s": world * nrhs * 1e3 / ms,
+        "refinement": {"iters": rep_np["iters"], "status": rep_np["status"], "resid_first": rep_np["resid_first"],
+                       "resid_final": rep_np["resid_final"], "rel_resid_sampled_oracle": rel_resid_sampled,
+                       "err_vs_x_true": err_true, "info": info_v},
+        "fp64_plain": fp64,
+        "roofline": roofline,
+        "kernel_classes_ms": {k: round(v[0], 4) for k, v in prof.items() if v[2] > 0},
+        "kernel_classes_launches": {k: v[2] for k, v in prof.items() if v[2] > 0},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(a_np.nbytes + b_np.nbytes), "d2h_bytes_per_step": int(b_np.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "input_gen_s": t_gen,
+    }
+    return line
+
+
+def roofline_for(name, ms, work, cnt, peaks, args):
+    if cnt == 0 or ms <= 0:
+        return None
+    per_launch_ms = ms / cnt
+    if name in ("lowp_gemm",):
+        tc = args.tc_used
+        if tc:
+            peak = peaks.get("bf16_tflops_sustained") or 1700.0
+            src = "measured bf16 sustained" if "bf16_tflops_sustained" in peaks else "fallback"
+            bound = "tensor"
+        else:
+            peak, src, bound = 75.1, "measured FFMA probe (FP32 SIMT fallback)", "alu"
+        achieved = work / (ms / 1e3) / 1e12
+        return {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src, "launches": cnt,
+                "avg_launch_ms": per_launch_ms}
+    if name == "residual":
+        # double-float residual: ~12 FP32 instructions per multiply-add
+        peak = 75.1 * 2.0 / 12.0
+        achieved = work / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64-equiv)",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured FFMA 75.1 TF/s / 6 (12 FP32 ops per emulated FP64 multiply-add)",
+                "launches": cnt, "avg_launch_ms": per_launch_ms}
+    achieved = work / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 75.1, "unit": "TFLOP/s",
+            "frac": achieved / 75.1, "traffic": None, "peak_source": "measured FFMA probe", "launches": cnt,
+            "avg_launch_ms": per_launch_ms}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    import synthetic
+    n = args.n
+    a_np, _, _ = synthetic.config2(n, args.nrhs)
+    kstop = args.ref_kstop
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, secs, used = cpu_oracle_rate(a_np, kstop)
+        if i >= args.warmup:
+            rates.append((rate, secs))
+    rate = float(np.median([r for r, _ in rates]))
+    ms = float(np.median([s for _, s in rates])) * 1e3
+    sample = (f"oracle FP64 Doolittle on the first {kstop} elimination steps of the n={n} workload matrix "
+              f"({cpu_model()})")
+    return {"metric": METRIC, "value": rate, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp64", "data": "synthetic (seeded)", "impl": "reference",
+            "config": {"workload": workload_desc(n, args.nrhs), "n": n, "nrhs": args.nrhs},
+            "cpu_baseline": {"value": rate, "unit": "GFLOP/s", "cores": used, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ebv", choices=["ebv", "reference"])
+    p.add_argument("--n", type=int, default=N_FULL)
+    p.add_argument("--nrhs", type=int, default=NRHS_FULL)
+    p.add_argument("--prec", default="bf16", choices=["bf16", "fp16"])
+    p.add_argument("--max-iter", type=int, default=10)
+    p.add_argument("--fp64-steps", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-kstop", type=int, default=384)
+    p.add_argument("--ref-kstop", type=int, default=96)
+    args = p.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    import paper_1907_05767_gb300 as ebv
+    args.tc_used = ebv.tc_available() if hasattr(ebv, "tc_available") else False
+
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_gpu(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

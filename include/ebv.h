@@ -1,0 +1,275 @@
+/*
+ * ebv.h -- C ABI of the GB300 (sm_103a) Equal bi-Vectorized LU solver.
+ *
+ * The method (Hashemi, Lahooti, Shirani, "Equal bi-Vectorized (EbV) method to
+ * high performance on GPU", arXiv 1907.05767):
+ *   - Eq. 1:  AX = B  <=>  L(UX) = B.  Factor A = LU, solve LY = B by forward
+ *             substitution, then UX = Y by backward substitution.
+ *   - Eq. 2:  A is diagonally dominant, so no pivoting is needed.
+ *   - Eq. 6a-c: Doolittle elimination.  Step r divides the L vector (column r
+ *             below the pivot) by the pivot A_rr and subtracts the outer product
+ *             of the L and U vectors from the trailing matrix.
+ *   - Eq. 7a-e: the 2n vectors (n columns of L, n rows of U) are paired long
+ *             with short so that every thread gets the same amount of work.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major: element (i, j) of a dense matrix is at
+ *     a[i*ld + j], ld >= n.  A band matrix with kl sub- and ku super-diagonals
+ *     is stored as a "row band": a_ij at ab[i*ld + (j - i + kl)] for
+ *     i - kl <= j <= i + ku, ld >= kl + ku + 1 (other slots are ignored).
+ *     Right-hand sides B are n x nrhs row-major with leading dimension ldb.
+ *   - Factors are returned packed in place ("L\U"): the strict lower triangle
+ *     holds L (its unit diagonal is implied), the upper triangle with the
+ *     diagonal holds U.
+ *   - Every pointer documented "device" must point to device memory of the
+ *     current CUDA device; the caller owns all memory.  The library never
+ *     allocates or frees device memory, never synchronises the host inside a
+ *     call, and issues all work on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream), so the calls are stream-ordered and can be captured
+ *     into a CUDA graph.
+ *   - Invalid arguments are reported synchronously (EBV_ERR_ARG) before any
+ *     work is enqueued.  A failed kernel launch returns EBV_ERR_CUDA.
+ *     Numerical trouble is reported through device-side `info` words,
+ *     LAPACK-style: 0 = fine, k > 0 = the first pivot that was zero or not
+ *     finite is U(k-1, k-1) (1-based k).  The elimination still runs to the
+ *     end (results are then meaningless but the call stays well-defined).
+ *   - Device-side waits inside the library's kernels are bounded; on expiry a
+ *     kernel sets EBV_ERR_TIMEOUT in its status word and returns.
+ *   - Calls are reentrant; concurrent calls must use distinct workspaces.
+ */
+#ifndef EBV_H_
+#define EBV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define EBV_API __attribute__((visibility("default")))
+#else
+#define EBV_API
+#endif
+
+typedef void *ebv_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  EBV_OK = 0,
+  EBV_ERR_ARG = 1,           /* invalid argument (sizes, null pointer, alignment, precision) */
+  EBV_ERR_ZERO_PIVOT = 2,    /* a zero pivot (reported through info) */
+  EBV_ERR_NONFINITE = 3,     /* a non-finite pivot (reported through info) */
+  EBV_ERR_NOT_CONVERGED = 4, /* refinement stopped at max_iter above tol */
+  EBV_ERR_TIMEOUT = 5,       /* a bounded device wait expired */
+  EBV_ERR_CUDA = 6,          /* a CUDA runtime/driver call failed */
+  EBV_ERR_UNSUPPORTED = 7,   /* valid but not implemented combination */
+  EBV_ERR_WORKSPACE = 8      /* workspace missing or smaller than ebv_workspace_size() */
+} ebv_status_t;
+
+typedef enum {
+  EBV_FP64 = 0,       /* binary64 throughout */
+  EBV_FP32 = 1,       /* binary32 throughout */
+  EBV_MIXED_BF16 = 2, /* FP32 factors whose trailing updates take bfloat16
+                         operands on the tensor cores (FP32 accumulation);
+                         FP64 residual / update / pivot reciprocals */
+  EBV_MIXED_FP16 = 3  /* as above with IEEE half operands, each operand panel
+                         scaled by a power of two to stay in half's normal range */
+} ebv_prec_t;
+
+typedef enum { EBV_DENSE = 0, EBV_BAND = 1 } ebv_storage_t;
+
+typedef struct ebv_desc {
+  int64_t n;       /* order of A, n >= 0 */
+  int64_t ld;      /* row stride in elements (dense: >= n; band: >= kl+ku+1) */
+  int64_t kl, ku;  /* band widths, 0 <= kl, ku < n (ignored for EBV_DENSE) */
+  int32_t storage; /* ebv_storage_t */
+  int32_t reserved;
+} ebv_desc_t;
+
+typedef struct ebv_refine {
+  double tol;       /* stop when max_c ||b_c - A x_c||_inf / ||b_c||_inf <= tol */
+  int32_t max_iter; /* upper bound on residual evaluations after the first solve */
+  int32_t reserved;
+} ebv_refine_t;
+
+/* Written by the device at the end of a refined solve. */
+typedef struct ebv_refine_report {
+  int32_t iters;       /* corrections applied after the initial solve */
+  int32_t status;      /* EBV_OK, or EBV_ERR_NOT_CONVERGED */
+  double resid_first;  /* relative residual of the initial (unrefined) solution */
+  double resid_final;  /* relative residual of the returned solution */
+} ebv_refine_report_t;
+
+/* Library version, as 10000*major + 100*minor + patch. */
+EBV_API int32_t ebv_version(void);
+
+/* Human-readable name of a status code (static storage). */
+EBV_API const char *ebv_status_string(ebv_status_t s);
+
+/*
+ * Bytes of device workspace that ebv_factor / ebv_solve need for this matrix,
+ * precision and number of right-hand sides (the same buffer may serve both,
+ * one call at a time).  Returns 0 for invalid arguments or when none is needed.
+ */
+EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64_t nrhs);
+
+/*
+ * ebv_factor -- A = LU without pivoting (Eq. 6a-c, equalised as in Eq. 7).
+ *
+ *   desc      matrix shape and storage.
+ *   prec      EBV_FP64 or EBV_FP32: `a` (device, double* or float*) is
+ *             overwritten by the packed factors; `lowp` must be NULL.
+ *             EBV_MIXED_BF16 / EBV_MIXED_FP16 (dense only): `a` is a device
+ *             double* holding A and is NOT modified; `lowp` (device float*,
+ *             n x n, leading dimension n) receives the packed FP32 factors,
+ *             whose trailing (Schur) updates were computed from bfloat16 /
+ *             half operands on the tensor cores with FP32 accumulation.
+ *   info_dev  device int32: 0, or the 1-based index of the first zero or
+ *             non-finite pivot.  Always written.
+ *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
+ *             256-byte aligned (may be NULL when that size is 0).
+ * Band storage (EBV_BAND) supports EBV_FP64 and EBV_FP32; fill-in stays inside
+ * the band because no rows are exchanged.
+ */
+EBV_API ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *lowp,
+                        int32_t *info_dev, void *ws, size_t ws_bytes, ebv_stream_t stream);
+
+/*
+ * ebv_solve -- X = A^{-1} B from the factors: LY = B, then UX = Y (Eq. 1).
+ *
+ *   lu        device: packed factors from ebv_factor (double* for EBV_FP64,
+ *             float* for EBV_FP32 and the mixed precisions, i.e. `lowp`).
+ *   a_orig    device double*, the original A (same desc); required for the mixed
+ *             precisions and whenever `refine` is given, else may be NULL.
+ *   b         device, n x nrhs, leading dimension ldb >= nrhs; overwritten by X.
+ *             double* for EBV_FP64 and the mixed precisions, float* for EBV_FP32.
+ *   refine    NULL: no refinement.  Otherwise iterative refinement: r = b - A x
+ *             in FP64, correction from the factors, x += d in FP64, until the
+ *             relative residual (max over columns of ||r||_inf / ||b||_inf) is
+ *             <= tol or max_iter residuals were taken.  The stop test runs on
+ *             the device (no host synchronisation).
+ *   report_dev device ebv_refine_report_t, written when refine != NULL (may be
+ *             NULL otherwise).
+ *   ws        workspace of ws_bytes >= ebv_workspace_size(desc, prec, nrhs).
+ */
+EBV_API ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, const double *a_orig,
+                       void *b, int64_t nrhs, int64_t ldb, const ebv_refine_t *refine,
+                       ebv_refine_report_t *report_dev, void *ws, size_t ws_bytes, ebv_stream_t stream);
+
+/*
+ * Batched factor + solve of many independent dense systems of uneven order
+ * (project addition; the paper factors one matrix).  Systems are grouped into
+ * long/short pairs (the pairing idea of Eq. 7 applied across systems) and run
+ * by one persistent kernel launch.
+ *
+ * ebv_batch_schedule_len(batch): int32 entries of a schedule.
+ * ebv_batch_schedule (host): builds the schedule for the given orders and
+ *   right-hand-side counts (host arrays) into `schedule_host`.  `variant_of_n`
+ *   (host, nullable) maps each order 1..512 to a kernel variant id
+ *   (0 = blocked nb 16, 1 = nb 32, 2 = nb 64), e.g. from ebv_batch_autotune;
+ *   NULL uses the built-in default.  The caller copies the schedule to device
+ *   memory once and may reuse it for every call with the same sizes.
+ * ebv_factor_solve_batched: system s has order n_dev[s] (1..4096) and
+ *   nrhs_dev[s] right-hand sides (0..64); a_ptrs_dev[s] points to its n x n
+ *   matrix (leading dimension n), overwritten by its packed factors;
+ *   b_ptrs_dev[s] to its n x nrhs right-hand sides (leading dimension nrhs),
+ *   overwritten by X.  prec is EBV_FP64 or EBV_FP32 (all matrices alike).
+ *   info_dev[s] receives the system's pivot status.  ws: workspace of at least
+ *   ebv_batch_workspace_size(batch) bytes (a work counter and a status word).
+ *   All arrays named _dev are device memory.
+ */
+EBV_API int64_t ebv_batch_schedule_len(int64_t batch);
+EBV_API size_t ebv_batch_workspace_size(int64_t batch);
+EBV_API ebv_status_t ebv_batch_schedule(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host,
+                                const int8_t *variant_of_n, int32_t *schedule_host);
+EBV_API ebv_status_t ebv_factor_solve_batched(int64_t batch, const int32_t *n_dev, const int32_t *nrhs_dev,
+                                      void *const *a_ptrs_dev, void *const *b_ptrs_dev, ebv_prec_t prec,
+                                      const int32_t *schedule_dev, int32_t *info_dev, void *ws,
+                                      size_t ws_bytes, ebv_stream_t stream);
+
+/*
+ * Autotuner for the batched kernel: times every variant on `reps` synthetic
+ * systems of each order in `orders` (host array of count entries) and writes
+ * the fastest variant id per order to best_variant_host.  scratch_dev must
+ * hold ebv_batch_autotune_scratch(max order, reps, prec) bytes.  Synchronises
+ * the stream (it measures time).
+ */
+EBV_API size_t ebv_batch_autotune_scratch(int32_t max_n, int32_t reps, ebv_prec_t prec);
+EBV_API ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, int32_t reps, ebv_prec_t prec,
+                                void *scratch_dev, size_t scratch_bytes, int8_t *best_variant_host,
+                                float *ms_host, ebv_stream_t stream);
+
+/*
+ * ebv_solve_adjoint -- gradients of X = A^{-1} B for a batch of equal-size
+ * FP64 systems (project addition; the paper has no gradients).  From the
+ * stored factors (A = LU, so A^T = U^T L^T):
+ *   grad_B = A^{-T} grad_X   (U^T z = grad_X forward, then L^T w = z backward),
+ *   grad_A = -grad_B X^T.
+ *   lu        device, system s at lu + s*stride_lu, leading dimension lda.
+ *   x, grad_x device, system s at + s*n*nrhs (n x nrhs, leading dim. nrhs).
+ *   grad_b    device output, same layout as x.
+ *   grad_a    device output or NULL, system s at + s*n*n (leading dim. n).
+ */
+EBV_API ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs, const double *lu, int64_t lda,
+                               int64_t stride_lu, const double *x, const double *grad_x, double *grad_b,
+                               double *grad_a, ebv_stream_t stream);
+
+/*
+ * Testing hook (no counterpart in the paper): selects how the mixed-precision
+ * trailing updates run.  0 = automatic (tensor cores where the shape allows),
+ * 1 = SIMT FP32 kernel from the same bfloat16/half operands, 2 = tensor cores
+ * only.  Process-wide; not for concurrent use with running factorisations.
+ */
+EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
+
+/*
+ * Testing hook (project addition; the residual of the refinement loop):
+ * R = B - A X for a dense FP64 A (n x n, lda) and FP64 X, B (n x nrhs,
+ * leading dimension nrhs), evaluated exactly as ebv_solve's refinement does
+ * it (double-float arithmetic).  R: device, n x nrhs.  ws: a workspace of at
+ * least ebv_workspace_size(dense n, EBV_FP64, nrhs) bytes.
+ */
+/*
+ * Testing hook (project addition; the aggregated rank-1 update of Eq. 6c as
+ * the mixed-precision factorisation runs it):
+ *   C(m0+i, n0+j) -= scale[2] * sum_{k<K} lb(m0+i, k0+k) * ut(n0+j, k0+k)
+ * for 0 <= i < M, 0 <= j < N.  op: 0 = bfloat16 operands, 1 = half.  engine:
+ * 1 = SIMT FP32 kernel, 2 = tcgen05 tensor-core kernel (returns
+ * EBV_ERR_UNSUPPORTED unless K is a multiple of 64, k0 of 8, ldsh*2 of 16 and
+ * lb, ut are 16-byte aligned).  C: device float, row stride ldc.  lb, ut:
+ * device 16-bit matrices with row stride ldsh.  scale: device float[3].
+ * ws: 256-byte-aligned device scratch of at least 256 bytes (status block).
+ */
+EBV_API ebv_status_t ebv_debug_lowp_update(int32_t op, int32_t engine, float *C, int64_t ldc, const void *lb,
+                                           const void *ut, int64_t ldsh, const float *scale, int64_t m0, int64_t n0,
+                                           int64_t k0, int64_t M, int64_t N, int64_t K, void *ws,
+                                           ebv_stream_t stream);
+/* 1 when the tensor-map encoder of the CUDA driver could be resolved. */
+EBV_API int32_t ebv_debug_tc_available(void);
+
+EBV_API ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b,
+                                        int64_t nrhs, double *r, void *ws, size_t ws_bytes, ebv_stream_t stream);
+
+/*
+ * Instrumentation (no counterpart in the paper).
+ * ebv_debug_launch_count: kernels launched by this library so far (process-wide).
+ * ebv_debug_profile(1) brackets every later launch with CUDA events on its
+ * stream, per kernel class: 0 mixed-precision trailing update, 1 working-
+ * precision trailing update, 2 panel (diagonal block, L21, U12), 3 block
+ * substitutions, 4 refinement residual, 5 batched kernel, 6 adjoint, 7 other.
+ * ebv_debug_profile_read fills, for the 8 classes, the summed device time in
+ * ms, the summed algorithmic work (flops) and the launch count of the launches
+ * recorded since the previous read (host arrays of 8; synchronises on the
+ * recorded events).  Profiling adds an event pair per launch; switch it off
+ * for timed runs.
+ */
+EBV_API int64_t ebv_debug_launch_count(void);
+EBV_API void ebv_debug_profile(int32_t enable);
+EBV_API int32_t ebv_debug_profile_read(double *ms_by_class, double *work_by_class, int64_t *count_by_class);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBV_H_ */

@@ -1,0 +1,309 @@
+"""EbV linear solver for GB300 (sm_103a): Python binding of libebv.so.
+
+The binding only marshals arguments: every step of the factorisation and the
+solves runs in the library's CUDA kernels.  PyTorch supplies device memory and
+the current CUDA stream.  If libebv.so has not been built the import succeeds
+but every call raises ``EbvUnavailable``; there is no CPU fallback.
+
+Method: Hashemi, Lahooti, Shirani, "Equal bi-Vectorized (EbV) method to high
+performance on GPU" (arXiv 1907.05767).  AX = B is solved as L(UX) = B (Eq. 1)
+after a Doolittle factorisation without pivoting of a diagonally dominant A
+(Eq. 2, Eq. 6a-c), with long and short vectors paired for equal work (Eq. 7).
+
+Names follow the C ABI in include/ebv.h: ``ebv_factor``, ``ebv_solve``,
+``ebv_factor_solve_batched``, ``ebv_solve_adjoint`` take torch tensors.
+Convenience wrappers: ``factor``, ``solve``, ``band_factor``, ``band_solve``,
+``factor_solve_batched``, and the autograd function ``EbvSolve``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libebv.so")
+
+# ebv_status_t
+OK, ERR_ARG, ERR_ZERO_PIVOT, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, \
+    ERR_WORKSPACE = range(9)
+# ebv_prec_t
+FP64, FP32, MIXED_BF16, MIXED_FP16 = range(4)
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
+DENSE, BAND = 0, 1
+
+
+class EbvError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class EbvUnavailable(RuntimeError):
+    pass
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("kl", ctypes.c_int64), ("ku", ctypes.c_int64),
+                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Refine(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RefineReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("resid_first", ctypes.c_double),
+                ("resid_final", ctypes.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_VP, _I64, _I32, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+_SIGNATURES = [
+    ("ebv_version", _I32, []),
+    ("ebv_status_string", ctypes.c_char_p, [_I32]),
+    ("ebv_workspace_size", _SZ, [ctypes.POINTER(Desc), _I32, _I64]),
+    ("ebv_factor", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    ("ebv_solve", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _I64, _I64, ctypes.POINTER(Refine), _VP, _VP,
+                         _SZ, _VP]),
+    ("ebv_batch_schedule_len", _I64, [_I64]),
+    ("ebv_batch_workspace_size", _SZ, [_I64]),
+    ("ebv_batch_schedule", _I32, [_I64, _VP, _VP, _VP, _VP]),
+    ("ebv_factor_solve_batched", _I32, [_I64, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _SZ, _VP]),
+    ("ebv_batch_autotune_scratch", _SZ, [_I32, _I32, _I32]),
+    ("ebv_batch_autotune", _I32, [_VP, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP]),
+    ("ebv_solve_adjoint", _I32, [_I64, _I64, _I64, _VP, _I64, _I64, _VP, _VP, _VP, _VP, _VP]),
+    ("ebv_debug_set_lowp_gemm", None, [_I32]),
+    ("ebv_debug_residual", _I32, [_I64, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
+    ("ebv_debug_lowp_update", _I32, [_I32, _I32, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _I64, _I64, _I64, _I64, _I64,
+                                     _VP, _VP]),
+    ("ebv_debug_tc_available", _I32, []),
+    ("ebv_debug_launch_count", _I64, []),
+    ("ebv_debug_profile", None, [_I32]),
+    ("ebv_debug_profile_read", _I32, [_VP, _VP, _VP]),
+]
+PROFILE_CLASSES = ["lowp_gemm", "simt_gemm", "panel", "trsv", "residual", "batched", "adjoint", "other"]
+
+
+def launch_count() -> int:
+    return int(lib().ebv_debug_launch_count())
+
+
+def profile(enable: bool):
+    lib().ebv_debug_profile(1 if enable else 0)
+
+
+def profile_read() -> dict:
+    """{class: (ms, work, launches)} for launches recorded since the last read."""
+    import numpy as np
+    ms = np.zeros(8)
+    work = np.zeros(8)
+    cnt = np.zeros(8, dtype=np.int64)
+    _check(lib().ebv_debug_profile_read(ms.ctypes.data, work.ctypes.data, cnt.ctypes.data), "profile_read")
+    return {c: (float(ms[i]), float(work[i]), int(cnt[i])) for i, c in enumerate(PROFILE_CLASSES)}
+EXPORTED = [s[0] for s in _SIGNATURES]
+
+
+def lib():
+    """The loaded libebv.so (raises EbvUnavailable when it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise EbvUnavailable(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def build(**kw) -> str:
+    from ._build import build as _b
+    return _b(**kw)
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().ebv_status_string(status).decode()
+    except EbvUnavailable:
+        return "unknown"
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise EbvError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _desc(n, ld, kl=0, ku=0, storage=DENSE):
+    return Desc(int(n), int(ld), int(kl), int(ku), int(storage), 0)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must live on a CUDA device")
+
+
+# ----------------------------------------------------------------------------
+# C-ABI names, torch arguments
+# ----------------------------------------------------------------------------
+
+def ebv_workspace_size(n, prec, nrhs=0, ld=None, kl=0, ku=0, storage=DENSE) -> int:
+    d = _desc(n, ld if ld is not None else (max(1, n) if storage == DENSE else kl + ku + 1), kl, ku, storage)
+    return int(lib().ebv_workspace_size(ctypes.byref(d), _prec(prec), int(nrhs)))
+
+
+def workspace(n, prec, nrhs=0, device="cuda", **kw) -> torch.Tensor:
+    """A device workspace tensor large enough for factor and solve."""
+    nbytes = max(256, ebv_workspace_size(n, prec, nrhs, **kw))
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def ebv_factor(a: torch.Tensor, prec="fp64", lowp: torch.Tensor | None = None, info: torch.Tensor | None = None,
+               ws: torch.Tensor | None = None, kl=0, ku=0, storage=DENSE) -> torch.Tensor:
+    """Factor in place (FP64/FP32) or into ``lowp`` (mixed).  Returns ``info``."""
+    p = _prec(prec)
+    _need_cuda(a, lowp, info, ws)
+    n = a.shape[0]
+    ld = a.stride(0)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=a.device)
+    if ws is None:
+        ws = workspace(n, p, 0, a.device, ld=ld, kl=kl, ku=ku, storage=storage)
+    d = _desc(n, ld, kl, ku, storage)
+    _check(lib().ebv_factor(ctypes.byref(d), p, _ptr(a), _ptr(lowp), _ptr(info), _ptr(ws), ws.numel(),
+                            _stream(a.device)), "ebv_factor")
+    return info
+
+
+def ebv_solve(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tensor | None = None,
+              refine: tuple | None = None, report: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+              kl=0, ku=0, storage=DENSE, ld=None) -> torch.Tensor:
+    """Overwrite ``b`` (n x nrhs) with X.  ``refine`` = (tol, max_iter) or None."""
+    p = _prec(prec)
+    _need_cuda(lu, b, a_orig, report, ws)
+    n = b.shape[0]
+    b2 = b if b.dim() == 2 else b.view(n, 1)
+    nrhs = b2.shape[1]
+    if ld is None:
+        ld = lu.stride(0)
+    if ws is None:
+        ws = workspace(n, p, nrhs, b.device, ld=ld, kl=kl, ku=ku, storage=storage)
+    d = _desc(n, ld, kl, ku, storage)
+    ref = Refine(float(refine[0]), int(refine[1]), 0) if refine is not None else None
+    if refine is not None and report is None:
+        report = torch.zeros(3, dtype=torch.float64, device=b.device)
+    _check(lib().ebv_solve(ctypes.byref(d), p, _ptr(lu), _ptr(a_orig), _ptr(b2), nrhs, b2.stride(0),
+                           ctypes.byref(ref) if ref is not None else None, _ptr(report), _ptr(ws), ws.numel(),
+                           _stream(b.device)), "ebv_solve")
+    return b
+
+
+def read_report(report: torch.Tensor) -> dict:
+    raw = report.detach().cpu().numpy().tobytes()[:ctypes.sizeof(RefineReport)]
+    r = RefineReport.from_buffer_copy(raw)
+    return {"iters": r.iters, "status": r.status, "resid_first": r.resid_first, "resid_final": r.resid_final}
+
+
+def read_device_status(ws: torch.Tensor) -> tuple[int, int]:
+    """(code, where) of the device status block at the start of a workspace."""
+    v = ws[:8].cpu().view(torch.int32)
+    return int(v[0]), int(v[1])
+
+
+# ----------------------------------------------------------------------------
+# Convenience API
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Factors:
+    lu: torch.Tensor          # packed L\U (FP64 / FP32)
+    info: torch.Tensor        # device int32
+    prec: int
+    a: torch.Tensor | None    # original FP64 A (mixed precisions, refinement)
+    kl: int = 0
+    ku: int = 0
+    storage: int = DENSE
+
+
+def factor(a: torch.Tensor, prec="fp64", keep_a: bool = True) -> Factors:
+    """Factor a dense matrix.  FP64/FP32: a copy of ``a`` is factored.  Mixed:
+    ``a`` (FP64) is kept and the FP32 factors go to a new tensor."""
+    p = _prec(prec)
+    n = a.shape[0]
+    if p in (MIXED_BF16, MIXED_FP16):
+        a64 = a.to(torch.float64).contiguous()
+        lowp = torch.empty((n, n), dtype=torch.float32, device=a.device)
+        info = ebv_factor(a64, p, lowp=lowp)
+        return Factors(lowp, info, p, a64)
+    dt = torch.float64 if p == FP64 else torch.float32
+    lu = a.to(dt).clone().contiguous()
+    info = ebv_factor(lu, p)
+    return Factors(lu, info, p, a.to(torch.float64).contiguous() if keep_a else None)
+
+
+def solve(f: Factors, b: torch.Tensor, refine: tuple | None = None, report: torch.Tensor | None = None):
+    dt = torch.float32 if f.prec == FP32 else torch.float64
+    x = b.to(dt).clone().contiguous()
+    if x.dim() == 1:
+        x = x.view(-1, 1)
+    ebv_solve(f.lu, x, f.prec, a_orig=f.a, refine=refine, report=report, kl=f.kl, ku=f.ku, storage=f.storage)
+    return x.view(b.shape) if b.dim() == 1 else x
+
+
+def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64") -> Factors:
+    """Factor a row-band matrix (n x (kl+ku+1))."""
+    p = _prec(prec)
+    dt = torch.float64 if p == FP64 else torch.float32
+    lu = ab.to(dt).clone().contiguous()
+    info = ebv_factor(lu, p, kl=kl, ku=ku, storage=BAND)
+    return Factors(lu, info, p, ab.to(torch.float64).contiguous(), kl, ku, BAND)
+
+
+def debug_residual(a: torch.Tensor, x: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """R = B - A X through the refinement's residual kernel (testing hook)."""
+    n = a.shape[0]
+    x2 = x.reshape(n, -1).contiguous()
+    b2 = b.reshape(n, -1).contiguous()
+    nrhs = x2.shape[1]
+    r = torch.empty_like(x2)
+    ws = workspace(n, FP64, nrhs, a.device)
+    _check(lib().ebv_debug_residual(n, _ptr(a), a.stride(0), _ptr(x2), _ptr(b2), nrhs, _ptr(r), _ptr(ws), ws.numel(),
+                                    _stream(a.device)), "ebv_debug_residual")
+    return r
+
+
+def tc_available() -> bool:
+    return bool(lib().ebv_debug_tc_available())
+
+
+def debug_lowp_update(c: torch.Tensor, lb: torch.Tensor, ut: torch.Tensor, scale: torch.Tensor, m0: int, n0: int,
+                      k0: int, M: int, N: int, K: int, engine: str = "tc") -> torch.Tensor:
+    """C(m0.., n0..) -= scale[2] * lb(m0.., k0..) @ ut(n0.., k0..)^T in place (testing hook)."""
+    op = 0 if lb.dtype == torch.bfloat16 else 1
+    ws = torch.empty(256, dtype=torch.uint8, device=c.device)
+    _check(lib().ebv_debug_lowp_update(op, 2 if engine == "tc" else 1, _ptr(c), c.stride(0), _ptr(lb), _ptr(ut),
+                                       lb.stride(0), _ptr(scale), m0, n0, k0, M, N, K, _ptr(ws), _stream(c.device)),
+           "ebv_debug_lowp_update")
+    code, where = read_device_status(ws)
+    if code != OK:
+        raise EbvError(code, f"device status (where={where})")
+    return c

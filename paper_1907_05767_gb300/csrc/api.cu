@@ -1,0 +1,137 @@
+// C ABI of the EbV library: argument checks and dispatch.  Every check runs
+// on the host before anything is enqueued, so invalid calls return EBV_ERR_ARG
+// without touching the GPU.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace ebv;
+
+namespace {
+
+constexpr int64_t kMaxN = int64_t(1) << 30;
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+size_t elem_size(ebv_prec_t p) { return p == EBV_FP32 ? 4 : 8; }
+
+bool valid_prec(ebv_prec_t p) {
+  return p == EBV_FP64 || p == EBV_FP32 || p == EBV_MIXED_BF16 || p == EBV_MIXED_FP16;
+}
+bool is_mixed(ebv_prec_t p) { return p == EBV_MIXED_BF16 || p == EBV_MIXED_FP16; }
+
+ebv_status_t check_desc(const ebv_desc_t *d, ebv_prec_t prec) {
+  if (!d || !valid_prec(prec)) return EBV_ERR_ARG;
+  if (d->n < 0 || d->n > kMaxN) return EBV_ERR_ARG;
+  if (d->storage == EBV_DENSE) {
+    if (d->ld < std::max<int64_t>(1, d->n)) return EBV_ERR_ARG;
+  } else if (d->storage == EBV_BAND) {
+    if (d->kl < 0 || d->ku < 0) return EBV_ERR_ARG;
+    if (d->n > 0 && (d->kl >= d->n || d->ku >= d->n)) return EBV_ERR_ARG;
+    if (d->ld < d->kl + d->ku + 1) return EBV_ERR_ARG;
+    if (is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
+  } else {
+    return EBV_ERR_ARG;
+  }
+  return EBV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ebv_version(void) { return 100; }
+
+const char *ebv_status_string(ebv_status_t s) {
+  switch (s) {
+    case EBV_OK: return "ok";
+    case EBV_ERR_ARG: return "invalid argument";
+    case EBV_ERR_ZERO_PIVOT: return "zero pivot";
+    case EBV_ERR_NONFINITE: return "non-finite pivot";
+    case EBV_ERR_NOT_CONVERGED: return "refinement did not converge";
+    case EBV_ERR_TIMEOUT: return "device wait timed out";
+    case EBV_ERR_CUDA: return "CUDA error";
+    case EBV_ERR_UNSUPPORTED: return "unsupported combination";
+    case EBV_ERR_WORKSPACE: return "workspace missing or too small";
+  }
+  return "unknown status";
+}
+
+size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64_t nrhs) {
+  if (check_desc(desc, prec) != EBV_OK || nrhs < 0) return 0;
+  const int64_t n = desc->n;
+  if (desc->storage == EBV_BAND)
+    return std::max(band_factor_ws(n, desc->kl, desc->ku, prec), band_solve_ws(n, nrhs, prec));
+  return std::max(dense_factor_ws(n, prec), dense_solve_ws(n, nrhs, prec));
+}
+
+ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *lowp, int32_t *info_dev, void *ws,
+                        size_t ws_bytes, ebv_stream_t stream) {
+  EBV_TRY(check_desc(desc, prec));
+  if (!info_dev || !aligned(info_dev, 4)) return EBV_ERR_ARG;
+  if (desc->n > 0 && (!a || !aligned(a, elem_size(prec)))) return EBV_ERR_ARG;
+  if (is_mixed(prec) && desc->n > 0 && (!lowp || !aligned(lowp, 16))) return EBV_ERR_ARG;
+  if (ws && !aligned(ws, 256)) return EBV_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (desc->storage == EBV_BAND) {
+    if (!ws || ws_bytes < band_factor_ws(desc->n, desc->kl, desc->ku, prec)) return EBV_ERR_WORKSPACE;
+    return band_factor(desc, prec, a, info_dev, ws, ws_bytes, s);
+  }
+  const size_t need = dense_factor_ws(desc->n, prec);
+  if (need > 0 && (!ws || ws_bytes < need)) return EBV_ERR_WORKSPACE;
+  return dense_factor(desc, prec, a, lowp, info_dev, ws, ws_bytes, s);
+}
+
+ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
+                       int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *report_dev,
+                       void *ws, size_t ws_bytes, ebv_stream_t stream) {
+  EBV_TRY(check_desc(desc, prec));
+  if (nrhs < 0 || nrhs > (int64_t(1) << 20) || ldb < std::max<int64_t>(1, nrhs)) return EBV_ERR_ARG;
+  const bool any = desc->n > 0 && nrhs > 0;
+  const size_t bsz = prec == EBV_FP32 ? 4 : 8;
+  const size_t fsz = prec == EBV_FP64 ? 8 : 4;
+  if (any && (!lu || !aligned(lu, fsz) || !b || !aligned(b, bsz))) return EBV_ERR_ARG;
+  const bool need_a = is_mixed(prec) && refine;
+  if (refine) {
+    if (!(refine->tol >= 0.0) || refine->max_iter < 0 || refine->max_iter > 1000) return EBV_ERR_ARG;
+    if (prec == EBV_FP32) return EBV_ERR_UNSUPPORTED;  // refinement returns FP64 solutions
+  }
+  if ((need_a || refine) && any && (!a_orig || !aligned(a_orig, 8))) return EBV_ERR_ARG;
+  if (report_dev && !aligned(report_dev, 8)) return EBV_ERR_ARG;
+  if (!ws || !aligned(ws, 256)) return EBV_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (desc->storage == EBV_BAND)
+    return band_solve(desc, prec, lu, a_orig, b, nrhs, ldb, refine, report_dev, ws, ws_bytes, s);
+  return dense_solve(desc, prec, lu, a_orig, b, nrhs, ldb, refine, report_dev, ws, ws_bytes, s);
+}
+
+// Testing hook: 0 = automatic, 1 = SIMT only, 2 = tensor cores where possible.
+void ebv_debug_set_lowp_gemm(int32_t mode) { set_lowp_gemm_mode(mode); }
+
+ebv_status_t ebv_debug_lowp_update(int32_t op, int32_t engine, float *C, int64_t ldc, const void *lb, const void *ut,
+                                   int64_t ldsh, const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M,
+                                   int64_t N, int64_t K, void *ws, ebv_stream_t stream) {
+  if ((op != 0 && op != 1) || (engine != 1 && engine != 2)) return EBV_ERR_ARG;
+  if (M < 0 || N < 0 || K < 0 || m0 < 0 || n0 < 0 || k0 < 0 || ldsh < k0 + K || ldc < n0 + N) return EBV_ERR_ARG;
+  if (M == 0 || N == 0 || K == 0) return EBV_OK;
+  if (!C || !lb || !ut || !scale || !ws || !aligned(ws, 256)) return EBV_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(ws, 0, sizeof(DevStatus), s) != cudaSuccess) return EBV_ERR_CUDA;
+  if (engine == 2)
+    return tc_update(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, (DevStatus *)ws, s);
+  return simt_update(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, s);
+}
+
+int32_t ebv_debug_tc_available(void) { return tc_available() ? 1 : 0; }
+
+ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b,
+                                int64_t nrhs, double *r, void *ws, size_t ws_bytes, ebv_stream_t stream) {
+  if (n < 0 || nrhs < 0 || lda < std::max<int64_t>(1, n)) return EBV_ERR_ARG;
+  if (n == 0 || nrhs == 0) return EBV_OK;
+  if (!a || !x || !b || !r || !aligned(a, 8) || !aligned(x, 8) || !aligned(b, 8) || !aligned(r, 8)) return EBV_ERR_ARG;
+  if (!ws || !aligned(ws, 256)) return EBV_ERR_WORKSPACE;
+  return debug_residual(n, a, lda, x, b, nrhs, r, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+}  // extern "C"

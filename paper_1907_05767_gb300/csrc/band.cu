@@ -1,0 +1,142 @@
+// Banded factorisation and solve (the sparse case of the paper's first
+// experiment, stored as a band).  Without row exchanges the L vectors of step
+// r reach rows r+1..r+kl only and the U vectors columns r+1..r+ku only, so all
+// fill-in stays inside the band (Eq. 6a-c restricted to the band).
+//
+// Right-looking over 64-column leaf blocks: per block, the equal
+// bi-vectorised diagonal kernel, L21 for the <= kl rows below, U12 for the
+// <= ku columns to the right, and one dense (kl x ku x 64) window update.  All
+// kernels read through a band view (out-of-band entries read as 0, never
+// written).
+#include <algorithm>
+
+#include "internal.h"
+#include "solve_driver.cuh"
+
+namespace ebv {
+
+namespace {
+
+template <typename T>
+struct BandGemm;
+template <>
+struct BandGemm<double> {
+  static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2;
+};
+template <>
+struct BandGemm<float> {
+  static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+};
+
+template <typename T>
+ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, cudaStream_t s) {
+  const Shadow<float> none{nullptr, nullptr, 0, nullptr};
+  using G = BandGemm<T>;
+  for (int64_t c0 = 0; c0 < n; c0 += kNB) {
+    const int w = (int)std::min<int64_t>(kNB, n - c0);
+    {
+      prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
+      k_diag_factor<T, kNB, 256><<<1, 256, 0, s>>>(A, c0, w, info);
+      EBV_TRY(launch_ok());
+    }
+    const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
+    const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
+    if (re > rb) {
+      prof::Scope ps(s, prof::kPanel, (double)(re - rb) * w * w);
+      k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, 128), 128, 0, s>>>(A, c0, w, rb, re, none);
+      EBV_TRY(launch_ok());
+    }
+    if (ce > cb) {
+      prof::Scope ps(s, prof::kPanel, (double)w * w * (ce - cb));
+      k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, 128), 128, 0, s>>>(A, c0, w, cb, ce, none);
+      EBV_TRY(launch_ok());
+    }
+    if (re > rb && ce > cb) {
+      prof::Scope ps(s, prof::kSimtGemm, 2.0 * (re - rb) * (ce - cb) * w);
+      dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
+      k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
+          <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w);
+      EBV_TRY(launch_ok());
+    }
+  }
+  return EBV_OK;
+}
+
+// R = B - A X for a row-band A, double-float accumulation as in the dense
+// residual.  One warp per row; the lanes stride over the row's band.
+__global__ void __launch_bounds__(256)
+    k_band_residual_df(const double *ab, int64_t ldab, int64_t n, int64_t kl, int64_t ku, const float *xhi,
+                       const float *xlo, int nrhs, const double *B, int64_t ldb, double *R, int64_t ldr,
+                       unsigned long long *rmax, const DevStatus *st) {
+  if (st && st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (i >= n) return;
+  const int64_t j0 = max64(0, i - kl), j1 = min64(n - 1, i + ku);
+  for (int c = 0; c < nrhs; ++c) {
+    TripleF acc;
+    acc.zero();
+    for (int64_t j = j0 + lane; j <= j1; j += 32) {
+      float a_h, a_l;
+      split_f64(ab[i * ldab + (j - i + kl)], a_h, a_l);
+      acc.fma_split(a_h, a_l, xhi[j * nrhs + c], xlo[j * nrhs + c]);
+    }
+    // Error-free (up to the l words) warp reduction of the triples.
+    for (int off = 16; off > 0; off >>= 1) {
+      TripleF o;
+      o.h = __shfl_xor_sync(0xffffffffu, acc.h, off);
+      o.m = __shfl_xor_sync(0xffffffffu, acc.m, off);
+      o.l = __shfl_xor_sync(0xffffffffu, acc.l, off);
+      acc.add(o);
+    }
+    if (lane == 0) {
+      const double rv = B[i * ldb + c] - acc.value();
+      R[i * ldr + c] = rv;
+      atomicMax(&rmax[c], (unsigned long long)__double_as_longlong(fabs(rv)));
+    }
+  }
+}
+
+}  // namespace
+
+size_t band_factor_ws(int64_t, int64_t, int64_t, ebv_prec_t) { return kStatusBytes; }
+size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
+  return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
+}
+
+ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t,
+                         cudaStream_t s) {
+  EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  if (d->n == 0) return EBV_OK;
+  if (prec == EBV_FP64) return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, s);
+  if (prec == EBV_FP32) return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, s);
+  return EBV_ERR_UNSUPPORTED;
+}
+
+ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
+                        int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
+                        size_t ws_bytes, cudaStream_t s) {
+  const int64_t n = d->n;
+  const bool fp64 = prec == EBV_FP64;
+  const DenseSolveLayout L = solve_layout(n, nrhs, fp64 ? 8 : 4);
+  if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
+  EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  if (n == 0 || nrhs == 0) return EBV_OK;
+  auto residual = [&](const float *xhi, const float *xlo, const double *bs, double *r, unsigned long long *rmax,
+                      DevStatus *st) -> ebv_status_t {
+    prof::Scope ps(s, prof::kResidual, 2.0 * n * (d->kl + d->ku + 1) * nrhs);
+    k_band_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(a_orig, d->ld, n, d->kl, d->ku, xhi, xlo, (int)nrhs, bs,
+                                                       nrhs, r, nrhs, rmax, st);
+    return launch_ok();
+  };
+  if (fp64)
+    return solve_refined<double>(band_view((double *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
+                                 (char *)ws, L, true, residual, s);
+  if (prec == EBV_FP32)
+    return solve_refined<float>(band_view((float *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
+                                (char *)ws, L, false, residual, s);
+  return EBV_ERR_UNSUPPORTED;
+}
+
+}  // namespace ebv

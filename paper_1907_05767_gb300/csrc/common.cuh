@@ -1,0 +1,93 @@
+// Shared helpers for the EbV CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstddef>
+
+#include "ebv.h"
+#include "profile.h"
+
+namespace ebv {
+
+// Leaf block size of the dense and banded factorisations (columns handled by
+// one diagonal-block kernel).
+constexpr int kNB = 64;
+
+// Bound on the polls of any device-side wait (each poll sleeps ~100 ns), so a
+// wait that never completes ends in well under a second with EBV_ERR_TIMEOUT.
+constexpr long long kSpinLimit = 1LL << 22;
+
+// Device status block kept at the start of every workspace.
+struct DevStatus {
+  int32_t code;   // ebv_status_t of the first device-side failure (0 = none)
+  int32_t where;  // kernel-specific detail (e.g. the block that timed out)
+  int32_t done;   // refinement: set once the stop test has passed
+  int32_t pad;
+};
+constexpr size_t kStatusBytes = 256;  // keeps what follows 256-byte aligned
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+#define EBV_TRY(expr)                       \
+  do {                                      \
+    ebv_status_t s_ = (expr);               \
+    if (s_ != EBV_OK) return s_;            \
+  } while (0)
+
+#define EBV_CU(expr)                        \
+  do {                                      \
+    cudaError_t e_ = (expr);                \
+    if (e_ != cudaSuccess) return EBV_ERR_CUDA; \
+  } while (0)
+
+inline ebv_status_t launch_ok() {
+  prof::count_launch();
+  return cudaGetLastError() == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
+}
+
+__host__ __device__ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// Conversions between the working types and the tensor-core operand types.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T from_float(float x);
+template <> __device__ __forceinline__ float from_float<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half from_float<__half>(float x) { return __float2half_rn(x); }
+
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(double x) { return (float)x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
+
+// Record the first device-side failure in a status block (first writer wins).
+__device__ __forceinline__ void set_status(DevStatus *st, int code, int where) {
+  if (st && atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+// Acquire load of a flag written by another CTA.
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *flag >= want; bounded.  Returns false on expiry.
+__device__ __forceinline__ bool wait_flag_geq(const int *flag, int want) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (ld_acquire(flag) >= want) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+}  // namespace ebv

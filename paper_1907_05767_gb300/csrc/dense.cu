@@ -1,0 +1,301 @@
+// Dense factorisation and solve drivers.
+//
+// Factorisation: recursive column-halving Doolittle (no pivoting).  A panel of
+// w columns is factored by factoring its left half, computing the U vectors of
+// the left half's rows for the right half (U12 = L11^{-1} A12), applying the
+// aggregated rank-1 updates of Eq. 6c to the right half (A22 -= L21 U12, one
+// GEMM with K = w/2) and factoring the right half.  The leaves are 64-column
+// blocks: an equal bi-vectorised diagonal-block kernel (Eq. 6-7) plus the
+// row-parallel L21 = A21 U11^{-1}.  Compared with a fixed-width right-looking
+// loop, the halving keeps most flops in GEMMs with a large K, which moves the
+// FP32 working matrix through HBM O(log n) times instead of O(n / nb) times.
+#include <algorithm>
+
+#include "internal.h"
+#include "solve_driver.cuh"
+
+namespace ebv {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Conversion of A to the FP32 working matrix and the power-of-two operand
+// scales of the half-precision tensor-core path.
+// ---------------------------------------------------------------------------
+__global__ void k_to_working(const double *a, int64_t lda, int64_t n, float *w, unsigned int *maxoff,
+                             unsigned int *mindiag) {
+  unsigned int lmax = 0u, lmin = 0x7F800000u;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    const float v = (float)a[i * lda + j];
+    w[e] = v;
+    const unsigned int bits = __float_as_uint(fabsf(v));
+    if (i == j)
+      lmin = min(lmin, bits);
+    else
+      lmax = max(lmax, bits);
+  }
+  atomicMax(maxoff, lmax);
+  atomicMin(mindiag, lmin);
+}
+
+// scale = [sL, sU, 1/(sL sU), -].  bfloat16 shares FP32's exponent range and
+// needs no scaling.  For half, L and U entries are bounded here by the largest
+// off-diagonal |a_ij| (over the smallest |a_ii| for L); each is scaled by the
+// power of two that brings that bound to 2^10, well inside half's normal range
+// [6.1e-5, 65504].  Powers of two make the scaling and the unscaling exact.
+__global__ void k_make_scale(int op, const unsigned int *maxoff, const unsigned int *mindiag, float *scale) {
+  float sl = 1.f, su = 1.f;
+  if (op == 1) {
+    const float mo = __uint_as_float(*maxoff);
+    float md = __uint_as_float(*mindiag);
+    if (!(md > 0.f) || isinf(md)) md = 1.f;
+    if (mo > 0.f && isfinite(mo)) {
+      int el = (int)floorf(log2f(1024.f * md / mo));
+      int eu = (int)floorf(log2f(1024.f / mo));
+      el = max(-40, min(40, el));
+      eu = max(-40, min(40, eu));
+      sl = ldexpf(1.f, el);
+      su = ldexpf(1.f, eu);
+    }
+  }
+  scale[0] = sl;
+  scale[1] = su;
+  scale[2] = (float)(1.0 / ((double)sl * (double)su));
+  scale[3] = 0.f;
+}
+
+template <typename T>
+struct SimtGemm;
+template <>
+struct SimtGemm<double> {
+  static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+};
+template <>
+struct SimtGemm<float> {
+  static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Mixed-precision GEMM dispatch.
+// ---------------------------------------------------------------------------
+static int g_lowp_mode = 0;
+void set_lowp_gemm_mode(int mode) { g_lowp_mode = mode; }
+int get_lowp_gemm_mode() { return g_lowp_mode; }
+
+ebv_status_t simt_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
+                         const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
+                         cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return EBV_OK;
+  constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
+  if (op == 0)
+    k_gemm_nt_simt<__nv_bfloat16, BM, BN, BK, TM, TN><<<grid, 256, 0, s>>>(
+        C, ldc, (const __nv_bfloat16 *)lb, (const __nv_bfloat16 *)ut, ldsh, scale, m0, n0, k0, M, N, K);
+  else
+    k_gemm_nt_simt<__half, BM, BN, BK, TM, TN><<<grid, 256, 0, s>>>(C, ldc, (const __half *)lb, (const __half *)ut,
+                                                                    ldsh, scale, m0, n0, k0, M, N, K);
+  return launch_ok();
+}
+
+ebv_status_t lowp_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
+                         const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
+                         DevStatus *dst, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return EBV_OK;
+  prof::Scope ps(s, prof::kLowpGemm, 2.0 * M * N * K);
+  if (g_lowp_mode != 1) {
+    ebv_status_t st = tc_update(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, dst, s);
+    if (st != EBV_ERR_UNSUPPORTED) return st;
+  }
+  return simt_update(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, s);
+}
+
+// ---------------------------------------------------------------------------
+// Recursive factorisation.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T, typename SH>
+struct Factorizer {
+  MatView<T> A;
+  int64_t n;
+  int32_t *info;
+  cudaStream_t s;
+  Shadow<SH> sh;
+  int op;  // -1: working-precision SIMT updates; 0/1: bf16/half tensor-core updates
+  DevStatus *st = nullptr;
+
+  static int64_t split(int64_t w) {  // leaf-aligned first half of a w-wide range
+    const int64_t nb = (w + kNB - 1) / kNB;
+    return ((nb + 1) / 2) * kNB;
+  }
+
+  ebv_status_t leaf(int64_t c0, int w) {
+    {
+      prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
+      k_diag_factor<T, kNB, 256><<<1, 256, 0, s>>>(A, c0, w, info);
+      EBV_TRY(launch_ok());
+    }
+    const int64_t rb = c0 + w, re = n;
+    if (re > rb) {
+      prof::Scope ps(s, prof::kPanel, (double)(re - rb) * w * w);
+      k_trsm_ru<T, SH, kNB><<<ceil_div(re - rb, 128), 128, 0, s>>>(A, c0, w, rb, re, sh);
+      EBV_TRY(launch_ok());
+    }
+    return EBV_OK;
+  }
+
+  ebv_status_t gemm(int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K) {
+    if (M <= 0 || N <= 0 || K <= 0) return EBV_OK;
+    if (op >= 0)
+      return lowp_update(op, (float *)A.base, A.ld, sh.lb, sh.ut, sh.ld, sh.scale, m0, n0, k0, M, N, K, st, s);
+    using G = SimtGemm<T>;
+    prof::Scope ps(s, prof::kSimtGemm, 2.0 * M * N * K);
+    dim3 grid(ceil_div(N, G::BN), ceil_div(M, G::BM));
+    k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
+        <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, m0, n0, k0, M, N, K);
+    return launch_ok();
+  }
+
+  // U(r0 .. r0+h, cl .. ch) = L(r0.., r0..)^{-1} A(r0.., cl..ch)
+  ebv_status_t trsm_ll(int64_t r0, int64_t h, int64_t cl, int64_t ch) {
+    if (ch <= cl || h <= 0) return EBV_OK;
+    if (h <= kNB) {
+      prof::Scope ps(s, prof::kPanel, (double)h * h * (ch - cl));
+      k_trsm_ll<T, SH, kNB><<<ceil_div(ch - cl, 128), 128, 0, s>>>(A, r0, (int)h, cl, ch, sh);
+      return launch_ok();
+    }
+    const int64_t h1 = split(h);
+    EBV_TRY(trsm_ll(r0, h1, cl, ch));
+    EBV_TRY(gemm(r0 + h1, cl, r0, h - h1, ch - cl, h1));
+    return trsm_ll(r0 + h1, h - h1, cl, ch);
+  }
+
+  // Factor columns c0 .. c0+w of rows c0 .. n.
+  ebv_status_t rlu(int64_t c0, int64_t w) {
+    if (w <= kNB) return leaf(c0, (int)w);
+    const int64_t w1 = split(w);
+    EBV_TRY(rlu(c0, w1));
+    EBV_TRY(trsm_ll(c0, w1, c0 + w1, c0 + w));
+    EBV_TRY(gemm(c0 + w1, c0 + w1, c0, n - c0 - w1, w - w1, w1));
+    return rlu(c0 + w1, w - w1);
+  }
+};
+
+struct DenseFactorLayout {
+  size_t lb, ut, scale, scan, total;
+  int64_t ldsh;  // shadow row stride: a multiple of 64 elements (128 B), as TMA wants 16-byte strides
+};
+
+DenseFactorLayout factor_layout(int64_t n, ebv_prec_t prec) {
+  DenseFactorLayout L{};
+  size_t off = kStatusBytes;
+  L.ldsh = (n + 63) / 64 * 64;
+  if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
+    L.lb = off; off = align256(off + (size_t)n * L.ldsh * 2);
+    L.ut = off; off = align256(off + (size_t)n * L.ldsh * 2);
+    L.scale = off; off = align256(off + 16);
+    L.scan = off; off = align256(off + 16);
+  }
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+size_t dense_factor_ws(int64_t n, ebv_prec_t prec) { return factor_layout(n, prec).total; }
+size_t dense_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
+  return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
+}
+
+ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
+                          size_t ws_bytes, cudaStream_t s) {
+  const int64_t n = d->n;
+  EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  if (n == 0) return EBV_OK;
+  if (prec == EBV_FP64) {
+    Factorizer<double, float> f{dense_view((double *)a, d->ld), n, info, s, Shadow<float>{nullptr, nullptr, 0, nullptr},
+                                -1};
+    return f.rlu(0, n);
+  }
+  if (prec == EBV_FP32) {
+    Factorizer<float, float> f{dense_view((float *)a, d->ld), n, info, s, Shadow<float>{nullptr, nullptr, 0, nullptr},
+                               -1};
+    return f.rlu(0, n);
+  }
+  // Mixed precisions: FP32 working copy in `lowp`, low-precision shadows in ws.
+  const DenseFactorLayout L = factor_layout(n, prec);
+  if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
+  char *w = (char *)ws;
+  unsigned int *scan = (unsigned int *)(w + L.scan);
+  float *scale = (float *)(w + L.scale);
+  EBV_CU(cudaMemsetAsync(scan, 0, 4, s));         // max |a_ij|, i != j: starts at +0
+  EBV_CU(cudaMemsetAsync(scan + 1, 0x7F, 4, s));  // min |a_ii|: starts at 0x7F7F7F7F (3.4e38)
+  k_to_working<<<grid_for(n * n), 256, 0, s>>>((const double *)a, d->ld, n, (float *)lowp, scan, scan + 1);
+  EBV_TRY(launch_ok());
+  const int op = prec == EBV_MIXED_BF16 ? 0 : 1;
+  k_make_scale<<<1, 1, 0, s>>>(op, scan, scan + 1, scale);
+  EBV_TRY(launch_ok());
+  if (op == 0) {
+    Factorizer<float, __nv_bfloat16> f{dense_view((float *)lowp, n), n, info, s,
+                                       Shadow<__nv_bfloat16>{(__nv_bfloat16 *)(w + L.lb), (__nv_bfloat16 *)(w + L.ut),
+                                                             L.ldsh, scale},
+                                       0, (DevStatus *)ws};
+    return f.rlu(0, n);
+  }
+  Factorizer<float, __half> f{dense_view((float *)lowp, n), n, info, s,
+                              Shadow<__half>{(__half *)(w + L.lb), (__half *)(w + L.ut), L.ldsh, scale}, 1,
+                              (DevStatus *)ws};
+  return f.rlu(0, n);
+}
+
+// R = B - A X with the refinement's residual kernel (testing hook).
+ebv_status_t debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b, int64_t nrhs,
+                            double *r, void *ws, size_t ws_bytes, cudaStream_t s) {
+  const DenseSolveLayout L = solve_layout(n, nrhs, 8);
+  if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
+  char *w = (char *)ws;
+  DevStatus *st = (DevStatus *)w;
+  EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  float *xhi = (float *)(w + L.xhi), *xlo = (float *)(w + L.xlo);
+  unsigned long long *rmax = (unsigned long long *)(w + L.rmax);
+  EBV_CU(cudaMemsetAsync(rmax, 0, nrhs * 8, s));
+  k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, nrhs, n, (int)nrhs, xhi, xlo, st);
+  EBV_TRY(launch_ok());
+  constexpr int RB = 32, RC = 32, KC = 32;
+  dim3 grid(ceil_div(n, RB), ceil_div(nrhs, RC));
+  k_residual_df<RB, RC, KC><<<grid, 256, 0, s>>>(a, lda, n, xhi, xlo, (int)nrhs, b, nrhs, r, nrhs, rmax, st);
+  return launch_ok();
+}
+
+ebv_status_t dense_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
+                         int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
+                         size_t ws_bytes, cudaStream_t s) {
+  const int64_t n = d->n;
+  const bool fp64 = prec == EBV_FP64;
+  const DenseSolveLayout L = solve_layout(n, nrhs, fp64 ? 8 : 4);
+  if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
+  EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  if (n == 0 || nrhs == 0) return EBV_OK;
+  char *w = (char *)ws;
+  auto residual = [&](const float *xhi, const float *xlo, const double *bs, double *r, unsigned long long *rmax,
+                      DevStatus *st) -> ebv_status_t {
+    constexpr int RB = 32, RC = 32, KC = 32;
+    dim3 grid(ceil_div(n, RB), ceil_div(nrhs, RC));
+    prof::Scope ps(s, prof::kResidual, 2.0 * n * n * nrhs);
+    k_residual_df<RB, RC, KC><<<grid, 256, 0, s>>>(a_orig, d->ld, n, xhi, xlo, (int)nrhs, bs, nrhs, r, nrhs, rmax,
+                                                    st);
+    return launch_ok();
+  };
+  const bool b_double = prec != EBV_FP32;
+  if (fp64)
+    return solve_refined<double>(dense_view((double *)lu, d->ld), n, b, nrhs, ldb, refine, rep, w, L, b_double,
+                                 residual, s);
+  const int64_t ldf = (prec == EBV_FP32) ? d->ld : n;
+  return solve_refined<float>(dense_view((float *)lu, ldf), n, b, nrhs, ldb, refine, rep, w, L, b_double, residual, s);
+}
+
+}  // namespace ebv

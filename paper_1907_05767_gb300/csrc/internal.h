@@ -1,0 +1,57 @@
+// Internal interfaces between the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ebv.h"
+
+namespace ebv {
+
+// Workspace bytes of the dense paths.
+size_t dense_factor_ws(int64_t n, ebv_prec_t prec);
+size_t dense_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec);
+size_t band_factor_ws(int64_t n, int64_t kl, int64_t ku, ebv_prec_t prec);
+size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec);
+
+ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
+                          size_t ws_bytes, cudaStream_t s);
+ebv_status_t dense_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
+                         int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
+                         size_t ws_bytes, cudaStream_t s);
+ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t ws_bytes,
+                         cudaStream_t s);
+ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
+                        int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
+                        size_t ws_bytes, cudaStream_t s);
+
+struct DevStatus;
+
+// Mixed-precision trailing update C(m0.., n0..) -= scale[2] * lb(m0.., k0..) * ut(n0.., k0..)^T
+// (op 0 = bfloat16 operands, 1 = half).  Uses the tcgen05 kernel when the
+// shape allows it, else the SIMT kernel.  st: device status block (timeouts).
+ebv_status_t lowp_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
+                         const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
+                         DevStatus *st, cudaStream_t s);
+
+// tcgen05 GEMM (tc_gemm.cu).  Returns EBV_ERR_UNSUPPORTED when the shape or
+// alignment does not fit the kernel (the caller then uses the SIMT kernel).
+ebv_status_t tc_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
+                       const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
+                       DevStatus *st, cudaStream_t s);
+bool tc_available();
+ebv_status_t simt_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
+                         const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
+                         cudaStream_t s);
+
+// 0 = automatic, 1 = force SIMT, 2 = force tensor cores (testing hooks).
+void set_lowp_gemm_mode(int mode);
+int get_lowp_gemm_mode();
+
+}  // namespace ebv
+
+namespace ebv {
+ebv_status_t debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b, int64_t nrhs,
+                            double *r, void *ws, size_t ws_bytes, cudaStream_t s);
+}  // namespace ebv

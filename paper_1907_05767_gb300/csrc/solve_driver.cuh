@@ -1,0 +1,127 @@
+// Solve driver shared by the dense and banded paths: block substitutions
+// (Eq. 1) and iterative refinement with an FP64-accurate residual.
+#pragma once
+
+#include <algorithm>
+
+#include "solve_kernels.cuh"
+
+namespace ebv {
+namespace {
+
+struct DenseSolveLayout {
+  size_t bsave, r, corr, xhi, xlo, flags, ticket, rmax, bmax, total;
+};
+
+DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize) {
+  DenseSolveLayout L{};
+  size_t off = kStatusBytes;
+  const size_t nn = (size_t)n * (size_t)std::max<int64_t>(nrhs, 1);
+  const size_t nblk = (size_t)std::max<int64_t>(1, (n + kNB - 1) / kNB);
+  const size_t nchunk = (size_t)std::max<int64_t>(1, (nrhs + 7) / 8);
+  L.bsave = off; off = align256(off + nn * 8);
+  L.r = off; off = align256(off + nn * 8);
+  L.corr = off; off = align256(off + nn * tsize);
+  L.xhi = off; off = align256(off + nn * 4);
+  L.xlo = off; off = align256(off + nn * 4);
+  L.flags = off; off = align256(off + 2 * nblk * nchunk * 4);
+  L.ticket = off; off = align256(off + 2 * 4);
+  L.rmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
+  L.bmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+struct TrsvCfg;
+template <>
+struct TrsvCfg<double> {
+  static constexpr int RC = 8;
+};
+template <>
+struct TrsvCfg<float> {
+  static constexpr int RC = 32;
+};
+
+// Forward then backward block substitution of B (n x nrhs, T) in place.
+template <typename T>
+ebv_status_t trsv_pair(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, int *flags, int *ticket, DevStatus *st,
+                       cudaStream_t s) {
+  constexpr int RC = TrsvCfg<T>::RC;
+  const int nblk = ceil_div(n, kNB), nchunk = ceil_div(nrhs, RC);
+  const size_t smem = trsv_smem_bytes<T, kNB, RC>();
+  EBV_CU(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * (size_t)nblk * nchunk, s));
+  EBV_CU(cudaMemsetAsync(ticket, 0, sizeof(int) * 2, s));
+  const double work = (double)n * n * nrhs;  // nominal n^2 flops per right-hand side and triangle
+  {
+    prof::Scope ps(s, prof::kTrsv, work);
+    k_trsv<T, kNB, RC, false><<<nblk * nchunk, 256, smem, s>>>(F, n, B, ldb, nrhs, flags, ticket, st);
+    EBV_TRY(launch_ok());
+  }
+  prof::Scope ps(s, prof::kTrsv, work);
+  k_trsv<T, kNB, RC, true><<<nblk * nchunk, 256, smem, s>>>(F, n, B, ldb, nrhs, flags + (size_t)nblk * nchunk,
+                                                            ticket + 1, st);
+  return launch_ok();
+}
+
+inline int grid_for(int64_t elems) { return (int)std::min<int64_t>(4096, std::max<int64_t>(1, (elems + 255) / 256)); }
+
+
+// ---------------------------------------------------------------------------
+// Solve with optional refinement.  Shared by the dense and banded paths
+// through the factor view F and the residual callback.
+// ---------------------------------------------------------------------------
+template <typename T, typename ResidualFn>
+ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64_t ldb,
+                                  const ebv_refine_t *refine, ebv_refine_report_t *rep, char *w,
+                                  const DenseSolveLayout &L, bool b_is_double, ResidualFn residual, cudaStream_t s) {
+  DevStatus *st = (DevStatus *)w;
+  int *flags = (int *)(w + L.flags);
+  int *ticket = (int *)(w + L.ticket);
+  const int nr = (int)nrhs;
+  if (!refine) {
+    if (b_is_double == (sizeof(T) == 8)) return trsv_pair<T>(F, n, (T *)b, ldb, nr, flags, ticket, st, s);
+    // FP32 factors applied to FP64 right-hand sides (mixed precisions, no refinement).
+    T *c = (T *)(w + L.corr);
+    k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>((const double *)b, ldb, c, nrhs, n, nr, st);
+    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, flags, ticket, st, s));
+    k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>((double *)b, ldb, c, nrhs, n, nr, 0, st);
+    return launch_ok();
+  }
+  if (!b_is_double) return EBV_ERR_UNSUPPORTED;
+  double *x = (double *)b;
+  double *bsave = (double *)(w + L.bsave);
+  double *r = (double *)(w + L.r);
+  T *c = (T *)(w + L.corr);
+  float *xhi = (float *)(w + L.xhi), *xlo = (float *)(w + L.xlo);
+  unsigned long long *rmax = (unsigned long long *)(w + L.rmax), *bmax = (unsigned long long *)(w + L.bmax);
+  EBV_CU(cudaMemcpy2DAsync(bsave, nrhs * 8, x, ldb * 8, nrhs * 8, n, cudaMemcpyDeviceToDevice, s));
+  EBV_CU(cudaMemsetAsync(bmax, 0, nrhs * 8, s));
+  k_colmax<<<grid_for(n * nrhs), 256, 0, s>>>(bsave, nrhs, n, nr, bmax);
+  EBV_TRY(launch_ok());
+  // x0 from the factors.
+  k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>(bsave, nrhs, c, nrhs, n, nr, st);
+  EBV_TRY(launch_ok());
+  EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, flags, ticket, st, s));
+  k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, c, nrhs, n, nr, 0, st);
+  EBV_TRY(launch_ok());
+  const int max_iter = std::max(0, refine->max_iter);
+  for (int it = 0; it <= max_iter; ++it) {
+    EBV_CU(cudaMemsetAsync(rmax, 0, nrhs * 8, s));
+    k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, n, nr, xhi, xlo, st);
+    EBV_TRY(launch_ok());
+    EBV_TRY(residual(xhi, xlo, bsave, r, rmax, st));
+    k_ir_check<<<1, 1, 0, s>>>(rmax, bmax, nr, it, max_iter, refine->tol, st, rep);
+    EBV_TRY(launch_ok());
+    if (it == max_iter) break;
+    k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>(r, nrhs, c, nrhs, n, nr, st);
+    EBV_TRY(launch_ok());
+    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, flags, ticket, st, s));
+    k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, c, nrhs, n, nr, 1, st);
+    EBV_TRY(launch_ok());
+  }
+  return EBV_OK;
+}
+
+}  // namespace
+}  // namespace ebv

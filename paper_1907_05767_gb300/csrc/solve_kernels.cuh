@@ -1,0 +1,382 @@
+// Triangular solves (Eq. 1: LY = B, then UX = Y) and iterative-refinement
+// kernels.
+#pragma once
+
+#include "dense_kernels.cuh"
+
+namespace ebv {
+namespace {  // internal linkage: every translation unit gets its own kernels
+
+// ---------------------------------------------------------------------------
+// Block triangular solve in one launch.  CTA "ticket" t (taken in start order,
+// so a CTA only ever waits on CTAs that already run) owns block row b of one
+// chunk of right-hand-side columns.  It folds in the finished blocks that row
+// b depends on as their flags appear (bounded waits), solves its diagonal
+// block from shared memory, writes its rows and releases its flag.
+//   UPPER = false: unit lower L,   forward,  blocks in increasing order.
+//   UPPER = true:  upper U,        backward, blocks in decreasing order; the
+//                  diagonal is applied through FP64 reciprocals.
+// Dynamic shared memory: T acc[NB][RC+1], T yb[NB][RC+1], T F[NB][NB+1],
+// double rcp[NB].
+// ---------------------------------------------------------------------------
+template <typename T, int NB, int RC>
+constexpr size_t trsv_smem_bytes() {
+  return sizeof(T) * (2 * NB * (RC + 1) + NB * (NB + 1)) + sizeof(double) * NB;
+}
+
+template <typename T, int NB, int RC, bool UPPER>
+__global__ void __launch_bounds__(256)
+    k_trsv(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, int *flags, int *ticket, DevStatus *st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*acc)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw);
+  T(*yb)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
+  T(*Fb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * 2 * NB * (RC + 1));
+  double *rcp = reinterpret_cast<double *>(smem_raw + sizeof(T) * (2 * NB * (RC + 1) + NB * (NB + 1)));
+  __shared__ int s_t, s_ok;
+  if (st && st->done) return;  // refinement already converged
+  const int nblk = ceil_div(n, NB);
+  const int nchunk = ceil_div(nrhs, RC);
+  if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
+  __syncthreads();
+  const int t = s_t;
+  const int chunk = t % nchunk, step = t / nchunk;
+  const int b = UPPER ? nblk - 1 - step : step;
+  const int64_t i0 = (int64_t)b * NB;
+  const int hb = (int)min64(NB, n - i0);
+  const int c0 = chunk * RC;
+  const int wc = min(RC, nrhs - c0);
+  int *myflags = flags + (int64_t)chunk * nblk;
+
+  for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
+    const int i = e / RC, c = e % RC;
+    acc[i][c] = (i < hb && c < wc) ? B[(i0 + i) * ldb + c0 + c] : T(0);
+  }
+  // Range of blocks row block b depends on (band limits included).
+  int jlo, jhi;
+  if (!UPPER) {
+    const int64_t cmin = i0 - F.kl;
+    jlo = cmin <= 0 ? 0 : (int)(cmin / NB);
+    jhi = b - 1;
+  } else {
+    const int64_t cmax = i0 + hb - 1 + F.ku;
+    jlo = b + 1;
+    jhi = (int)min64(nblk - 1, cmax / NB);
+  }
+  for (int q = 0; q <= jhi - jlo; ++q) {
+    const int j = UPPER ? jhi - q : jlo + q;  // the earliest-finished block first
+    const int64_t j0 = (int64_t)j * NB;
+    const int hj = (int)min64(NB, n - j0);
+    if (threadIdx.x == 0) {
+      bool ok = false;
+      for (long long it = 0; it < kSpinLimit; ++it) {
+        if (ld_acquire(&myflags[j]) >= 1) { ok = true; break; }
+        if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) break;
+        __nanosleep(100);
+      }
+      s_ok = ok;
+      if (!ok) set_status(st, EBV_ERR_TIMEOUT, b);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int i = e / NB, k = e % NB;
+      Fb[i][k] = (i < hb && k < hj) ? F.get(i0 + i, j0 + k) : T(0);
+    }
+    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
+      const int k = e / RC, c = e % RC;
+      yb[k][c] = (k < hj && c < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + c]) : T(0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
+      const int i = e / RC, c = e % RC;
+      T s = acc[i][c];
+#pragma unroll 16
+      for (int k = 0; k < NB; ++k) s -= Fb[i][k] * yb[k][c];
+      acc[i][c] = s;
+    }
+    __syncthreads();
+  }
+  // Diagonal block.
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, k = e % NB;
+    T v = T(0);
+    if (i < hb && k < hb) {
+      if (!UPPER && k < i) v = F.get(i0 + i, i0 + k);
+      if (UPPER && k >= i) v = F.get(i0 + i, i0 + k);
+    }
+    Fb[i][k] = v;
+  }
+  __syncthreads();
+  if (UPPER) {
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) rcp[i] = i < hb ? 1.0 / (double)Fb[i][i] : 0.0;
+    __syncthreads();
+    // Fold the reciprocal of pivot k into column k: row i then subtracts
+    // (u_ik / u_kk) * (unscaled final value of row k).
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+      const int i = e / NB, k = e % NB;
+      if (k > i) Fb[i][k] = (T)((double)Fb[i][k] * rcp[k]);
+    }
+    __syncthreads();
+    for (int r = hb - 1; r > 0; --r) {
+      for (int e = threadIdx.x; e < r * RC; e += blockDim.x) {
+        const int i = e / RC, c = e % RC;
+        acc[i][c] -= Fb[i][r] * acc[r][c];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
+      const int i = e / RC, c = e % RC;
+      if (i < hb && c < wc) B[(i0 + i) * ldb + c0 + c] = (T)((double)acc[i][c] * rcp[i]);
+    }
+  } else {
+    for (int r = 0; r < hb - 1; ++r) {
+      for (int e = threadIdx.x; e < (hb - 1 - r) * RC; e += blockDim.x) {
+        const int i = r + 1 + e / RC, c = e % RC;
+        acc[i][c] -= Fb[i][r] * acc[r][c];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
+      const int i = e / RC, c = e % RC;
+      if (i < hb && c < wc) B[(i0 + i) * ldb + c0 + c] = acc[i][c];
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(&myflags[b], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Iterative refinement helpers.
+// ---------------------------------------------------------------------------
+
+// Split a binary64 value into two binary32 values with a = hi + lo up to
+// 2^-47 |a|, using integer operations only (the FP64 pipe is the scarce unit
+// on this GPU).  hi is a with its significand truncated to 24 bits; lo is the
+// remainder rounded to binary32.  Magnitudes below 2^-126 map to 0 (their
+// contribution to a residual of an O(1) system is below 1e-37).
+__device__ __forceinline__ void split_f64(double a, float &hi, float &lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  const int ebias = (int)((u >> 52) & 0x7FF);
+  const int e = ebias - 1023;
+  if (ebias == 0x7FF) {  // inf / nan
+    hi = __int_as_float(sign | 0x7F800000u | (((u << 12) != 0) ? 0x400000u : 0u));
+    lo = 0.f;
+    return;
+  }
+  if (e < -126) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  if (e > 127) {
+    hi = __int_as_float(sign | 0x7F800000u);
+    lo = 0.f;
+    return;
+  }
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  hi = __int_as_float(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29));
+  const unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);
+  float l = __uint2float_rn(rem) * 2.220446049250313e-16f;  // * 2^-52, exact
+  l = l * __int_as_float((unsigned int)(e + 127) << 23);    // * 2^e
+  lo = sign ? -l : l;
+}
+
+// hi/lo planes of X (n x nrhs, FP64, ldx) for the residual kernel.
+__global__ void k_split_x(const double *x, int64_t ldx, int64_t n, int nrhs, float *xhi, float *xlo,
+                          const DevStatus *st) {
+  if (st && st->done) return;
+  const int64_t total = n * nrhs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nrhs;
+    const int c = (int)(e % nrhs);
+    const double v = x[i * ldx + c];
+    const float h = __double2float_rn(v);
+    xhi[e] = h;
+    xlo[e] = __double2float_rn(v - (double)h);
+  }
+}
+
+// Knuth's TwoSum, s + e == a + b exactly.  The _rn intrinsics are never
+// contracted into fused multiply-adds, which would break the identity.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// p + e == a * b exactly (TwoProduct through the fused multiply-add).
+__device__ __forceinline__ void two_prod_f(float a, float b, float &p, float &e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+
+// Accumulation of long dot products whose partial sums are O(1) while the
+// result is tiny (a residual b - Ax near convergence), in binary32 only.
+//
+// A double-float (h, l) pair is not enough: once a large term (the diagonal
+// of a dominant row) has entered, each TwoSum error of h is ~2^-25 |h|, the
+// low word grows to ~sqrt(k) 2^-25 |h| after k terms and its own binary32
+// rounding random-walks to ~1e-13 |h| and beyond.  TripleF gives every
+// first-order quantity an error-free level: the products go into h by TwoSum,
+// the TwoSum errors of h and the product errors / cross terms (both
+// ~2^-24 |a x|) go into m by TwoSum, and only second-order errors
+// (~2^-48 |partial sums|) reach the plain word l.  About 25 binary32
+// operations per multiply-add, with no FP64 instruction in the loop.
+struct TripleF {
+  float h, m, l;
+  __device__ __forceinline__ void zero() { h = m = l = 0.f; }
+  // += (a_h + a_l) * (x_h + x_l), dropping a_l * x_l (relative 2^-47 or less).
+  __device__ __forceinline__ void fma_split(float a_h, float a_l, float x_h, float x_l) {
+    float p, pe, s, e1, t, e2, u, e3;
+    two_prod_f(a_h, x_h, p, pe);
+    const float c = pe + fmaf(a_h, x_l, a_l * x_h);  // rounding ~2^-48 |a x|
+    two_sum_f(h, p, s, e1);
+    two_sum_f(m, e1, t, e2);
+    two_sum_f(t, c, u, e3);
+    h = s;
+    m = u;
+    l += e2 + e3;
+  }
+  __device__ __forceinline__ void add(const TripleF &o) {
+    float s, e1, t, e2, u, e3;
+    two_sum_f(h, o.h, s, e1);
+    two_sum_f(m, o.m, t, e2);
+    two_sum_f(t, e1, u, e3);
+    h = s;
+    m = u;
+    l += o.l + e2 + e3;
+  }
+  __device__ __forceinline__ double value() const { return (double)h + ((double)m + (double)l); }
+};
+
+// R = B - A X with A in FP64, evaluated in double-float arithmetic (pairs of
+// binary32 with error-free TwoSum / FMA-based TwoProduct, i.e. about 48
+// significant bits) so the FP64 ALU, ~75x slower than FP32 on GB300, is
+// touched once per output.  CTA tile: RB rows x RC right-hand sides; K staged
+// through shared memory in KC-wide slabs.  Also folds max_i |R_ic| per column
+// into rmax (as ordered bit patterns).
+template <int RB, int RC, int KC>
+__global__ void __launch_bounds__(256)
+    k_residual_df(const double *A, int64_t lda, int64_t n, const float *xhi, const float *xlo, int nrhs,
+                  const double *B, int64_t ldb, double *R, int64_t ldr, unsigned long long *rmax,
+                  const DevStatus *st) {
+  constexpr int NT = 256;
+  constexpr int ROWS_PER_PASS = NT / RC;
+  constexpr int OPT = RB / ROWS_PER_PASS;  // outputs per thread
+  static_assert(NT % RC == 0 && RB % ROWS_PER_PASS == 0, "shape");
+  __shared__ float ah[RB][KC + 1], al[RB][KC + 1];
+  __shared__ float xh[KC][RC + 1], xl[KC][RC + 1];
+  __shared__ unsigned long long cmax[RC];
+  if (st && st->done) return;
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  const int c0 = blockIdx.y * RC;
+  const int c = threadIdx.x % RC;
+  const int rr = threadIdx.x / RC;
+  TripleF acc[OPT];
+#pragma unroll
+  for (int q = 0; q < OPT; ++q) acc[q].zero();
+  if (threadIdx.x < RC) cmax[threadIdx.x] = 0ull;
+  for (int64_t k0 = 0; k0 < n; k0 += KC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < RB * KC; e += NT) {
+      const int i = e / KC, k = e % KC;
+      const int64_t gi = r0 + i, gk = k0 + k;
+      float h = 0.f, l = 0.f;
+      if (gi < n && gk < n) split_f64(A[gi * lda + gk], h, l);
+      ah[i][k] = h;
+      al[i][k] = l;
+    }
+    for (int e = threadIdx.x; e < KC * RC; e += NT) {
+      const int k = e / RC, cc = e % RC;
+      const int64_t gk = k0 + k;
+      const bool ok = gk < n && c0 + cc < nrhs;
+      xh[k][cc] = ok ? xhi[gk * nrhs + c0 + cc] : 0.f;
+      xl[k][cc] = ok ? xlo[gk * nrhs + c0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KC; ++k) {
+      const float xhk = xh[k][c], xlk = xl[k][c];
+#pragma unroll
+      for (int q = 0; q < OPT; ++q) {
+        const int i = rr + q * ROWS_PER_PASS;
+        acc[q].fma_split(ah[i][k], al[i][k], xhk, xlk);
+      }
+    }
+  }
+  double dmax = 0.0;
+#pragma unroll
+  for (int q = 0; q < OPT; ++q) {
+    const int64_t gi = r0 + rr + q * ROWS_PER_PASS;
+    if (gi < n && c0 + c < nrhs) {
+      const double rv = B[gi * ldb + c0 + c] - acc[q].value();
+      R[gi * ldr + c0 + c] = rv;
+      dmax = fmax(dmax, fabs(rv));
+    }
+  }
+  atomicMax(&cmax[c], (unsigned long long)__double_as_longlong(dmax));
+  __syncthreads();
+  if (threadIdx.x < RC && c0 + threadIdx.x < nrhs) atomicMax(&rmax[c0 + threadIdx.x], cmax[threadIdx.x]);
+}
+
+// max_i |B_ic| per column (ordered bit patterns).
+__global__ void k_colmax(const double *B, int64_t ldb, int64_t n, int nrhs, unsigned long long *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nrhs;
+    const int c = (int)(e % nrhs);
+    atomicMax(&out[c], (unsigned long long)__double_as_longlong(fabs(B[i * ldb + c])));
+  }
+}
+
+// Stop test of refinement step `it` (0 = residual of the unrefined solution).
+__global__ void k_ir_check(const unsigned long long *rmax, const unsigned long long *bmax, int nrhs, int it,
+                           int max_iter, double tol, DevStatus *st, ebv_refine_report_t *rep) {
+  if (st->done) return;
+  double rel = 0.0;
+  for (int c = 0; c < nrhs; ++c) {
+    const double r = __longlong_as_double((long long)rmax[c]);
+    const double bb = __longlong_as_double((long long)bmax[c]);
+    const double q = bb > 0.0 ? r / bb : r;
+    rel = (q > rel || q != q) ? q : rel;
+  }
+  if (rep) {
+    if (it == 0) rep->resid_first = rel;
+    rep->resid_final = rel;
+    rep->iters = it;
+  }
+  const bool conv = rel <= tol;
+  if (conv || it >= max_iter) {
+    st->done = 1;
+    if (rep) rep->status = conv ? EBV_OK : EBV_ERR_NOT_CONVERGED;
+  }
+}
+
+// dst(n x nrhs, T) = (T) src (FP64), skipped once refinement has converged.
+template <typename T>
+__global__ void k_narrow(const double *src, int64_t lds, T *dst, int64_t ldd, int64_t n, int nrhs,
+                         const DevStatus *st) {
+  if (st && st->done) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nrhs;
+    const int c = (int)(e % nrhs);
+    dst[i * ldd + c] = (T)src[i * lds + c];
+  }
+}
+
+// x (FP64) = d, or x += d when accumulate; skipped once converged.
+template <typename T>
+__global__ void k_update_x(double *x, int64_t ldx, const T *d, int64_t ldd, int64_t n, int nrhs, int accumulate,
+                           const DevStatus *st) {
+  if (st && st->done) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / nrhs;
+    const int c = (int)(e % nrhs);
+    const double v = (double)d[i * ldd + c];
+    x[i * ldx + c] = accumulate ? x[i * ldx + c] + v : v;
+  }
+}
+
+}  // namespace
+}  // namespace ebv

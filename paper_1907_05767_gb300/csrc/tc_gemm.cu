@@ -1,0 +1,310 @@
+// Tensor-core (tcgen05) trailing update of the mixed-precision factorisation:
+//
+//   C(m0+i, n0+j) -= scale * sum_{k<K} lb(m0+i, k0+k) * ut(n0+j, k0+k)
+//
+// i.e. K aggregated rank-1 updates of Eq. 6c with bfloat16 / half operands
+// and FP32 accumulation.  lb holds L (row-major) and ut holds U^T, so both
+// operands are K-major.
+//
+// One 128 x BN output tile per CTA of 6 warps:
+//   warp 0      TMA producer: 128x64 A and BNx64 B slabs, 128-byte swizzle,
+//               into a STAGES-deep ring guarded by full/empty mbarriers;
+//   warp 1      allocates BN TMEM columns; one lane issues tcgen05.mma
+//               (M=128, N=BN, K=16) into the TMEM accumulator and commits
+//               each slab back to its empty barrier;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32*(w%4)...), C -= scale * D in FP32.
+// Every mbarrier wait is bounded; on expiry the CTA records EBV_ERR_TIMEOUT,
+// drains its own TMA copies and MMAs (bounded), frees TMEM and returns.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ebv {
+
+namespace {
+
+constexpr int BM = 128, BK = 64, STAGES = 4, NTHREADS = 192;
+constexpr long long kMbarPolls = 1LL << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; gives up early once the
+// CTA's abort flag is set (abort may be null).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  for (long long i = 0; i < kMbarPolls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (abort && (i & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile whose rows are 128 bytes
+// (64 x 16-bit) stored with the 128-byte swizzle: 8-row core groups 1024 bytes
+// apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B of the same
+// 16-bit type (fmt 0 = half, 1 = bfloat16), both K-major, M = 128, N = n.
+constexpr uint32_t make_idesc(uint32_t fmt, int n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int BN>
+constexpr int smem_bytes() {
+  return STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 /* alignment slack */ + 256 /* barriers */;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *C, int64_t ldc,
+                const float *scale, int64_t m0, int64_t n0, int k0, int M, int N, int KB, uint32_t idesc, int vec_ok,
+                DevStatus *st) {
+  constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(base + STAGES * STAGE_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *tfull = empty + STAGES;
+  uint32_t *tmem_holder = (uint32_t *)(tfull + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+  auto stage_a = [&](int s) { return base + s * STAGE_BYTES; };
+  auto stage_b = [&](int s) { return base + s * STAGE_BYTES + A_BYTES; };
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tile_n = blockIdx.x, tile_m = blockIdx.y;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  auto fail = [&](int where) {
+    *abort_flag = 1;
+    set_status(st, EBV_ERR_TIMEOUT, where);
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    const int ya = (int)(m0 + (int64_t)tile_m * BM), yb = (int)(n0 + (int64_t)tile_n * BN);
+    int issued = 0;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES, u = kb / STAGES;
+      if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, abort_flag)) {
+        fail(1);
+        break;
+      }
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(stage_a(s), &tmA, &full[s], k0 + kb * BK, ya);
+      tma_load_2d(stage_b(s), &tmB, &full[s], k0 + kb * BK, yb);
+      issued = kb + 1;
+    }
+    // Our own copies must have landed before the CTA may exit.
+    for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; ++kb)
+      if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, nullptr)) set_status(st, EBV_ERR_TIMEOUT, 2);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % STAGES, u = kb / STAGES;
+      if (!mbar_wait(&full[s], u & 1, abort_flag)) {
+        fail(3);
+        break;
+      }
+      tc_fence_after();
+      const uint64_t adesc = sw128_desc(smem_u32(stage_a(s)));
+      const uint64_t bdesc = sw128_desc(smem_u32(stage_b(s)));
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)  // +32 bytes along K inside the swizzle atom
+        umma_f16(tmem, adesc + 2 * k, bdesc + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(tfull);
+    if (!mbar_wait(tfull, 0, nullptr)) set_status(st, EBV_ERR_TIMEOUT, 4);  // MMAs retired before TMEM is freed
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int64_t gi = m0 + (int64_t)tile_m * BM + row;
+    const bool row_ok = gi < m0 + M;
+    if (mbar_wait(tfull, 0, abort_flag)) {
+      tc_fence_after();
+      const float inv = scale[2];
+      float *crow = C + gi * ldc;
+      const int64_t jbase = n0 + (int64_t)tile_n * BN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the divergent stores
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        const int64_t gj0 = jbase + c0;
+        if (!row_ok || gj0 >= n0 + N) continue;
+        if (vec_ok && gj0 + 16 <= n0 + N) {
+          float4 *p = reinterpret_cast<float4 *>(crow + gj0);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float4 c = p[v];
+            c.x -= __uint_as_float(r[4 * v + 0]) * inv;
+            c.y -= __uint_as_float(r[4 * v + 1]) * inv;
+            c.z -= __uint_as_float(r[4 * v + 2]) * inv;
+            c.w -= __uint_as_float(r[4 * v + 3]) * inv;
+            p[v] = c;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (gj0 + j < n0 + N) crow[gj0 + j] -= __uint_as_float(r[j]) * inv;
+        }
+      }
+    } else {
+      fail(5);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *map, int op, const void *base, int64_t cols, int64_t rows, int64_t ld_elems, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld_elems * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, op == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                        const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+ebv_status_t launch_tc(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh, const float *scale,
+                       int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, DevStatus *st,
+                       cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_tc_update<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<BN>());
+  });
+  if (attr_err != cudaSuccess) return EBV_ERR_CUDA;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, op, lb, k0 + K, m0 + M, ldsh, BM)) return EBV_ERR_UNSUPPORTED;
+  if (!make_map(&mb, op, ut, k0 + K, n0 + N, ldsh, BN)) return EBV_ERR_UNSUPPORTED;
+  const int vec_ok = (ldc % 4 == 0) && (n0 % 4 == 0) && (((uintptr_t)C) % 16 == 0);
+  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
+  k_tc_update<BN><<<grid, NTHREADS, smem_bytes<BN>(), s>>>(ma, mb, C, ldc, scale, m0, n0, (int)k0, (int)M, (int)N,
+                                                          (int)(K / BK), make_idesc(op == 0 ? 1u : 0u, BN), vec_ok, st);
+  return launch_ok();
+}
+
+}  // namespace
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+ebv_status_t tc_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
+                       const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
+                       DevStatus *st, cudaStream_t s) {
+  // Shapes the kernel takes: whole 64-wide K slabs, 16-byte aligned rows and
+  // slab origins (TMA), coordinates inside int range.
+  if (K <= 0 || K % BK != 0 || k0 % 8 != 0 || (ldsh * 2) % 16 != 0) return EBV_ERR_UNSUPPORTED;
+  if (((uintptr_t)lb) % 16 != 0 || ((uintptr_t)ut) % 16 != 0) return EBV_ERR_UNSUPPORTED;
+  if (m0 + M > INT32_MAX || n0 + N > INT32_MAX || k0 + K > INT32_MAX) return EBV_ERR_UNSUPPORTED;
+  if (N >= 192) return launch_tc<256>(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, st, s);
+  if (N > 64) return launch_tc<128>(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, st, s);
+  return launch_tc<64>(op, C, ldc, lb, ut, ldsh, scale, m0, n0, k0, M, N, K, st, s);
+}
+
+}  // namespace ebv

@@ -1,0 +1,105 @@
+"""C ABI: the library loads without a GPU, exports every declared entry point,
+and rejects invalid arguments on the host before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1907_05767_gb300 as ebv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1907_05767_gb300 import _build
+    _build.build()
+    return ebv.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(ebv_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "ebv_factor" in names and "ebv_solve" in names
+    assert "ebv_factor_solve_batched" in names and "ebv_solve_adjoint" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(ebv.EXPORTED)
+
+
+def test_version_and_status_strings(lib):
+    assert lib.ebv_version() >= 100
+    for s in range(9):
+        assert lib.ebv_status_string(s)
+    assert lib.ebv_status_string(99) == b"unknown status"
+
+
+def _d(n, ld, kl=0, ku=0, storage=ebv.DENSE):
+    return ebv.Desc(n, ld, kl, ku, storage, 0)
+
+
+FAKE = ctypes.c_void_p(0x100000)  # never dereferenced: every call below fails its host checks
+
+
+def test_factor_argument_errors(lib):
+    info = FAKE
+    cases = [
+        (None, ebv.FP64),                                  # null descriptor
+        (_d(-1, 4), ebv.FP64),                             # negative order
+        (_d(8, 7), ebv.FP64),                              # ld < n
+        (_d(8, 8), 9),                                     # unknown precision
+        (_d(8, 8, 8, 1, ebv.BAND), ebv.FP64),              # kl >= n
+        (_d(8, 3, 1, 2, ebv.BAND), ebv.FP64),              # ld < kl+ku+1
+        (_d(8, 8, 0, 0, 7), ebv.FP64),                     # unknown storage
+    ]
+    for d, p in cases:
+        st = lib.ebv_factor(ctypes.byref(d) if d is not None else None, p, FAKE, None, info, None, 0, None)
+        assert st == ebv.ERR_ARG, (d and (d.n, d.ld, d.kl, d.ku, d.storage), p, st)
+    d = _d(8, 8)
+    assert lib.ebv_factor(ctypes.byref(d), ebv.FP64, FAKE, None, None, None, 0, None) == ebv.ERR_ARG  # null info
+    assert lib.ebv_factor(ctypes.byref(d), ebv.FP64, None, None, info, None, 0, None) == ebv.ERR_ARG  # null a
+    # mixed precision needs the FP32 output buffer and the workspace
+    assert lib.ebv_factor(ctypes.byref(d), ebv.MIXED_BF16, FAKE, None, info, None, 0, None) == ebv.ERR_ARG
+    assert lib.ebv_factor(ctypes.byref(d), ebv.MIXED_BF16, FAKE, FAKE, info, None, 0, None) == ebv.ERR_WORKSPACE
+    # mixed precision is dense only
+    db = _d(8, 3, 1, 1, ebv.BAND)
+    assert lib.ebv_factor(ctypes.byref(db), ebv.MIXED_FP16, FAKE, FAKE, info, None, 0, None) == ebv.ERR_UNSUPPORTED
+
+
+def test_solve_argument_errors(lib):
+    d = _d(8, 8)
+    ws = ctypes.c_void_p(0x200000)
+    ok_ref = ebv.Refine(1e-12, 5, 0)
+    bad_ref = ebv.Refine(-1.0, 5, 0)
+    call = lambda **k: lib.ebv_solve(ctypes.byref(k.get("d", d)), k.get("p", ebv.FP64), k.get("lu", FAKE),
+                                     k.get("a", None), k.get("b", FAKE), k.get("nrhs", 2), k.get("ldb", 2),
+                                     k.get("ref", None), None, k.get("ws", ws), k.get("wsb", 1 << 30), None)
+    assert call(nrhs=-1) == ebv.ERR_ARG
+    assert call(ldb=1) == ebv.ERR_ARG
+    assert call(lu=None) == ebv.ERR_ARG
+    assert call(b=None) == ebv.ERR_ARG
+    assert call(ref=ctypes.byref(bad_ref), a=FAKE) == ebv.ERR_ARG
+    assert call(ref=ctypes.byref(ok_ref)) == ebv.ERR_ARG          # refinement needs the original A
+    assert call(p=ebv.MIXED_BF16, ref=ctypes.byref(ok_ref)) == ebv.ERR_ARG
+    assert call(p=ebv.FP32, ref=ctypes.byref(ok_ref), a=FAKE) == ebv.ERR_UNSUPPORTED
+    assert call(ws=None) == ebv.ERR_WORKSPACE
+    assert call(ws=ctypes.c_void_p(0x200010)) == ebv.ERR_WORKSPACE  # misaligned workspace
+
+
+def test_workspace_sizes(lib):
+    sz = lambda n, p, r: ebv.ebv_workspace_size(n, p, r)
+    assert sz(1024, ebv.MIXED_BF16, 0) >= 2 * 2 * 1024 * 1024  # two 16-bit shadows of the factors
+    assert sz(1024, ebv.FP64, 32) >= 1024 * 32 * 8 * 2
+    assert sz(1024, ebv.FP64, 32) > sz(1024, ebv.FP64, 1)
+    d = _d(-3, 1)
+    assert lib.ebv_workspace_size(ctypes.byref(d), ebv.FP64, 0) == 0
