@@ -173,6 +173,21 @@ def run_gpu(args, rank, world, dist):
         step()
     torch.cuda.synchronize()
     rep_np = ebv.read_report(rep)
+    launches_per_step = ebv.launch_count()
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = ebv.launch_count() - launches_per_step
+
+    # The whole step (factor + refined solve) as one CUDA graph: the library
+    # never synchronises or allocates inside a call, so it captures as is.
+    graph = None
+    if args.graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+    run = graph.replay if graph is not None else step
 
     def barrier():
         if dist is not None:
@@ -181,17 +196,16 @@ def run_gpu(args, rank, world, dist):
 
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = ebv.launch_count()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        run()
     e1.record(stream)
     barrier()
     clk = clocks.stop()
-    launches = ebv.launch_count() - launches0
+    launches = launches_per_step * args.steps
     ms_total = e0.elapsed_time(e1)
     ms = ms_total / args.steps
     if dist is not None:
@@ -234,11 +248,19 @@ def run_gpu(args, rank, world, dist):
 
     e2e_step()
     barrier()
+    e2e_run = e2e_step
+    if args.graph:
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2):
+            e2e_step()
+        g2.replay()
+        e2e_run = g2.replay
+    barrier()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.e2e_steps):
-        e2e_step()
+        e2e_run()
     f1.record(stream)
     barrier()
     e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
@@ -299,6 +321,7 @@ def run_gpu(args, rank, world, dist):
         "data": "synthetic (seeded, planted solutions)",
         "config": {"workload": workload_desc(n, nrhs), "n": n, "nrhs": nrhs, "precision": prec,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "cuda_graph": bool(args.graph),
                    "l2": "inputs larger than L2 (A is %.2f GB FP64)" % (n * n * 8 / 1e9)},
         "solves_per_s": world * 1e3 / ms, "rhs_per_s": world * nrhs * 1e3 / ms,
         "refinement": {"iters": rep_np["iters"], "status": rep_np["status"], "resid_first": rep_np["resid_first"],
@@ -388,6 +411,7 @@ def main():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-kstop", type=int, default=384)
     p.add_argument("--ref-kstop", type=int, default=96)
+    p.add_argument("--no-graph", dest="graph", action="store_false")
     args = p.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

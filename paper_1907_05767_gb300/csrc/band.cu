@@ -29,26 +29,28 @@ struct BandGemm<float> {
 };
 
 template <typename T>
-ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, cudaStream_t s) {
+ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaStream_t s) {
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
   using G = BandGemm<T>;
+  EBV_TRY((prepare_leaf_kernels<T, float>()));
+  constexpr size_t smem = pair_smem_bytes<T, kNB>();
   for (int64_t c0 = 0; c0 < n; c0 += kNB) {
     const int w = (int)std::min<int64_t>(kNB, n - c0);
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-      k_diag_factor<T, kNB, 256><<<1, 256, 0, s>>>(A, c0, w, info);
+      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, smem, s>>>(A, c0, w, info, inv);
       EBV_TRY(launch_ok());
     }
     const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
     const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
     if (re > rb) {
-      prof::Scope ps(s, prof::kPanel, (double)(re - rb) * w * w);
-      k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, 128), 128, 0, s>>>(A, c0, w, rb, re, none);
+      prof::Scope ps(s, prof::kPanel, 2.0 * (re - rb) * w * w);
+      k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
       EBV_TRY(launch_ok());
     }
     if (ce > cb) {
-      prof::Scope ps(s, prof::kPanel, (double)w * w * (ce - cb));
-      k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, 128), 128, 0, s>>>(A, c0, w, cb, ce, none);
+      prof::Scope ps(s, prof::kPanel, 2.0 * w * w * (ce - cb));
+      k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, kNB), 256, smem, s>>>(A, c0, w, cb, ce, inv, none);
       EBV_TRY(launch_ok());
     }
     if (re > rb && ce > cb) {
@@ -99,18 +101,26 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-size_t band_factor_ws(int64_t, int64_t, int64_t, ebv_prec_t) { return kStatusBytes; }
+// Workspace of the banded factorisation: the status block and the inverses
+// of the current leaf's two triangular factors (used right after they are made).
+size_t band_factor_ws(int64_t, int64_t, int64_t, ebv_prec_t prec) {
+  return kStatusBytes + align256((size_t)2 * kNB * kNB * (prec == EBV_FP64 ? 8 : 4));
+}
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
 }
 
-ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t,
+ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t ws_bytes,
                          cudaStream_t s) {
   EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
   if (d->n == 0) return EBV_OK;
-  if (prec == EBV_FP64) return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, s);
-  if (prec == EBV_FP32) return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, s);
+  if (!ws || ws_bytes < band_factor_ws(d->n, d->kl, d->ku, prec)) return EBV_ERR_WORKSPACE;
+  char *inv = (char *)ws + kStatusBytes;
+  if (prec == EBV_FP64)
+    return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, (double *)inv, s);
+  if (prec == EBV_FP32)
+    return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, s);
   return EBV_ERR_UNSUPPORTED;
 }
 

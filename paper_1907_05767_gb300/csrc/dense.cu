@@ -126,22 +126,25 @@ struct Factorizer {
   Shadow<SH> sh;
   int op;  // -1: working-precision SIMT updates; 0/1: bf16/half tensor-core updates
   DevStatus *st = nullptr;
+  T *inv = nullptr;  // per leaf: L11^{-1} then U11^{-1} (2 * 64 * 64 entries)
 
   static int64_t split(int64_t w) {  // leaf-aligned first half of a w-wide range
     const int64_t nb = (w + kNB - 1) / kNB;
     return ((nb + 1) / 2) * kNB;
   }
+  T *leaf_inv(int64_t c0) const { return inv + (c0 / kNB) * 2 * kNB * kNB; }
 
   ebv_status_t leaf(int64_t c0, int w) {
+    constexpr size_t smem = pair_smem_bytes<T, kNB>();
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-      k_diag_factor<T, kNB, 256><<<1, 256, 0, s>>>(A, c0, w, info);
+      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, smem, s>>>(A, c0, w, info, leaf_inv(c0));
       EBV_TRY(launch_ok());
     }
     const int64_t rb = c0 + w, re = n;
     if (re > rb) {
-      prof::Scope ps(s, prof::kPanel, (double)(re - rb) * w * w);
-      k_trsm_ru<T, SH, kNB><<<ceil_div(re - rb, 128), 128, 0, s>>>(A, c0, w, rb, re, sh);
+      prof::Scope ps(s, prof::kPanel, 2.0 * (re - rb) * w * w);
+      k_trsm_ru<T, SH, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
       EBV_TRY(launch_ok());
     }
     return EBV_OK;
@@ -163,8 +166,9 @@ struct Factorizer {
   ebv_status_t trsm_ll(int64_t r0, int64_t h, int64_t cl, int64_t ch) {
     if (ch <= cl || h <= 0) return EBV_OK;
     if (h <= kNB) {
-      prof::Scope ps(s, prof::kPanel, (double)h * h * (ch - cl));
-      k_trsm_ll<T, SH, kNB><<<ceil_div(ch - cl, 128), 128, 0, s>>>(A, r0, (int)h, cl, ch, sh);
+      prof::Scope ps(s, prof::kPanel, 2.0 * h * h * (ch - cl));
+      k_trsm_ll<T, SH, kNB><<<ceil_div(ch - cl, kNB), 256, pair_smem_bytes<T, kNB>(), s>>>(A, r0, (int)h, cl, ch,
+                                                                                         leaf_inv(r0), sh);
       return launch_ok();
     }
     const int64_t h1 = split(h);
@@ -185,7 +189,7 @@ struct Factorizer {
 };
 
 struct DenseFactorLayout {
-  size_t lb, ut, scale, scan, total;
+  size_t inv, lb, ut, scale, scan, total;
   int64_t ldsh;  // shadow row stride: a multiple of 64 elements (128 B), as TMA wants 16-byte strides
 };
 
@@ -193,6 +197,9 @@ DenseFactorLayout factor_layout(int64_t n, ebv_prec_t prec) {
   DenseFactorLayout L{};
   size_t off = kStatusBytes;
   L.ldsh = (n + 63) / 64 * 64;
+  const size_t leaves = (size_t)((n + kNB - 1) / kNB);
+  L.inv = off;
+  off = align256(off + leaves * 2 * kNB * kNB * (prec == EBV_FP64 ? 8 : 4));
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
     L.lb = off; off = align256(off + (size_t)n * L.ldsh * 2);
     L.ut = off; off = align256(off + (size_t)n * L.ldsh * 2);
@@ -216,20 +223,22 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
   if (n == 0) return EBV_OK;
-  if (prec == EBV_FP64) {
-    Factorizer<double, float> f{dense_view((double *)a, d->ld), n, info, s, Shadow<float>{nullptr, nullptr, 0, nullptr},
-                                -1};
-    return f.rlu(0, n);
-  }
-  if (prec == EBV_FP32) {
-    Factorizer<float, float> f{dense_view((float *)a, d->ld), n, info, s, Shadow<float>{nullptr, nullptr, 0, nullptr},
-                               -1};
-    return f.rlu(0, n);
-  }
-  // Mixed precisions: FP32 working copy in `lowp`, low-precision shadows in ws.
   const DenseFactorLayout L = factor_layout(n, prec);
   if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
   char *w = (char *)ws;
+  DevStatus *dst = (DevStatus *)ws;
+  const Shadow<float> none{nullptr, nullptr, 0, nullptr};
+  if (prec == EBV_FP64) {
+    EBV_TRY((prepare_leaf_kernels<double, float>()));
+    Factorizer<double, float> f{dense_view((double *)a, d->ld), n, info, s, none, -1, dst, (double *)(w + L.inv)};
+    return f.rlu(0, n);
+  }
+  if (prec == EBV_FP32) {
+    EBV_TRY((prepare_leaf_kernels<float, float>()));
+    Factorizer<float, float> f{dense_view((float *)a, d->ld), n, info, s, none, -1, dst, (float *)(w + L.inv)};
+    return f.rlu(0, n);
+  }
+  // Mixed precisions: FP32 working copy in `lowp`, low-precision shadows in ws.
   unsigned int *scan = (unsigned int *)(w + L.scan);
   float *scale = (float *)(w + L.scale);
   EBV_CU(cudaMemsetAsync(scan, 0, 4, s));         // max |a_ij|, i != j: starts at +0
@@ -239,16 +248,17 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   const int op = prec == EBV_MIXED_BF16 ? 0 : 1;
   k_make_scale<<<1, 1, 0, s>>>(op, scan, scan + 1, scale);
   EBV_TRY(launch_ok());
+  float *inv = (float *)(w + L.inv);
   if (op == 0) {
-    Factorizer<float, __nv_bfloat16> f{dense_view((float *)lowp, n), n, info, s,
-                                       Shadow<__nv_bfloat16>{(__nv_bfloat16 *)(w + L.lb), (__nv_bfloat16 *)(w + L.ut),
-                                                             L.ldsh, scale},
-                                       0, (DevStatus *)ws};
+    EBV_TRY((prepare_leaf_kernels<float, __nv_bfloat16>()));
+    Factorizer<float, __nv_bfloat16> f{
+        dense_view((float *)lowp, n), n, info, s,
+        Shadow<__nv_bfloat16>{(__nv_bfloat16 *)(w + L.lb), (__nv_bfloat16 *)(w + L.ut), L.ldsh, scale}, 0, dst, inv};
     return f.rlu(0, n);
   }
+  EBV_TRY((prepare_leaf_kernels<float, __half>()));
   Factorizer<float, __half> f{dense_view((float *)lowp, n), n, info, s,
-                              Shadow<__half>{(__half *)(w + L.lb), (__half *)(w + L.ut), L.ldsh, scale}, 1,
-                              (DevStatus *)ws};
+                              Shadow<__half>{(__half *)(w + L.lb), (__half *)(w + L.ut), L.ldsh, scale}, 1, dst, inv};
   return f.rlu(0, n);
 }
 

@@ -61,8 +61,53 @@ struct Shadow {
 // pivot row, the pivot column and the FP64 pivot reciprocal through shared
 // memory (double-buffered: one barrier per step).
 // ---------------------------------------------------------------------------
+// Inverses of the unit-lower and the upper factor of a packed NB x NB block
+// F (shared memory), written to inv[0 .. NB*NB) (L^{-1}) and
+// inv[NB*NB .. 2*NB*NB) (U^{-1}), row-major.  Row sweeps with four threads per
+// column splitting each dot product; the diagonal of U^{-1} is the FP64
+// reciprocal of the pivot.
 template <typename T, int NB, int NT>
-__global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info) {
+__device__ void block_inverses(T (*Fs)[NB + 1], T (*Iv)[NB + 1], T *inv) {
+  static_assert(NT == 4 * NB, "four threads per column");
+  const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
+  // L^{-1}: X[i][c] = -(F[i][c] + sum_{c<k<i} F[i][k] X[k][c]) for c < i.
+  for (int e = threadIdx.x; e < NB * NB; e += NT) Iv[e / NB][e % NB] = (e / NB == e % NB) ? T(1) : T(0);
+  __syncthreads();
+  for (int i = 1; i < NB; ++i) {
+    T s = T(0);
+    if (c < i)
+      for (int k = c + 1 + part; k < i; k += 4) s += Fs[i][k] * Iv[k][c];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0 && c < i) Iv[i][c] = -(Fs[i][c] + s);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += NT) inv[e] = Iv[e / NB][e % NB];
+  __syncthreads();
+  // U^{-1}: X[i][i] = 1/u_ii; X[i][c] = -(sum_{i<k<=c} F[i][k] X[k][c]) / u_ii for c > i.
+  // The NB pivot reciprocals are FP64 divisions, one per thread, done once.
+  __shared__ T rcp_t[NB];
+  for (int e = threadIdx.x; e < NB * NB; e += NT) Iv[e / NB][e % NB] = T(0);
+  for (int i = threadIdx.x; i < NB; i += NT) rcp_t[i] = (T)(1.0 / (double)Fs[i][i]);
+  __syncthreads();
+  for (int i = NB - 1; i >= 0; --i) {
+    const T r = rcp_t[i];
+    T s = T(0);
+    if (c > i)
+      for (int k = i + 1 + part; k <= c; k += 4) s += Fs[i][k] * Iv[k][c];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0 && c >= i) Iv[i][c] = (c == i) ? r : -s * r;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += NT) inv[NB * NB + e] = Iv[e / NB][e % NB];
+}
+
+template <typename T, int NB>
+constexpr size_t pair_smem_bytes() { return 2 * sizeof(T) * NB * (NB + 1); }
+
+template <typename T, int NB, int NT>
+__global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
   constexpr int NP = NB / 2;
   constexpr int NG = NT / NP;
   constexpr int RPT = NB / NG;
@@ -71,7 +116,7 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
   const int cj0 = p, cj1 = NB - 1 - p;
   __shared__ T rowbuf[2][NB];
   __shared__ T colbuf[2][NB];
-  __shared__ double rcp[NB];
+  __shared__ T rcp[NB];  // FP64 pivot reciprocal (one division, by the pivot's owner), rounded to T
   __shared__ int bad;
   T v[RPT][2];
   if (threadIdx.x == 0) bad = NB;
@@ -96,7 +141,7 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
         if (j == r && i > r) colbuf[buf][i] = v[t][s];
         if (i == r && j == r) {
           const double pv = (double)v[t][s];
-          rcp[r] = 1.0 / pv;
+          rcp[r] = (T)(1.0 / pv);
           if (!(pv != 0.0) || !isfinite(pv)) atomicMin(&bad, r);
         }
       }
@@ -106,12 +151,12 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
   __syncthreads();
   for (int r = 0; r < w; ++r) {
     const int buf = r & 1;
-    const double rc = rcp[r];
+    const T rc = rcp[r];
 #pragma unroll
     for (int t = 0; t < RPT; ++t) {
       const int i = g + NG * t;
       if (i > r && i < w) {
-        const T l = (T)((double)colbuf[buf][i] * rc);  // Eq. 6a
+        const T l = colbuf[buf][i] * rc;  // Eq. 6a
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
           const int j = s ? cj1 : cj0;
@@ -132,85 +177,135 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     if (i < w && cj1 < w) A.put(k0 + i, k0 + cj1, v[t][1]);
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
+  if (!inv) return;
+  // Inverses of the two triangular factors, so that L21 = A21 U11^{-1} and
+  // U12 = L11^{-1} A12 become independent tile products.  The block is padded
+  // with the identity beyond w.  Dynamic shared memory: T F[NB][NB+1], T I[NB][NB+1].
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*Iv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  for (int e = threadIdx.x; e < NB * NB; e += NT) Fs[e / NB][e % NB] = (e / NB == e % NB) ? T(1) : T(0);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < RPT; ++t) {
+    const int i = g + NG * t;
+    if (i < w && cj0 < w) Fs[i][cj0] = v[t][0];
+    if (i < w && cj1 < w) Fs[i][cj1] = v[t][1];
+  }
+  block_inverses<T, NB, NT>(Fs, Iv, inv);
 }
 
 // ---------------------------------------------------------------------------
-// L21 = A21 U11^{-1}: the L vectors of the block's columns for all rows below
-// it (Eq. 6a applied to rows r_begin..r_end-1).  Without pivoting every row is
-// independent, so one thread owns one row (its w entries in registers) and U11
-// is broadcast from shared memory.  Optionally writes the scaled low-precision
-// shadow of L.
+// L21 = A21 U11^{-1}: the L vectors of the block's columns for the rows
+// r_begin..r_end-1 below it (Eq. 6a for every row at once).  Without pivoting
+// the rows are independent; with U11^{-1} from the diagonal-block kernel each
+// 64 x w tile is one small product, computed from shared memory and written
+// back coalesced (plus the scaled low-precision shadow of L).
+// Dynamic shared memory: pair_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, typename SH, int NB>
-__global__ void __launch_bounds__(128) k_trsm_ru(MatView<T> A, int64_t k0, int w, int64_t r_begin, int64_t r_end,
-                                                 Shadow<SH> sh) {
-  __shared__ T U[NB][NB + 1];
-  __shared__ double rc[NB];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, j = e % NB;
-    U[i][j] = (i < w && j < w && j >= i) ? A.get(k0 + i, k0 + j) : T(0);
+__global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w, int64_t r_begin, int64_t r_end,
+                                                 const T *inv, Shadow<SH> sh) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T(*At)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*Ui)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  const int64_t r0 = r_begin + (int64_t)blockIdx.x * NB;
+  const int h = (int)min64(NB, r_end - r0);
+  const T *uinv = inv + NB * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int i = e / NB, k = e % NB;
+    Ui[i][k] = uinv[e];
+    At[i][k] = (i < h && k < w) ? A.get(r0 + i, k0 + k) : T(0);
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < NB; j += blockDim.x) rc[j] = j < w ? 1.0 / (double)U[j][j] : 0.0;
-  __syncthreads();
-  const int64_t i = r_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= r_end) return;
-  T v[NB];
+  const int i = threadIdx.x >> 2, jq = threadIdx.x & 3;
+  T out[NB / 4];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) v[j] = (j < w) ? A.get(i, k0 + j) : T(0);
+  for (int q = 0; q < NB / 4; ++q) out[q] = T(0);
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    const T a = At[i][k];
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    v[j] = (T)((double)v[j] * rc[j]);
-#pragma unroll
-    for (int jj = j + 1; jj < NB; ++jj) v[jj] -= v[j] * U[j][jj];
+    for (int q = 0; q < NB / 4; ++q) out[q] += a * Ui[k][jq + 4 * q];
   }
+  __syncthreads();
 #pragma unroll
-  for (int j = 0; j < NB; ++j)
-    if (j < w) A.put(i, k0 + j, v[j]);
-  if (sh.lb) {
-    const float s = sh.scale[0];
-    SH *dst = sh.lb + i * sh.ld + k0;
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-      if (j < w) dst[j] = from_float<SH>((float)v[j] * s);
+  for (int q = 0; q < NB / 4; ++q) At[i][jq + 4 * q] = out[q];
+  __syncthreads();
+  const float s = sh.lb ? sh.scale[0] : 1.f;
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int ii = e / NB, k = e % NB;
+    if (ii < h && k < w) {
+      A.put(r0 + ii, k0 + k, At[ii][k]);
+      if (sh.lb) sh.lb[(r0 + ii) * sh.ld + k0 + k] = from_float<SH>((float)At[ii][k] * s);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// U12 = L11^{-1} A12: the U vectors of the block's rows for the columns
-// c_begin..c_end-1 (unit lower forward substitution).  One thread owns one
-// column; L11 is broadcast from shared memory.  Optionally writes the scaled
-// low-precision shadow of U^T.
+// U12 = L11^{-1} A12: the U vectors of the block's h rows for the columns
+// c_begin..c_end-1 (Eq. 6b for every column at once), one h x 64 tile per CTA
+// from L11^{-1}.  Also writes the scaled low-precision shadow of U^T.
+// Dynamic shared memory: pair_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, typename SH, int NB>
-__global__ void __launch_bounds__(128) k_trsm_ll(MatView<T> A, int64_t r0, int h, int64_t c_begin, int64_t c_end,
-                                                 Shadow<SH> sh) {
-  __shared__ T L[NB][NB + 1];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, j = e % NB;
-    L[i][j] = (i < h && j < i) ? A.get(r0 + i, r0 + j) : T(0);
+__global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h, int64_t c_begin, int64_t c_end,
+                                                 const T *inv, Shadow<SH> sh) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T(*At)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*Li)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
+  const int wc = (int)min64(NB, c_end - c0);
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int k = e / NB, j = e % NB;
+    Li[k][j] = inv[e];
+    At[k][j] = (k < h && j < wc) ? A.get(r0 + k, c0 + j) : T(0);
   }
   __syncthreads();
-  const int64_t j = c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= c_end) return;
-  T v[NB];
+  const int i = threadIdx.x >> 2, jq = threadIdx.x & 3;
+  T out[NB / 4];
 #pragma unroll
-  for (int i = 0; i < NB; ++i) v[i] = (i < h) ? A.get(r0 + i, j) : T(0);
+  for (int q = 0; q < NB / 4; ++q) out[q] = T(0);
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    const T l = Li[i][k];
 #pragma unroll
-  for (int i = 0; i < NB; ++i) {
-#pragma unroll
-    for (int ii = i + 1; ii < NB; ++ii) v[ii] -= L[ii][i] * v[i];
+    for (int q = 0; q < NB / 4; ++q) out[q] += l * At[k][jq + 4 * q];
   }
+  __syncthreads();
 #pragma unroll
-  for (int i = 0; i < NB; ++i)
-    if (i < h) A.put(r0 + i, j, v[i]);
+  for (int q = 0; q < NB / 4; ++q) At[i][jq + 4 * q] = out[q];
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int k = e / NB, j = e % NB;
+    if (k < h && j < wc) A.put(r0 + k, c0 + j, At[k][j]);
+  }
   if (sh.ut) {
     const float s = sh.scale[1];
-    SH *dst = sh.ut + j * sh.ld + r0;
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i < h) dst[i] = from_float<SH>((float)v[i] * s);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int j = e / NB, k = e % NB;
+      if (k < h && j < wc) sh.ut[(c0 + j) * sh.ld + r0 + k] = from_float<SH>((float)At[k][j] * s);
+    }
   }
+}
+
+// Opt the leaf kernels into more than 48 KB of dynamic shared memory (FP64
+// tiles need 66.5 KB); once per process and instantiation.
+template <typename T, typename SH>
+ebv_status_t prepare_leaf_kernels() {
+  static const cudaError_t err = [] {
+    const int bytes = (int)pair_smem_bytes<T, kNB>();
+    cudaError_t e = cudaFuncSetAttribute(k_diag_factor<T, kNB, 4 * kNB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsm_ru<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsm_ll<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+  }();
+  return err == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,29 +9,6 @@
 namespace ebv {
 namespace {
 
-struct DenseSolveLayout {
-  size_t bsave, r, corr, xhi, xlo, flags, ticket, rmax, bmax, total;
-};
-
-DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize) {
-  DenseSolveLayout L{};
-  size_t off = kStatusBytes;
-  const size_t nn = (size_t)n * (size_t)std::max<int64_t>(nrhs, 1);
-  const size_t nblk = (size_t)std::max<int64_t>(1, (n + kNB - 1) / kNB);
-  const size_t nchunk = (size_t)std::max<int64_t>(1, (nrhs + 7) / 8);
-  L.bsave = off; off = align256(off + nn * 8);
-  L.r = off; off = align256(off + nn * 8);
-  L.corr = off; off = align256(off + nn * tsize);
-  L.xhi = off; off = align256(off + nn * 4);
-  L.xlo = off; off = align256(off + nn * 4);
-  L.flags = off; off = align256(off + 2 * nblk * nchunk * 4);
-  L.ticket = off; off = align256(off + 2 * 4);
-  L.rmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
-  L.bmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
-  L.total = off;
-  return L;
-}
-
 template <typename T>
 struct TrsvCfg;
 template <>
@@ -43,48 +20,108 @@ struct TrsvCfg<float> {
   static constexpr int RC = 32;
 };
 
-// Forward then backward block substitution of B (n x nrhs, T) in place.
-template <typename T>
-ebv_status_t trsv_pair(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, int *flags, int *ticket, DevStatus *st,
-                       cudaStream_t s) {
-  constexpr int RC = TrsvCfg<T>::RC;
-  const int nblk = ceil_div(n, kNB), nchunk = ceil_div(nrhs, RC);
-  const size_t smem = trsv_smem_bytes<T, kNB, RC>();
-  EBV_CU(cudaMemsetAsync(flags, 0, sizeof(int) * 2 * (size_t)nblk * nchunk, s));
-  EBV_CU(cudaMemsetAsync(ticket, 0, sizeof(int) * 2, s));
-  const double work = (double)n * n * nrhs;  // nominal n^2 flops per right-hand side and triangle
-  {
-    prof::Scope ps(s, prof::kTrsv, work);
-    k_trsv<T, kNB, RC, false><<<nblk * nchunk, 256, smem, s>>>(F, n, B, ldb, nrhs, flags, ticket, st);
-    EBV_TRY(launch_ok());
-  }
-  prof::Scope ps(s, prof::kTrsv, work);
-  k_trsv<T, kNB, RC, true><<<nblk * nchunk, 256, smem, s>>>(F, n, B, ldb, nrhs, flags + (size_t)nblk * nchunk,
-                                                            ticket + 1, st);
-  return launch_ok();
+struct DenseSolveLayout {
+  size_t dinv, flags, bsave, r, corr, xhi, xlo, rmax, bmax, total;
+};
+
+// Solve workspace: status block, inverses of the diagonal blocks of both
+// factors, per-step flags of the two substitutions, refinement buffers.
+DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize) {
+  DenseSolveLayout L{};
+  size_t off = kStatusBytes;
+  const size_t nn = (size_t)n * (size_t)std::max<int64_t>(nrhs, 1);
+  const size_t nblk = (size_t)std::max<int64_t>(1, (n + kNB - 1) / kNB);
+  const size_t nchunk = (size_t)std::max<int64_t>(1, (nrhs + 7) / 8);  // RC >= 8 for every type
+  L.dinv = off; off = align256(off + nblk * 2 * kNB * kNB * tsize);
+  L.flags = off; off = align256(off + 2 * nchunk * nblk * sizeof(int));
+  L.bsave = off; off = align256(off + nn * 8);
+  L.r = off; off = align256(off + nn * 8);
+  L.corr = off; off = align256(off + nn * tsize);
+  L.xhi = off; off = align256(off + nn * 4);
+  L.xlo = off; off = align256(off + nn * 4);
+  L.rmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
+  L.bmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
+  L.total = off;
+  return L;
 }
 
 inline int grid_for(int64_t elems) { return (int)std::min<int64_t>(4096, std::max<int64_t>(1, (elems + 255) / 256)); }
 
+// Inverses of the diagonal blocks of the factors (once per solve call).
+template <typename T>
+ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_diag_inverses<T, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes<T, kNB>());
+  if (attr != cudaSuccess) return EBV_ERR_CUDA;
+  prof::Scope ps(s, prof::kTrsv, 2.0 * ceil_div(n, kNB) * kNB * kNB * kNB / 3.0);
+  k_diag_inverses<T, kNB><<<ceil_div(n, kNB), 4 * kNB, pair_smem_bytes<T, kNB>(), s>>>(F, n, dinv);
+  return launch_ok();
+}
+
+// One triangle of the substitution as a cooperative persistent launch: at
+// most as many CTAs per right-hand-side chunk as can be resident at once
+// (the CTAs wait on one another's flags).
+template <typename T, bool UPPER>
+ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
+                      DevStatus *st, cudaStream_t s) {
+  constexpr int RC = TrsvCfg<T>::RC;
+  constexpr size_t smem = trsvp_smem_bytes<T, kNB, RC>();
+  auto kern = k_trsv_persistent<T, kNB, RC, UPPER>;
+  static int resident = [&] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    return sms * per_sm;
+  }();
+  const int nblk = ceil_div(n, kNB), nchunk = ceil_div(nrhs, RC);
+  if (resident < nchunk) return EBV_ERR_UNSUPPORTED;
+  const int G = std::max(1, std::min(resident / nchunk, nblk));
+  EBV_CU(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)nchunk * nblk, s));
+  prof::Scope ps(s, prof::kTrsv, (double)n * n * nrhs);  // nominal n^2 flops per right-hand side
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(G * nchunk));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  EBV_CU(cudaLaunchKernelEx(&cfg, kern, F, n, B, ldb, nrhs, dinv, flags, st));
+  return launch_ok();
+}
+
+// Forward then backward block substitution of B (n x nrhs, T) in place.
+template <typename T>
+ebv_status_t trsv_pair(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
+                       DevStatus *st, cudaStream_t s) {
+  const int nblk = ceil_div(n, kNB), nchunk = ceil_div(nrhs, TrsvCfg<T>::RC);
+  EBV_TRY((trsv_one<T, false>(F, n, B, ldb, nrhs, dinv, flags, st, s)));
+  return trsv_one<T, true>(F, n, B, ldb, nrhs, dinv, flags + (size_t)nchunk * nblk, st, s);
+}
 
 // ---------------------------------------------------------------------------
 // Solve with optional refinement.  Shared by the dense and banded paths
 // through the factor view F and the residual callback.
 // ---------------------------------------------------------------------------
 template <typename T, typename ResidualFn>
-ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64_t ldb,
-                                  const ebv_refine_t *refine, ebv_refine_report_t *rep, char *w,
-                                  const DenseSolveLayout &L, bool b_is_double, ResidualFn residual, cudaStream_t s) {
+ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64_t ldb, const ebv_refine_t *refine,
+                           ebv_refine_report_t *rep, char *w, const DenseSolveLayout &L, bool b_is_double,
+                           ResidualFn residual, cudaStream_t s) {
   DevStatus *st = (DevStatus *)w;
-  int *flags = (int *)(w + L.flags);
-  int *ticket = (int *)(w + L.ticket);
   const int nr = (int)nrhs;
+  T *dinv = (T *)(w + L.dinv);
+  int *flags = (int *)(w + L.flags);
+  EBV_TRY(diag_inverses<T>(F, n, dinv, s));
   if (!refine) {
-    if (b_is_double == (sizeof(T) == 8)) return trsv_pair<T>(F, n, (T *)b, ldb, nr, flags, ticket, st, s);
+    if (b_is_double == (sizeof(T) == 8)) return trsv_pair<T>(F, n, (T *)b, ldb, nr, dinv, flags, st, s);
     // FP32 factors applied to FP64 right-hand sides (mixed precisions, no refinement).
     T *c = (T *)(w + L.corr);
     k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>((const double *)b, ldb, c, nrhs, n, nr, st);
-    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, flags, ticket, st, s));
+    EBV_TRY(launch_ok());
+    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, flags, st, s));
     k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>((double *)b, ldb, c, nrhs, n, nr, 0, st);
     return launch_ok();
   }
@@ -102,7 +139,7 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
   // x0 from the factors.
   k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>(bsave, nrhs, c, nrhs, n, nr, st);
   EBV_TRY(launch_ok());
-  EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, flags, ticket, st, s));
+  EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, flags, st, s));
   k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, c, nrhs, n, nr, 0, st);
   EBV_TRY(launch_ok());
   const int max_iter = std::max(0, refine->max_iter);
@@ -116,7 +153,7 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
     if (it == max_iter) break;
     k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>(r, nrhs, c, nrhs, n, nr, st);
     EBV_TRY(launch_ok());
-    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, flags, ticket, st, s));
+    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, flags, st, s));
     k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, c, nrhs, n, nr, 1, st);
     EBV_TRY(launch_ok());
   }

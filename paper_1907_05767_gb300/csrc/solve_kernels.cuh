@@ -8,142 +8,152 @@ namespace ebv {
 namespace {  // internal linkage: every translation unit gets its own kernels
 
 // ---------------------------------------------------------------------------
-// Block triangular solve in one launch.  CTA "ticket" t (taken in start order,
-// so a CTA only ever waits on CTAs that already run) owns block row b of one
-// chunk of right-hand-side columns.  It folds in the finished blocks that row
-// b depends on as their flags appear (bounded waits), solves its diagonal
-// block from shared memory, writes its rows and releases its flag.
-//   UPPER = false: unit lower L,   forward,  blocks in increasing order.
-//   UPPER = true:  upper U,        backward, blocks in decreasing order; the
-//                  diagonal is applied through FP64 reciprocals.
-// Dynamic shared memory: T acc[NB][RC+1], T yb[NB][RC+1], T F[NB][NB+1],
-// double rcp[NB].
+// Inverses of the diagonal blocks of the packed factors (block b: L_bb^{-1}
+// then U_bb^{-1} at dinv + b * 2 * NB * NB), one CTA per block, so that each
+// diagonal solve of the substitution is a tile product.
+// Dynamic shared memory: pair_smem_bytes<T, NB>().
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t n, T *dinv) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*Iv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  const int64_t i0 = (int64_t)blockIdx.x * NB;
+  const int hb = (int)min64(NB, n - i0);
+  for (int e = threadIdx.x; e < NB * NB; e += 4 * NB) {
+    const int r = e / NB, k = e % NB;
+    Fs[r][k] = (r < hb && k < hb) ? F.get(i0 + r, i0 + k) : (r == k ? T(1) : T(0));
+  }
+  __syncthreads();
+  block_inverses<T, NB, 4 * NB>(Fs, Iv, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
+}
+
+// ---------------------------------------------------------------------------
+// Block substitution in one cooperative launch per triangle (Eq. 1: LY = B,
+// then UX = Y).  Steps s = 0..nblk-1 visit the row blocks in solve order
+// (increasing for L, decreasing for U).  CTA h of a right-hand-side chunk
+// owns the steps s = h (mod G) and keeps those blocks of B up to date in
+// global memory: when the block of step s is published, the owner of step
+// s+1 first folds it into its own block, solves that block through the
+// diagonal-block inverse (a 64 x 64 tile product, no sequential chain) and
+// publishes it; only then does every CTA fold step s into the other blocks it
+// owns.  Flags are per step; every wait is bounded and gives up once the
+// workspace status reports an error.  All CTAs must be co-resident: the
+// driver launches at most the occupancy limit, cooperatively.
+// Dynamic shared memory: trsvp_smem_bytes<T, NB, RC>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB, int RC>
-constexpr size_t trsv_smem_bytes() {
-  return sizeof(T) * (2 * NB * (RC + 1) + NB * (NB + 1)) + sizeof(double) * NB;
+constexpr size_t trsvp_smem_bytes() {
+  return sizeof(T) * (2 * NB * (RC + 1) + NB * (NB + 1));
 }
 
 template <typename T, int NB, int RC, bool UPPER>
 __global__ void __launch_bounds__(256)
-    k_trsv(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, int *flags, int *ticket, DevStatus *st) {
+    k_trsv_persistent(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
+                      DevStatus *st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*acc)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw);
-  T(*yb)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
+  T(*Y)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw);
+  T(*acc)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
   T(*Fb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * 2 * NB * (RC + 1));
-  double *rcp = reinterpret_cast<double *>(smem_raw + sizeof(T) * (2 * NB * (RC + 1) + NB * (NB + 1)));
-  __shared__ int s_t, s_ok;
+  __shared__ int s_ok;
   if (st && st->done) return;  // refinement already converged
   const int nblk = ceil_div(n, NB);
   const int nchunk = ceil_div(nrhs, RC);
-  if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
-  __syncthreads();
-  const int t = s_t;
-  const int chunk = t % nchunk, step = t / nchunk;
-  const int b = UPPER ? nblk - 1 - step : step;
-  const int64_t i0 = (int64_t)b * NB;
-  const int hb = (int)min64(NB, n - i0);
-  const int c0 = chunk * RC;
-  const int wc = min(RC, nrhs - c0);
-  int *myflags = flags + (int64_t)chunk * nblk;
+  const int chunk = blockIdx.x % nchunk, h = blockIdx.x / nchunk;
+  const int G = gridDim.x / nchunk;
+  if (h >= G) return;
+  const int c0 = chunk * RC, wc = min(RC, nrhs - c0);
+  int *fl = flags + (int64_t)chunk * nblk;
+  auto blk = [&](int s) { return UPPER ? nblk - 1 - s : s; };
+  // Steps s+1 .. s+reach depend on the block of step s (a band limits reach);
+  // at least step s+1, whose diagonal block is solved right after its fold.
+  const int reach = (int)max64(1, min64((UPPER ? F.ku + NB - 1 : F.kl + NB - 1) / NB, (int64_t)nblk));
+  constexpr int PASS = 256 / RC;  // rows covered per pass of the thread block
+  const int tc = threadIdx.x % RC, tr = threadIdx.x / RC;
 
-  for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
-    const int i = e / RC, c = e % RC;
-    acc[i][c] = (i < hb && c < wc) ? B[(i0 + i) * ldb + c0 + c] : T(0);
+  // acc <- B_blk(t) - F(blk(t), blk(s)) * Y   (Y = published block of step s)
+  auto fold = [&](int s, int t) {
+    const int64_t i0 = (int64_t)blk(t) * NB, j0 = (int64_t)blk(s) * NB;
+    const int hi = (int)min64(NB, n - i0), hj = (int)min64(NB, n - j0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int r = e / NB, k = e % NB;
+      Fb[r][k] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
+    }
+    __syncthreads();
+    for (int r = tr; r < NB; r += PASS) {
+      T a = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
+#pragma unroll 16
+      for (int k = 0; k < NB; ++k) a -= Fb[r][k] * Y[k][tc];
+      acc[r][tc] = a;
+    }
+    __syncthreads();
+  };
+  auto store = [&](int t) {
+    const int64_t i0 = (int64_t)blk(t) * NB;
+    const int hi = (int)min64(NB, n - i0);
+    for (int r = tr; r < hi; r += PASS)
+      if (tc < wc) B[(i0 + r) * ldb + c0 + tc] = acc[r][tc];
+  };
+  // Solve the block of step t in place from acc: B_blk(t) = D^{-1} acc, then release flag t.
+  auto solve_publish = [&](int t) {
+    const T *di = dinv + (int64_t)blk(t) * 2 * NB * NB + (UPPER ? NB * NB : 0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Fb[e / NB][e % NB] = di[e];
+    __syncthreads();
+    const int64_t i0 = (int64_t)blk(t) * NB;
+    const int hi = (int)min64(NB, n - i0);
+    for (int r = tr; r < hi; r += PASS) {
+      T a = T(0);
+#pragma unroll 16
+      for (int k = 0; k < NB; ++k) a += Fb[r][k] * acc[k][tc];
+      if (tc < wc) B[(i0 + r) * ldb + c0 + tc] = a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(&fl[t], 1);
+  };
+
+  if (h == 0) {  // step 0: its block has no updates to receive
+    const int64_t i0 = (int64_t)blk(0) * NB;
+    const int hi = (int)min64(NB, n - i0);
+    for (int r = tr; r < NB; r += PASS) acc[r][tc] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
+    __syncthreads();
+    solve_publish(0);
   }
-  // Range of blocks row block b depends on (band limits included).
-  int jlo, jhi;
-  if (!UPPER) {
-    const int64_t cmin = i0 - F.kl;
-    jlo = cmin <= 0 ? 0 : (int)(cmin / NB);
-    jhi = b - 1;
-  } else {
-    const int64_t cmax = i0 + hb - 1 + F.ku;
-    jlo = b + 1;
-    jhi = (int)min64(nblk - 1, cmax / NB);
-  }
-  for (int q = 0; q <= jhi - jlo; ++q) {
-    const int j = UPPER ? jhi - q : jlo + q;  // the earliest-finished block first
-    const int64_t j0 = (int64_t)j * NB;
-    const int hj = (int)min64(NB, n - j0);
+  for (int s = 0; s + 1 < nblk; ++s) {
+    const int last = (int)min64(nblk - 1, (int64_t)s + reach);
+    // first step > s owned by this CTA
+    int t = s + 1 + (((h - (s + 1)) % G) + G) % G;
+    if (t > last) continue;  // nothing of ours depends on step s
     if (threadIdx.x == 0) {
       bool ok = false;
       for (long long it = 0; it < kSpinLimit; ++it) {
-        if (ld_acquire(&myflags[j]) >= 1) { ok = true; break; }
+        if (ld_acquire(&fl[s]) >= 1) {
+          ok = true;
+          break;
+        }
         if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) break;
-        __nanosleep(100);
+        __nanosleep(64);
       }
       s_ok = ok;
-      if (!ok) set_status(st, EBV_ERR_TIMEOUT, b);
+      if (!ok) set_status(st, EBV_ERR_TIMEOUT, s);
     }
     __syncthreads();
     if (!s_ok) return;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      const int i = e / NB, k = e % NB;
-      Fb[i][k] = (i < hb && k < hj) ? F.get(i0 + i, j0 + k) : T(0);
-    }
-    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
-      const int k = e / RC, c = e % RC;
-      yb[k][c] = (k < hj && c < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + c]) : T(0);
+    {
+      const int64_t j0 = (int64_t)blk(s) * NB;
+      const int hj = (int)min64(NB, n - j0);
+      for (int k = tr; k < NB; k += PASS) Y[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
-      const int i = e / RC, c = e % RC;
-      T s = acc[i][c];
-#pragma unroll 16
-      for (int k = 0; k < NB; ++k) s -= Fb[i][k] * yb[k][c];
-      acc[i][c] = s;
-    }
-    __syncthreads();
-  }
-  // Diagonal block.
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, k = e % NB;
-    T v = T(0);
-    if (i < hb && k < hb) {
-      if (!UPPER && k < i) v = F.get(i0 + i, i0 + k);
-      if (UPPER && k >= i) v = F.get(i0 + i, i0 + k);
-    }
-    Fb[i][k] = v;
-  }
-  __syncthreads();
-  if (UPPER) {
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) rcp[i] = i < hb ? 1.0 / (double)Fb[i][i] : 0.0;
-    __syncthreads();
-    // Fold the reciprocal of pivot k into column k: row i then subtracts
-    // (u_ik / u_kk) * (unscaled final value of row k).
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-      const int i = e / NB, k = e % NB;
-      if (k > i) Fb[i][k] = (T)((double)Fb[i][k] * rcp[k]);
-    }
-    __syncthreads();
-    for (int r = hb - 1; r > 0; --r) {
-      for (int e = threadIdx.x; e < r * RC; e += blockDim.x) {
-        const int i = e / RC, c = e % RC;
-        acc[i][c] -= Fb[i][r] * acc[r][c];
-      }
+    for (; t <= last; t += G) {
+      fold(s, t);
+      if (t == s + 1)
+        solve_publish(t);  // every earlier step has already been folded into it
+      else
+        store(t);
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
-      const int i = e / RC, c = e % RC;
-      if (i < hb && c < wc) B[(i0 + i) * ldb + c0 + c] = (T)((double)acc[i][c] * rcp[i]);
-    }
-  } else {
-    for (int r = 0; r < hb - 1; ++r) {
-      for (int e = threadIdx.x; e < (hb - 1 - r) * RC; e += blockDim.x) {
-        const int i = r + 1 + e / RC, c = e % RC;
-        acc[i][c] -= Fb[i][r] * acc[r][c];
-      }
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < NB * RC; e += blockDim.x) {
-      const int i = e / RC, c = e % RC;
-      if (i < hb && c < wc) B[(i0 + i) * ldb + c0 + c] = acc[i][c];
-    }
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) st_release(&myflags[b], 1);
 }
 
 // ---------------------------------------------------------------------------
