@@ -160,16 +160,19 @@ EBV_API ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const vo
 /*
  * Batched factor + solve of many independent dense systems of uneven order
  * (project addition; the paper factors one matrix).  Systems are grouped into
- * long/short pairs (the pairing idea of Eq. 7 applied across systems) and run
- * by one persistent kernel launch.
+ * long/short pairs (the pairing idea of Eq. 7 applied across systems: a cheap
+ * system joins an expensive one while the pair costs no more than the most
+ * expensive system) and run by one persistent kernel launch.
  *
- * ebv_batch_schedule_len(batch): int32 entries of a schedule.
+ * ebv_batch_schedule_len(batch): int32 entries of a schedule (2*batch + 8).
  * ebv_batch_schedule (host): builds the schedule for the given orders and
- *   right-hand-side counts (host arrays) into `schedule_host`.  `variant_of_n`
- *   (host, nullable) maps each order 1..512 to a kernel variant id
- *   (0 = blocked nb 16, 1 = nb 32, 2 = nb 64), e.g. from ebv_batch_autotune;
- *   NULL uses the built-in default.  The caller copies the schedule to device
- *   memory once and may reuse it for every call with the same sizes.
+ *   right-hand-side counts (host arrays) into `schedule_host`; EBV_ERR_ARG for
+ *   an order outside 0..4096 or a count outside 0..64.  `variant_of_n`
+ *   (host, nullable, 4096 entries) maps each order 1..4096 to a kernel
+ *   variant id (0 = blocks of 16 columns, 1 = blocks of 32), e.g. from
+ *   ebv_batch_autotune; NULL uses the built-in default (16 up to order 64).
+ *   The caller copies the schedule to device memory once and may reuse it for
+ *   every call with the same sizes.
  * ebv_factor_solve_batched: system s has order n_dev[s] (1..4096) and
  *   nrhs_dev[s] right-hand sides (0..64); a_ptrs_dev[s] points to its n x n
  *   matrix (leading dimension n), overwritten by its packed factors;
@@ -210,6 +213,8 @@ EBV_API ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, in
  *   x, grad_x device, system s at + s*n*nrhs (n x nrhs, leading dim. nrhs).
  *   grad_b    device output, same layout as x.
  *   grad_a    device output or NULL, system s at + s*n*n (leading dim. n).
+ * Limits: batch <= 65535, nrhs <= 16, and with grad_a one system's X (n*nrhs
+ * doubles) must fit in 200 KB of shared memory (EBV_ERR_UNSUPPORTED otherwise).
  */
 EBV_API ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs, const double *lu, int64_t lda,
                                int64_t stride_lu, const double *x, const double *grad_x, double *grad_b,

@@ -291,6 +291,181 @@ def debug_residual(a: torch.Tensor, x: torch.Tensor, b: torch.Tensor) -> torch.T
     return r
 
 
+BATCH_VARIANTS = {0: "nb16", 1: "nb32"}
+MAX_BATCH_ORDER = 4096
+
+
+def ebv_batch_schedule(n_list, nrhs_list, variant_of_n=None):
+    """Host schedule (int32 numpy array) for ebv_factor_solve_batched."""
+    import numpy as np
+    n_arr = np.ascontiguousarray(n_list, dtype=np.int32)
+    r_arr = np.ascontiguousarray(nrhs_list, dtype=np.int32)
+    batch = n_arr.size
+    sched = np.zeros(int(lib().ebv_batch_schedule_len(batch)), dtype=np.int32)
+    vmap = None
+    if variant_of_n is not None:
+        vmap = np.ascontiguousarray(variant_of_n, dtype=np.int8)
+        assert vmap.size >= MAX_BATCH_ORDER
+    _check(lib().ebv_batch_schedule(batch, n_arr.ctypes.data, r_arr.ctypes.data,
+                                    vmap.ctypes.data if vmap is not None else None, sched.ctypes.data),
+           "ebv_batch_schedule")
+    return sched
+
+
+class Batch:
+    """Many independent dense systems in one device buffer each for A and B.
+
+    System s: A_s (n_s x n_s, row-major) at a_buf[a_off[s]:], B_s (n_s x
+    nrhs_s) at b_buf[b_off[s]:].  ``run()`` factors every A_s in place and
+    overwrites every B_s with X_s in one persistent launch.
+    """
+
+    def __init__(self, n_list, nrhs_list, prec="fp64", device="cuda", variant_of_n=None):
+        import numpy as np
+        self.prec = _prec(prec)
+        if self.prec not in (FP64, FP32):
+            raise ValueError("batched path supports fp64 and fp32")
+        self.dtype = torch.float64 if self.prec == FP64 else torch.float32
+        self.n = np.asarray(n_list, dtype=np.int64)
+        self.nrhs = np.asarray(nrhs_list, dtype=np.int64)
+        self.batch = int(self.n.size)
+        esz = 8 if self.prec == FP64 else 4
+        align = 16 // esz  # every system starts on a 16-byte boundary
+        a_sz = ((self.n * self.n + align - 1) // align) * align
+        b_sz = ((self.n * self.nrhs + align - 1) // align) * align
+        self.a_off = np.concatenate([[0], np.cumsum(a_sz)[:-1]]).astype(np.int64)
+        self.b_off = np.concatenate([[0], np.cumsum(b_sz)[:-1]]).astype(np.int64)
+        self.a_buf = torch.zeros(int(a_sz.sum()), dtype=self.dtype, device=device)
+        self.b_buf = torch.zeros(max(1, int(b_sz.sum())), dtype=self.dtype, device=device)
+        a_ptrs = self.a_buf.data_ptr() + self.a_off * esz
+        b_ptrs = self.b_buf.data_ptr() + self.b_off * esz
+        self.ptrs = torch.from_numpy(np.concatenate([a_ptrs, b_ptrs]).astype(np.int64)).to(device)
+        self.dims = torch.from_numpy(np.concatenate([self.n, self.nrhs]).astype(np.int32)).to(device)
+        self.sched = torch.from_numpy(ebv_batch_schedule(self.n, self.nrhs, variant_of_n)).to(device)
+        self.info = torch.zeros(max(1, self.batch), dtype=torch.int32, device=device)
+        self.ws = torch.zeros(int(lib().ebv_batch_workspace_size(self.batch)), dtype=torch.uint8, device=device)
+
+    def a_view(self, s):
+        o, n = int(self.a_off[s]), int(self.n[s])
+        return self.a_buf[o:o + n * n].view(n, n)
+
+    def b_view(self, s):
+        o, n, r = int(self.b_off[s]), int(self.n[s]), int(self.nrhs[s])
+        return self.b_buf[o:o + n * r].view(n, r)
+
+    def run(self):
+        b = self.batch
+        dp = self.ptrs.data_ptr()
+        dd = self.dims.data_ptr()
+        _check(lib().ebv_factor_solve_batched(b, ctypes.c_void_p(dd), ctypes.c_void_p(dd + 4 * b),
+                                              ctypes.c_void_p(dp), ctypes.c_void_p(dp + 8 * b), self.prec,
+                                              _ptr(self.sched), _ptr(self.info), _ptr(self.ws), self.ws.numel(),
+                                              _stream(self.a_buf.device)), "ebv_factor_solve_batched")
+
+
+def batch_autotune(orders, prec="fp64", reps=16, device="cuda", cache_path=None):
+    """Fastest batched variant per order (times each variant on `reps`
+    synthetic systems of that order).  Returns (variant_of_n array for every
+    order 1..4096 filled by nearest tuned order, {order: [ms per variant]}).
+    With cache_path, results are read from / written to that JSON file."""
+    import json
+    import numpy as np
+    p = _prec(prec)
+    key = f"{torch.cuda.get_device_name(device)}|{p}|{reps}"
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+    entry = cache.get(key, {})
+    todo = [int(o) for o in orders if str(int(o)) not in entry]
+    if todo:
+        arr = np.asarray(todo, dtype=np.int32)
+        best = np.zeros(arr.size, dtype=np.int8)
+        ms = np.zeros(arr.size * len(BATCH_VARIANTS), dtype=np.float32)
+        scratch = torch.empty(int(lib().ebv_batch_autotune_scratch(int(arr.max()), reps, p)), dtype=torch.uint8,
+                              device=device)
+        _check(lib().ebv_batch_autotune(arr.ctypes.data, arr.size, reps, p, _ptr(scratch), scratch.numel(),
+                                        best.ctypes.data, ms.ctypes.data, _stream(scratch.device)),
+               "ebv_batch_autotune")
+        for i, o in enumerate(todo):
+            entry[str(o)] = {"best": int(best[i]), "ms": [float(v) for v in ms[i * 2:(i + 1) * 2]]}
+        cache[key] = entry
+        if cache_path:
+            with open(cache_path, "w") as fh:
+                json.dump(cache, fh, indent=1, sort_keys=True)
+    tuned = sorted((int(k), v["best"]) for k, v in entry.items())
+    vmap = np.zeros(MAX_BATCH_ORDER, dtype=np.int8)
+    keys = np.array([k for k, _ in tuned])
+    vals = np.array([v for _, v in tuned], dtype=np.int8)
+    for n in range(1, MAX_BATCH_ORDER + 1):
+        vmap[n - 1] = vals[np.abs(keys - n).argmin()]
+    return vmap, {k: entry[str(k)]["ms"] for k, _ in tuned}
+
+
+def uniform_batch(a: torch.Tensor, b: torch.Tensor, variant_of_n=None) -> "Batch":
+    """A Batch over existing contiguous (batch, n, n) / (batch, n, nrhs) FP64 or
+    FP32 tensors, factored and solved in place by ``run()``."""
+    import numpy as np
+    bsz, n, _ = a.shape
+    nrhs = b.shape[2]
+    self = Batch.__new__(Batch)
+    self.prec = FP64 if a.dtype == torch.float64 else FP32
+    self.dtype = a.dtype
+    self.n = np.full(bsz, n, dtype=np.int64)
+    self.nrhs = np.full(bsz, nrhs, dtype=np.int64)
+    self.batch = bsz
+    self.a_buf = a.view(-1)
+    self.b_buf = b.view(-1)
+    self.a_off = np.arange(bsz, dtype=np.int64) * n * n
+    self.b_off = np.arange(bsz, dtype=np.int64) * n * nrhs
+    esz = a.element_size()
+    ptrs = np.concatenate([a.data_ptr() + self.a_off * esz, b.data_ptr() + self.b_off * esz]).astype(np.int64)
+    self.ptrs = torch.from_numpy(ptrs).to(a.device)
+    self.dims = torch.from_numpy(np.concatenate([self.n, self.nrhs]).astype(np.int32)).to(a.device)
+    self.sched = torch.from_numpy(ebv_batch_schedule(self.n, self.nrhs, variant_of_n)).to(a.device)
+    self.info = torch.zeros(bsz, dtype=torch.int32, device=a.device)
+    self.ws = torch.zeros(int(lib().ebv_batch_workspace_size(bsz)), dtype=torch.uint8, device=a.device)
+    return self
+
+
+def ebv_solve_adjoint(lu: torch.Tensor, x: torch.Tensor, grad_x: torch.Tensor, want_grad_a: bool = True):
+    """(grad_B, grad_A) for a batch of FP64 systems from their packed factors
+    lu (batch, n, n), solutions x and dLoss/dX grad_x (batch, n, nrhs):
+    grad_B = A^{-T} grad_X, grad_A = -grad_B X^T."""
+    bsz, n, _ = lu.shape
+    nrhs = x.shape[2]
+    lu = lu.contiguous()
+    x = x.contiguous()
+    g = grad_x.contiguous().to(torch.float64)
+    gb = torch.empty_like(g)
+    ga = torch.empty((bsz, n, n), dtype=torch.float64, device=lu.device) if want_grad_a else None
+    _check(lib().ebv_solve_adjoint(bsz, n, nrhs, _ptr(lu), n, n * n, _ptr(x), _ptr(g), _ptr(gb), _ptr(ga),
+                                   _stream(lu.device)), "ebv_solve_adjoint")
+    return gb, ga
+
+
+class EbvSolve(torch.autograd.Function):
+    """X = A^{-1} B for a batch of FP64 systems, A (batch, n, n), B (batch, n,
+    nrhs).  Forward: batched EbV factor + solve (one persistent launch); the
+    packed factors are kept.  Backward: the adjoint kernels reuse them."""
+
+    @staticmethod
+    def forward(ctx, a, b):
+        lu = a.detach().to(torch.float64).contiguous().clone()
+        x = b.detach().to(torch.float64).contiguous().clone()
+        bt = uniform_batch(lu, x)
+        bt.run()
+        ctx.save_for_backward(lu, x)
+        ctx.info = bt.info
+        return x.clone()
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        lu, x = ctx.saved_tensors
+        gb, ga = ebv_solve_adjoint(lu, x, grad_x, want_grad_a=ctx.needs_input_grad[0])
+        return ga, gb
+
+
 def tc_available() -> bool:
     return bool(lib().ebv_debug_tc_available())
 
