@@ -372,6 +372,47 @@ def roofline_for(name, ms, work, cnt, peaks, args):
 
 
 # ----------------------------------------------------------------------------
+# single-kernel mode: the mixed-precision trailing update alone
+# ----------------------------------------------------------------------------
+
+def run_update_only(args):
+    """Time C -= L21 U12 (bf16 operands, FP32 C) for one M x N x K update with
+    the tcgen05 kernel, as in the top level of the n = 2M factorisation."""
+    import torch
+
+    import paper_1907_05767_gb300 as ebv
+    m, n, k = (int(v) for v in args.update_only.split(","))
+    dev = torch.device("cuda")
+    g = torch.Generator(device="cpu").manual_seed(1)
+    ld = (k + 63) // 64 * 64
+    lb = ((torch.rand((m, ld), generator=g) - 0.5) * 1e-3).to(torch.bfloat16).to(dev)
+    ut = ((torch.rand((n, ld), generator=g) - 0.5) * 1e-3).to(torch.bfloat16).to(dev)
+    c = torch.rand((m, n), generator=g, dtype=torch.float32).to(dev)
+    scale = torch.tensor([1.0, 1.0, 1.0, 0.0], device=dev)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        ebv.debug_lowp_update(c, lb, ut, scale, 0, 0, 0, m, n, k, "tc", ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ebv.debug_lowp_update(c, lb, ut, scale, 0, 0, 0, m, n, k, "tc", ws=ws, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    tf = 2.0 * m * n * k / (ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops", 1900.0)
+    return {"kernel": "k_tc_update", "m": m, "n": n, "k": k, "ms": ms, "tflops": tf, "peak_bf16_burst": peak,
+            "frac": tf / peak, "bytes_min": 8.0 * m * n + 2.0 * k * (m + n),
+            "hbm_gbs_at_min_bytes": (8.0 * m * n + 2.0 * k * (m + n)) / (ms / 1e3) / 1e9}
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the CPU oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------
 
@@ -412,7 +453,11 @@ def main():
     p.add_argument("--cpu-kstop", type=int, default=384)
     p.add_argument("--ref-kstop", type=int, default=96)
     p.add_argument("--no-graph", dest="graph", action="store_false")
+    p.add_argument("--update-only", default=None, help="M,N,K: time the tensor-core update alone and exit")
     args = p.parse_args()
+    if args.update_only:
+        print(json.dumps(run_update_only(args)), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -253,6 +253,15 @@ EBV_API ebv_status_t ebv_debug_lowp_update(int32_t op, int32_t engine, float *C,
 /* 1 when the tensor-map encoder of the CUDA driver could be resolved. */
 EBV_API int32_t ebv_debug_tc_available(void);
 
+/*
+ * Failure-detection probe (project addition): runs the library's bounded
+ * device wait for `polls` polls (1 .. 2^22) on a flag in `ws` that nothing
+ * sets.  Afterwards the status block at the start of ws (int32 code, where,
+ * done, pad) reads EBV_ERR_TIMEOUT, 77, 0, 1: the wait expired, the status was
+ * recorded and the kernel went on and returned.  ws: >= 256 bytes, 256-aligned.
+ */
+EBV_API ebv_status_t ebv_debug_wait_probe(int64_t polls, void *ws, ebv_stream_t stream);
+
 EBV_API ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b,
                                         int64_t nrhs, double *r, void *ws, size_t ws_bytes, ebv_stream_t stream);
 

@@ -82,6 +82,7 @@ _SIGNATURES = [
     ("ebv_debug_lowp_update", _I32, [_I32, _I32, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _I64, _I64, _I64, _I64, _I64,
                                      _VP, _VP]),
     ("ebv_debug_tc_available", _I32, []),
+    ("ebv_debug_wait_probe", _I32, [_I64, _VP, _VP]),
     ("ebv_debug_launch_count", _I64, []),
     ("ebv_debug_profile", None, [_I32]),
     ("ebv_debug_profile_read", _I32, [_VP, _VP, _VP]),
@@ -471,14 +472,18 @@ def tc_available() -> bool:
 
 
 def debug_lowp_update(c: torch.Tensor, lb: torch.Tensor, ut: torch.Tensor, scale: torch.Tensor, m0: int, n0: int,
-                      k0: int, M: int, N: int, K: int, engine: str = "tc") -> torch.Tensor:
-    """C(m0.., n0..) -= scale[2] * lb(m0.., k0..) @ ut(n0.., k0..)^T in place (testing hook)."""
+                      k0: int, M: int, N: int, K: int, engine: str = "tc", ws: torch.Tensor | None = None,
+                      check: bool = True) -> torch.Tensor:
+    """C(m0.., n0..) -= scale[2] * lb(m0.., k0..) @ ut(n0.., k0..)^T in place (testing hook).
+    check=True synchronises and raises if the device status reports a failure."""
     op = 0 if lb.dtype == torch.bfloat16 else 1
-    ws = torch.empty(256, dtype=torch.uint8, device=c.device)
+    if ws is None:
+        ws = torch.empty(256, dtype=torch.uint8, device=c.device)
     _check(lib().ebv_debug_lowp_update(op, 2 if engine == "tc" else 1, _ptr(c), c.stride(0), _ptr(lb), _ptr(ut),
                                        lb.stride(0), _ptr(scale), m0, n0, k0, M, N, K, _ptr(ws), _stream(c.device)),
            "ebv_debug_lowp_update")
-    code, where = read_device_status(ws)
-    if code != OK:
-        raise EbvError(code, f"device status (where={where})")
+    if check:
+        code, where = read_device_status(ws)
+        if code != OK:
+            raise EbvError(code, f"device status (where={where})")
     return c

@@ -12,6 +12,16 @@ namespace {
 
 constexpr int64_t kMaxN = int64_t(1) << 30;
 
+// Runs the library's bounded wait on flag (which the caller leaves at 0, so
+// nothing ever sets it): every thread of the CTA returns after `polls` polls
+// and the status block records EBV_ERR_TIMEOUT.
+__global__ void k_probe_wait(const int *flag, DevStatus *st, long long polls) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = bounded_wait_geq(flag, 1, st, polls, 77);
+  __syncthreads();
+  if (!ok && threadIdx.x == 0) st->pad = 1;  // the CTA went on after the expired wait
+}
+
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 size_t elem_size(ebv_prec_t p) { return p == EBV_FP32 ? 4 : 8; }
@@ -124,6 +134,15 @@ ebv_status_t ebv_debug_lowp_update(int32_t op, int32_t engine, float *C, int64_t
 }
 
 int32_t ebv_debug_tc_available(void) { return tc_available() ? 1 : 0; }
+
+ebv_status_t ebv_debug_wait_probe(int64_t polls, void *ws, ebv_stream_t stream) {
+  if (polls < 1 || polls > kSpinLimit) return EBV_ERR_ARG;
+  if (!ws || ((uintptr_t)ws % 256) != 0) return EBV_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  EBV_CU(cudaMemsetAsync(ws, 0, kStatusBytes, s));  // status block and the flag at byte 64
+  k_probe_wait<<<1, 64, 0, s>>>((const int *)((char *)ws + 64), (DevStatus *)ws, polls);
+  return launch_ok();
+}
 
 ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b,
                                 int64_t nrhs, double *r, void *ws, size_t ws_bytes, ebv_stream_t stream) {

@@ -81,12 +81,18 @@ __device__ __forceinline__ void st_release(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until *flag >= want; bounded.  Returns false on expiry.
-__device__ __forceinline__ bool wait_flag_geq(const int *flag, int want) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
+// Bounded wait until *flag >= want (acquire).  Gives up after `polls` polls,
+// or early once the status block reports a failure elsewhere; on expiry it
+// records EBV_ERR_TIMEOUT with `where` and returns false.  Every inter-CTA
+// wait of the library goes through here.
+__device__ __forceinline__ bool bounded_wait_geq(const int *flag, int want, DevStatus *st, long long polls,
+                                                 int where) {
+  for (long long it = 0; it < polls; ++it) {
     if (ld_acquire(flag) >= want) return true;
+    if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) return false;
     __nanosleep(64);
   }
+  set_status(st, EBV_ERR_TIMEOUT, where);
   return false;
 }
 

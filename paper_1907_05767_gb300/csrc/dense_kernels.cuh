@@ -53,58 +53,69 @@ struct Shadow {
 };
 
 // ---------------------------------------------------------------------------
-// Diagonal block: unblocked Doolittle on a w x w block (w <= NB), one CTA.
-// Equal bi-vectorised ownership (Eq. 7): thread (p, g) owns the column pair
-// {p, NB-1-p} -- one long and one short vector, so every pair meets the same
-// number of rank-1 updates over the whole elimination -- and the rows
-// g, g+NG, g+2NG, ...  The block lives in registers; each step broadcasts the
-// pivot row, the pivot column and the FP64 pivot reciprocal through shared
-// memory (double-buffered: one barrier per step).
+// Diagonal block: Doolittle on a w x w block (w <= NB), one CTA, block in
+// shared memory (identity beyond w).  Equal bi-vectorised ownership (Eq. 7):
+// thread (p, g) owns the column pair {p, NB-1-p} -- one long and one short
+// vector, so every pair meets the same number of rank-1 updates over the whole
+// elimination -- and the rows g, g+NG, g+2NG, ...
+// Step r reads column r and row r and writes only entries (i > r, j > r), so
+// one barrier per step suffices: the multiplier of row i is formed on the fly
+// as a_ir * (1/a_rr) and stored in place in one pass at the end (column r is
+// never written after step r).  The FP64 reciprocal of the next pivot is taken
+// once, by the thread that has just updated that pivot.
+// Then the two inverses (L11^{-1}, U11^{-1}) by the same right-looking,
+// hazard-free sweeps, both in one barrier per step, written to
+// inv[0..NB*NB) and inv[NB*NB..2*NB*NB) (row-major).
+// Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
-// Inverses of the unit-lower and the upper factor of a packed NB x NB block
-// F (shared memory), written to inv[0 .. NB*NB) (L^{-1}) and
-// inv[NB*NB .. 2*NB*NB) (U^{-1}), row-major.  Row sweeps with four threads per
-// column splitting each dot product; the diagonal of U^{-1} is the FP64
-// reciprocal of the pivot.
-template <typename T, int NB, int NT>
-__device__ void block_inverses(T (*Fs)[NB + 1], T (*Iv)[NB + 1], T *inv) {
-  static_assert(NT == 4 * NB, "four threads per column");
-  const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
-  // L^{-1}: X[i][c] = -(F[i][c] + sum_{c<k<i} F[i][k] X[k][c]) for c < i.
-  for (int e = threadIdx.x; e < NB * NB; e += NT) Iv[e / NB][e % NB] = (e / NB == e % NB) ? T(1) : T(0);
-  __syncthreads();
-  for (int i = 1; i < NB; ++i) {
-    T s = T(0);
-    if (c < i)
-      for (int k = c + 1 + part; k < i; k += 4) s += Fs[i][k] * Iv[k][c];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (part == 0 && c < i) Iv[i][c] = -(Fs[i][c] + s);
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < NB * NB; e += NT) inv[e] = Iv[e / NB][e % NB];
-  __syncthreads();
-  // U^{-1}: X[i][i] = 1/u_ii; X[i][c] = -(sum_{i<k<=c} F[i][k] X[k][c]) / u_ii for c > i.
-  // The NB pivot reciprocals are FP64 divisions, one per thread, done once.
-  __shared__ T rcp_t[NB];
-  for (int e = threadIdx.x; e < NB * NB; e += NT) Iv[e / NB][e % NB] = T(0);
-  for (int i = threadIdx.x; i < NB; i += NT) rcp_t[i] = (T)(1.0 / (double)Fs[i][i]);
-  __syncthreads();
-  for (int i = NB - 1; i >= 0; --i) {
-    const T r = rcp_t[i];
-    T s = T(0);
-    if (c > i)
-      for (int k = i + 1 + part; k <= c; k += 4) s += Fs[i][k] * Iv[k][c];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (part == 0 && c >= i) Iv[i][c] = (c == i) ? r : -s * r;
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < NB * NB; e += NT) inv[NB * NB + e] = Iv[e / NB][e % NB];
-}
+template <typename T, int NB>
+constexpr size_t diag_smem_bytes() { return 3 * sizeof(T) * NB * (NB + 1); }
 
 template <typename T, int NB>
 constexpr size_t pair_smem_bytes() { return 2 * sizeof(T) * NB * (NB + 1); }
+
+// X = L^{-1} and Y = U^{-1} from the packed factors D (NB x NB, identity
+// padded) and the pivot reciprocals rcp; thread ownership as in the
+// factorisation.  Writes inv (2 * NB * NB).
+template <typename T, int NB, int NT>
+__device__ void triangle_inverses(T (*D)[NB + 1], T (*X)[NB + 1], T (*Y)[NB + 1], const T *rcp, T *inv) {
+  constexpr int NP = NB / 2, NG = NT / NP, RPT = NB / NG;
+  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
+  const int c0 = p, c1 = NB - 1 - p;
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int i = e / NB, j = e % NB;
+    X[i][j] = Y[i][j] = (i == j) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int s = 0; s < NB; ++s) {
+    // L^{-1}, step k = s: rows i > k, columns c <= k:  X[i][c] -= l_ik X[k][c]
+    const int k = s;
+    const T x0 = X[k][c0], x1 = X[k][c1];
+    // U^{-1}, step q = NB-1-s: rows i < q, columns c >= q:  Y[i][c] -= (u_iq / u_qq) Y[q][c]
+    const int q = NB - 1 - s;
+    const T y0 = Y[q][c0], y1 = Y[q][c1], rq = rcp[q];
+#pragma unroll
+    for (int t = 0; t < RPT; ++t) {
+      const int i = g + NG * t;
+      if (i > k) {
+        const T l = D[i][k];
+        if (c0 <= k) X[i][c0] -= l * x0;
+        if (c1 <= k && c1 != c0) X[i][c1] -= l * x1;
+      }
+      if (i < q) {
+        const T u = D[i][q] * rq;
+        if (c0 >= q) Y[i][c0] -= u * y0;
+        if (c1 >= q && c1 != c0) Y[i][c1] -= u * y1;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int i = e / NB, j = e % NB;
+    inv[e] = X[i][j];
+    inv[NB * NB + e] = Y[i][j] * rcp[i];  // rows of U^{-1} take their pivot's reciprocal last
+  }
+}
 
 template <typename T, int NB, int NT>
 __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
@@ -112,87 +123,56 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
   constexpr int NG = NT / NP;
   constexpr int RPT = NB / NG;
   static_assert(NT % NP == 0 && NB % NG == 0, "shape");
-  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
-  const int cj0 = p, cj1 = NB - 1 - p;
-  __shared__ T rowbuf[2][NB];
-  __shared__ T colbuf[2][NB];
-  __shared__ T rcp[NB];  // FP64 pivot reciprocal (one division, by the pivot's owner), rounded to T
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  T(*Y)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + 2 * sizeof(T) * NB * (NB + 1));
+  __shared__ T rcp[NB];  // FP64 pivot reciprocals, rounded to T
   __shared__ int bad;
-  T v[RPT][2];
-  if (threadIdx.x == 0) bad = NB;
-#pragma unroll
-  for (int t = 0; t < RPT; ++t) {
-    const int i = g + NG * t;
-    v[t][0] = (i < w && cj0 < w) ? A.get(k0 + i, k0 + cj0) : T(0);
-    v[t][1] = (i < w && cj1 < w) ? A.get(k0 + i, k0 + cj1) : T(0);
+  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
+  const int c0 = p, c1 = NB - 1 - p;
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int i = e / NB, j = e % NB;
+    D[i][j] = (i < w && j < w) ? A.get(k0 + i, k0 + j) : (i == j ? T(1) : T(0));
   }
   __syncthreads();
-  auto publish = [&](int r) {
-    const int buf = r & 1;
-#pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-      const int i = g + NG * t;
-      if (i >= w) continue;
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int j = s ? cj1 : cj0;
-        if (j >= w) continue;
-        if (i == r && j > r) rowbuf[buf][j] = v[t][s];
-        if (j == r && i > r) colbuf[buf][i] = v[t][s];
-        if (i == r && j == r) {
-          const double pv = (double)v[t][s];
-          rcp[r] = (T)(1.0 / pv);
-          if (!(pv != 0.0) || !isfinite(pv)) atomicMin(&bad, r);
-        }
-      }
-    }
-  };
-  publish(0);
+  if (threadIdx.x == 0) {
+    const double pv = (double)D[0][0];
+    rcp[0] = (T)(1.0 / pv);
+    bad = (!(pv != 0.0) || !isfinite(pv)) ? 0 : NB;
+  }
   __syncthreads();
-  for (int r = 0; r < w; ++r) {
-    const int buf = r & 1;
+  for (int r = 0; r + 1 < NB; ++r) {
     const T rc = rcp[r];
+    const T u0 = D[r][c0], u1 = D[r][c1];
 #pragma unroll
     for (int t = 0; t < RPT; ++t) {
       const int i = g + NG * t;
-      if (i > r && i < w) {
-        const T l = colbuf[buf][i] * rc;  // Eq. 6a
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          const int j = s ? cj1 : cj0;
-          if (j == r)
-            v[t][s] = l;
-          else if (j > r && j < w)
-            v[t][s] -= l * rowbuf[buf][j];  // Eq. 6c
-        }
+      if (i > r) {
+        const T l = D[i][r] * rc;  // Eq. 6a
+        if (c0 > r) D[i][c0] -= l * u0;  // Eq. 6c
+        if (c1 > r && c1 != c0) D[i][c1] -= l * u1;
       }
     }
-    if (r + 1 < w) publish(r + 1);
+    // The owner of entry (r+1, r+1) has just produced the next pivot.
+    if (g == (r + 1) % NG && (c0 == r + 1 || c1 == r + 1)) {
+      const double pv = (double)D[r + 1][r + 1];
+      rcp[r + 1] = (T)(1.0 / pv);
+      if (r + 1 < w && (!(pv != 0.0) || !isfinite(pv))) atomicMin(&bad, r + 1);
+    }
     __syncthreads();
   }
-#pragma unroll
-  for (int t = 0; t < RPT; ++t) {
-    const int i = g + NG * t;
-    if (i < w && cj0 < w) A.put(k0 + i, k0 + cj0, v[t][0]);
-    if (i < w && cj1 < w) A.put(k0 + i, k0 + cj1, v[t][1]);
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {  // multipliers in place (Eq. 6a)
+    const int i = e / NB, j = e % NB;
+    if (i > j) D[i][j] *= rcp[j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int i = e / NB, j = e % NB;
+    if (i < w && j < w) A.put(k0 + i, k0 + j, D[i][j]);
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
-  if (!inv) return;
-  // Inverses of the two triangular factors, so that L21 = A21 U11^{-1} and
-  // U12 = L11^{-1} A12 become independent tile products.  The block is padded
-  // with the identity beyond w.  Dynamic shared memory: T F[NB][NB+1], T I[NB][NB+1].
-  extern __shared__ __align__(16) unsigned char dsm[];
-  T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T(*Iv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
-  for (int e = threadIdx.x; e < NB * NB; e += NT) Fs[e / NB][e % NB] = (e / NB == e % NB) ? T(1) : T(0);
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < RPT; ++t) {
-    const int i = g + NG * t;
-    if (i < w && cj0 < w) Fs[i][cj0] = v[t][0];
-    if (i < w && cj1 < w) Fs[i][cj1] = v[t][1];
-  }
-  block_inverses<T, NB, NT>(Fs, Iv, inv);
+  if (inv) triangle_inverses<T, NB, NT>(D, X, Y, rcp, inv);
 }
 
 // ---------------------------------------------------------------------------
@@ -298,7 +278,8 @@ ebv_status_t prepare_leaf_kernels() {
   static const cudaError_t err = [] {
     const int bytes = (int)pair_smem_bytes<T, kNB>();
     cudaError_t e = cudaFuncSetAttribute(k_diag_factor<T, kNB, 4 * kNB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)diag_smem_bytes<T, kNB>());
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_trsm_ru<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)

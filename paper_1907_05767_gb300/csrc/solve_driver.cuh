@@ -9,15 +9,12 @@
 namespace ebv {
 namespace {
 
+// Right-hand sides per substitution chain: each chunk of RC columns is solved
+// by its own chain of CTAs, so 32 columns make 4 chains whose per-step
+// critical work is a quarter of one.
 template <typename T>
-struct TrsvCfg;
-template <>
-struct TrsvCfg<double> {
+struct TrsvCfg {
   static constexpr int RC = 8;
-};
-template <>
-struct TrsvCfg<float> {
-  static constexpr int RC = 32;
 };
 
 struct DenseSolveLayout {
@@ -51,10 +48,10 @@ inline int grid_for(int64_t elems) { return (int)std::min<int64_t>(4096, std::ma
 template <typename T>
 ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
   static const cudaError_t attr = cudaFuncSetAttribute(
-      k_diag_inverses<T, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes<T, kNB>());
+      k_diag_inverses<T, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem_bytes<T, kNB>());
   if (attr != cudaSuccess) return EBV_ERR_CUDA;
   prof::Scope ps(s, prof::kTrsv, 2.0 * ceil_div(n, kNB) * kNB * kNB * kNB / 3.0);
-  k_diag_inverses<T, kNB><<<ceil_div(n, kNB), 4 * kNB, pair_smem_bytes<T, kNB>(), s>>>(F, n, dinv);
+  k_diag_inverses<T, kNB><<<ceil_div(n, kNB), 4 * kNB, diag_smem_bytes<T, kNB>(), s>>>(F, n, dinv);
   return launch_ok();
 }
 
@@ -69,6 +66,7 @@ ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, cons
   auto kern = k_trsv_persistent<T, kNB, RC, UPPER>;
   static int resident = [&] {
     int dev = 0, sms = 0, per_sm = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);

@@ -11,40 +11,46 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // Inverses of the diagonal blocks of the packed factors (block b: L_bb^{-1}
 // then U_bb^{-1} at dinv + b * 2 * NB * NB), one CTA per block, so that each
 // diagonal solve of the substitution is a tile product.
-// Dynamic shared memory: pair_smem_bytes<T, NB>().
+// Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
 __global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t n, T *dinv) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T(*Iv)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
+  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  T(*Y)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + 2 * sizeof(T) * NB * (NB + 1));
+  __shared__ T rcp[NB];
   const int64_t i0 = (int64_t)blockIdx.x * NB;
   const int hb = (int)min64(NB, n - i0);
   for (int e = threadIdx.x; e < NB * NB; e += 4 * NB) {
     const int r = e / NB, k = e % NB;
-    Fs[r][k] = (r < hb && k < hb) ? F.get(i0 + r, i0 + k) : (r == k ? T(1) : T(0));
+    D[r][k] = (r < hb && k < hb) ? F.get(i0 + r, i0 + k) : (r == k ? T(1) : T(0));
   }
   __syncthreads();
-  block_inverses<T, NB, 4 * NB>(Fs, Iv, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
+  for (int r = threadIdx.x; r < NB; r += 4 * NB) rcp[r] = (T)(1.0 / (double)D[r][r]);  // one FP64 division each
+  __syncthreads();
+  triangle_inverses<T, NB, 4 * NB>(D, X, Y, rcp, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
 }
 
 // ---------------------------------------------------------------------------
 // Block substitution in one cooperative launch per triangle (Eq. 1: LY = B,
 // then UX = Y).  Steps s = 0..nblk-1 visit the row blocks in solve order
-// (increasing for L, decreasing for U).  CTA h of a right-hand-side chunk
-// owns the steps s = h (mod G) and keeps those blocks of B up to date in
-// global memory: when the block of step s is published, the owner of step
-// s+1 first folds it into its own block, solves that block through the
-// diagonal-block inverse (a 64 x 64 tile product, no sequential chain) and
-// publishes it; only then does every CTA fold step s into the other blocks it
-// owns.  Flags are per step; every wait is bounded and gives up once the
-// workspace status reports an error.  All CTAs must be co-resident: the
-// driver launches at most the occupancy limit, cooperatively.
+// (increasing for L, decreasing for U); each chunk of RC right-hand sides is
+// an independent chain of CTAs.  CTA h of a chain owns the steps s = h (mod G)
+// and keeps those blocks of B up to date in global memory.  The critical path
+// is: block s published -> its owner-of-(s+1) folds it into block s+1 and
+// solves that block through the diagonal-block inverse (tile products, no
+// sequential chain) -> publishes.  So the owner of s+1 loads everything that
+// does not depend on block s (the coupling block of the factor, the inverse,
+// its own B block) before it waits, and folds block s into its other blocks
+// only after publishing.  Flags are per step; every wait is bounded and gives
+// up once the workspace status reports an error.  All CTAs must be
+// co-resident: the driver launches at most the occupancy limit, cooperatively.
 // Dynamic shared memory: trsvp_smem_bytes<T, NB, RC>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB, int RC>
 constexpr size_t trsvp_smem_bytes() {
-  return sizeof(T) * (2 * NB * (RC + 1) + NB * (NB + 1));
+  return sizeof(T) * (3 * NB * (RC + 1) + 2 * NB * (NB + 1));
 }
 
 template <typename T, int NB, int RC, bool UPPER>
@@ -52,9 +58,11 @@ __global__ void __launch_bounds__(256)
     k_trsv_persistent(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
                       DevStatus *st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*Y)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw);
+  T(*Y)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw);                           // block of step s
   T(*acc)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
-  T(*Fb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * 2 * NB * (RC + 1));
+  T(*Bo)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + 2 * sizeof(T) * NB * (RC + 1));  // own B block
+  T(*Fb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + 3 * sizeof(T) * NB * (RC + 1));
+  T(*Di)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * (3 * NB * (RC + 1) + NB * (NB + 1)));
   __shared__ int s_ok;
   if (st && st->done) return;  // refinement already converged
   const int nblk = ceil_div(n, NB);
@@ -71,40 +79,45 @@ __global__ void __launch_bounds__(256)
   constexpr int PASS = 256 / RC;  // rows covered per pass of the thread block
   const int tc = threadIdx.x % RC, tr = threadIdx.x / RC;
 
-  // acc <- B_blk(t) - F(blk(t), blk(s)) * Y   (Y = published block of step s)
-  auto fold = [&](int s, int t) {
+  auto load_f = [&](int s, int t) {  // Fb <- F(blk(t), blk(s))
     const int64_t i0 = (int64_t)blk(t) * NB, j0 = (int64_t)blk(s) * NB;
     const int hi = (int)min64(NB, n - i0), hj = (int)min64(NB, n - j0);
     for (int e = threadIdx.x; e < NB * NB; e += 256) {
       const int r = e / NB, k = e % NB;
       Fb[r][k] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
     }
-    __syncthreads();
+  };
+  auto load_b = [&](int t) {  // Bo <- B_blk(t)
+    const int64_t i0 = (int64_t)blk(t) * NB;
+    const int hi = (int)min64(NB, n - i0);
+    for (int r = tr; r < NB; r += PASS) Bo[r][tc] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
+  };
+  auto load_dinv = [&](int t) {
+    const T *di = dinv + (int64_t)blk(t) * 2 * NB * NB + (UPPER ? NB * NB : 0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Di[e / NB][e % NB] = di[e];
+  };
+  auto fold = [&]() {  // acc <- Bo - Fb * Y
     for (int r = tr; r < NB; r += PASS) {
-      T a = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
+      T a = Bo[r][tc];
 #pragma unroll 16
       for (int k = 0; k < NB; ++k) a -= Fb[r][k] * Y[k][tc];
       acc[r][tc] = a;
     }
-    __syncthreads();
   };
-  auto store = [&](int t) {
+  auto store_acc = [&](int t) {
     const int64_t i0 = (int64_t)blk(t) * NB;
     const int hi = (int)min64(NB, n - i0);
     for (int r = tr; r < hi; r += PASS)
       if (tc < wc) B[(i0 + r) * ldb + c0 + tc] = acc[r][tc];
   };
-  // Solve the block of step t in place from acc: B_blk(t) = D^{-1} acc, then release flag t.
+  // B_blk(t) = D^{-1} acc, then release flag t.
   auto solve_publish = [&](int t) {
-    const T *di = dinv + (int64_t)blk(t) * 2 * NB * NB + (UPPER ? NB * NB : 0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) Fb[e / NB][e % NB] = di[e];
-    __syncthreads();
     const int64_t i0 = (int64_t)blk(t) * NB;
     const int hi = (int)min64(NB, n - i0);
     for (int r = tr; r < hi; r += PASS) {
       T a = T(0);
 #pragma unroll 16
-      for (int k = 0; k < NB; ++k) a += Fb[r][k] * acc[k][tc];
+      for (int k = 0; k < NB; ++k) a += Di[r][k] * acc[k][tc];
       if (tc < wc) B[(i0 + r) * ldb + c0 + tc] = a;
     }
     __threadfence();
@@ -113,30 +126,24 @@ __global__ void __launch_bounds__(256)
   };
 
   if (h == 0) {  // step 0: its block has no updates to receive
-    const int64_t i0 = (int64_t)blk(0) * NB;
-    const int hi = (int)min64(NB, n - i0);
-    for (int r = tr; r < NB; r += PASS) acc[r][tc] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
+    load_b(0);
+    load_dinv(0);
+    __syncthreads();
+    for (int r = tr; r < NB; r += PASS) acc[r][tc] = Bo[r][tc];
     __syncthreads();
     solve_publish(0);
   }
   for (int s = 0; s + 1 < nblk; ++s) {
     const int last = (int)min64(nblk - 1, (int64_t)s + reach);
-    // first step > s owned by this CTA
-    int t = s + 1 + (((h - (s + 1)) % G) + G) % G;
-    if (t > last) continue;  // nothing of ours depends on step s
-    if (threadIdx.x == 0) {
-      bool ok = false;
-      for (long long it = 0; it < kSpinLimit; ++it) {
-        if (ld_acquire(&fl[s]) >= 1) {
-          ok = true;
-          break;
-        }
-        if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) break;
-        __nanosleep(64);
-      }
-      s_ok = ok;
-      if (!ok) set_status(st, EBV_ERR_TIMEOUT, s);
+    int t = s + 1 + (((h - (s + 1)) % G) + G) % G;  // first step > s owned by this CTA
+    if (t > last) continue;                          // nothing of ours depends on step s
+    const bool critical = t == s + 1;
+    if (critical) {  // independent of block s: fetch while its owner is still working
+      load_f(s, t);
+      load_b(t);
+      load_dinv(t);
     }
+    if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[s], 1, st, kSpinLimit, s);
     __syncthreads();
     if (!s_ok) return;
     {
@@ -145,12 +152,19 @@ __global__ void __launch_bounds__(256)
       for (int k = tr; k < NB; k += PASS) Y[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
     }
     __syncthreads();
+    if (critical) {
+      fold();
+      __syncthreads();
+      solve_publish(t);  // every earlier step has already been folded into block t
+      t += G;
+    }
     for (; t <= last; t += G) {
-      fold(s, t);
-      if (t == s + 1)
-        solve_publish(t);  // every earlier step has already been folded into it
-      else
-        store(t);
+      load_f(s, t);
+      load_b(t);
+      __syncthreads();
+      fold();
+      __syncthreads();
+      store_acc(t);
       __syncthreads();
     }
   }

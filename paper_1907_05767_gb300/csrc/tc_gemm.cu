@@ -128,7 +128,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   auto stage_b = [&](int s) { return base + s * STAGE_BYTES + A_BYTES; };
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tile_n = blockIdx.x, tile_m = blockIdx.y;
+  // Grouped raster: consecutive CTAs sweep the N tiles of a group of GROUP_M
+  // M tiles, so one wave touches ~GROUP_M A slabs and a few B slabs, which
+  // stay in L2 instead of streaming all of B from HBM once per wave.
+  constexpr int GROUP_M = 16;
+  const int num_m = (M + BM - 1) / BM, num_n = (N + BN - 1) / BN;
+  const int bid = blockIdx.x;
+  const int group = bid / (GROUP_M * num_n);
+  const int first_m = group * GROUP_M;
+  const int gsize = min(GROUP_M, num_m - first_m);
+  const int within = bid % (GROUP_M * num_n);
+  const int tile_m = first_m + within % gsize, tile_n = within / gsize;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -284,7 +294,7 @@ ebv_status_t launch_tc(int op, float *C, int64_t ldc, const void *lb, const void
   if (!make_map(&ma, op, lb, k0 + K, m0 + M, ldsh, BM)) return EBV_ERR_UNSUPPORTED;
   if (!make_map(&mb, op, ut, k0 + K, n0 + N, ldsh, BN)) return EBV_ERR_UNSUPPORTED;
   const int vec_ok = (ldc % 4 == 0) && (n0 % 4 == 0) && (((uintptr_t)C) % 16 == 0);
-  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
+  dim3 grid(ceil_div(N, BN) * ceil_div(M, BM));  // linear; the kernel maps it with a grouped raster
   k_tc_update<BN><<<grid, NTHREADS, smem_bytes<BN>(), s>>>(ma, mb, C, ldc, scale, m0, n0, (int)k0, (int)M, (int)N,
                                                           (int)(K / BK), make_idesc(op == 0 ? 1u : 0u, BN), vec_ok, st);
   return launch_ok();
