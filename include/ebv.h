@@ -221,6 +221,37 @@ EBV_API ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs, c
                                double *grad_a, ebv_stream_t stream);
 
 /*
+ * ebv_solve_static -- ebv_solve without a caller-supplied workspace, for
+ * callers that cannot allocate device memory (code running while someone
+ * else captures the stream into a CUDA graph, loops whose memory is budgeted
+ * up front, plug-ins whose host owns every allocation).  The paper has no
+ * counterpart: it is an interface addition of this library.
+ *
+ * Arguments, layouts, ownership and results are those of ebv_solve; the
+ * workspace is a fixed device array of EBV_STATIC_SCRATCH_BYTES inside this
+ * library, reserved on every device that loads it until the process exits.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).
+ *
+ * Limits: n <= EBV_STATIC_MAX_N and nrhs <= EBV_STATIC_MAX_NRHS; larger
+ * sizes return EBV_ERR_WORKSPACE before any work is enqueued.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture on that device.  All calls on a device share the
+ * one array, which keeps the last call's contents (each call clears what has
+ * to start at zero): calls whose work overlaps on the GPU (other streams,
+ * other host threads without ordering) race and give undefined results.
+ */
+#define EBV_STATIC_SCRATCH_BYTES ((size_t)9 << 20)
+#define EBV_STATIC_MAX_N 4096
+#define EBV_STATIC_MAX_NRHS 32
+EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu,
+                                      const double *a_orig, void *b, int64_t nrhs, int64_t ldb,
+                                      const ebv_refine_t *refine, ebv_refine_report_t *report_dev,
+                                      ebv_stream_t stream);
+
+/*
  * Testing hook (no counterpart in the paper): selects how the mixed-precision
  * trailing updates run.  0 = automatic (tensor cores where the shape allows),
  * 1 = SIMT FP32 kernel from the same bfloat16/half operands, 2 = tensor cores

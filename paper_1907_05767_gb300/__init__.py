@@ -70,6 +70,8 @@ _SIGNATURES = [
     ("ebv_factor", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _VP, _SZ, _VP]),
     ("ebv_solve", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _I64, _I64, ctypes.POINTER(Refine), _VP, _VP,
                          _SZ, _VP]),
+    ("ebv_solve_static", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _I64, _I64, ctypes.POINTER(Refine), _VP,
+                                _VP]),
     ("ebv_batch_schedule_len", _I64, [_I64]),
     ("ebv_batch_workspace_size", _SZ, [_I64]),
     ("ebv_batch_schedule", _I32, [_I64, _VP, _VP, _VP, _VP]),
@@ -215,6 +217,34 @@ def ebv_solve(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tens
     _check(lib().ebv_solve(ctypes.byref(d), p, _ptr(lu), _ptr(a_orig), _ptr(b2), nrhs, b2.stride(0),
                            ctypes.byref(ref) if ref is not None else None, _ptr(report), _ptr(ws), ws.numel(),
                            _stream(b.device)), "ebv_solve")
+    return b
+
+
+# Limits of ebv_solve_static (its workspace is a fixed device array).
+STATIC_SCRATCH_BYTES = 9 << 20
+STATIC_MAX_N = 4096
+STATIC_MAX_NRHS = 32
+
+
+def ebv_solve_static(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tensor | None = None,
+                     refine: tuple | None = None, report: torch.Tensor | None = None, kl=0, ku=0, storage=DENSE,
+                     ld=None) -> torch.Tensor:
+    """``ebv_solve`` for callers that cannot allocate device memory: the
+    workspace is the library's fixed device array (n <= STATIC_MAX_N,
+    nrhs <= STATIC_MAX_NRHS).  Overwrites ``b`` with X.  ``report`` must be
+    passed in (already allocated) when ``refine`` is given."""
+    p = _prec(prec)
+    _need_cuda(lu, b, a_orig, report)
+    n = b.shape[0]
+    b2 = b if b.dim() == 2 else b.view(n, 1)
+    nrhs = b2.shape[1]
+    if ld is None:
+        ld = lu.stride(0)
+    d = _desc(n, ld, kl, ku, storage)
+    ref = Refine(float(refine[0]), int(refine[1]), 0) if refine is not None else None
+    _check(lib().ebv_solve_static(ctypes.byref(d), p, _ptr(lu), _ptr(a_orig), _ptr(b2), nrhs, b2.stride(0),
+                                  ctypes.byref(ref) if ref is not None else None, _ptr(report),
+                                  _stream(b.device)), "ebv_solve_static")
     return b
 
 
