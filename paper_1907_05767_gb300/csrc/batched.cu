@@ -49,7 +49,7 @@ struct BatchSmem {
   T D[NB][NB + 1];   // diagonal block (packed L\U after the warp factorisation)
   T Li[NB][NB + 1];  // L11^{-1}
   T Ui[NB][NB + 1];  // U11^{-1}
-  T rcp[NB];         // FP64 pivot reciprocals, rounded to T
+  T rcp[NB];         // pivot reciprocals
   T As[NB][64 + 1];  // K-slab of L21 for one 64 x 64 output tile (transposed); also a 64 x NB tile
   T Bs[NB][64 + 1];  // K-slab of U12 for the same tile
   int bad;           // first failing pivot of the system (0-based), or INT32_MAX
@@ -58,7 +58,7 @@ struct BatchSmem {
 // Unblocked Doolittle of the w x w block D (w <= NB <= 32) by warp 0.  Lane
 // (p, g) owns the column pair {p, NB-1-p} and the rows g, g+NG, ...; the pair
 // holds one long and one short column, so all lanes do the same number of
-// updates over the elimination (Eq. 7).  Multipliers use the FP64 pivot
+// updates over the elimination (Eq. 7).  Multipliers use the pivot
 // reciprocal (one division per pivot).
 template <typename T, int NB>
 __device__ void warp_diag_factor(BatchSmem<T, NB> &sm, int w, int k0, int lane) {
@@ -67,9 +67,9 @@ __device__ void warp_diag_factor(BatchSmem<T, NB> &sm, int w, int k0, int lane) 
   const int c0 = p, c1 = NB - 1 - p;
   for (int r = 0; r < w; ++r) {
     if (lane == 0) {
-      const double pv = (double)sm.D[r][r];
-      sm.rcp[r] = (T)(1.0 / pv);
-      if ((!(pv != 0.0) || !isfinite(pv)) && sm.bad > k0 + r) sm.bad = k0 + r;
+      const T pv = sm.D[r][r];
+      sm.rcp[r] = pivot_rcp(pv);
+      if (pivot_bad(pv) && sm.bad > k0 + r) sm.bad = k0 + r;
     }
     __syncwarp();
     const T rc = sm.rcp[r];
@@ -248,12 +248,12 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
     }
     __syncthreads();
   }
-  // Backward substitution UX = Y, diagonal through FP64 reciprocals.
+  // Backward substitution UX = Y, diagonal through pivot reciprocals.
   for (int kend = n; kend > 0; kend -= NB) {
     const int k0 = max(0, kend - NB), w = kend - k0;
     if (warp == 0) {
       for (int r = w - 1; r >= 0; --r) {
-        const T rc = (T)(1.0 / (double)A[(int64_t)(k0 + r) * n + k0 + r]);
+        const T rc = pivot_rcp(A[(int64_t)(k0 + r) * n + k0 + r]);
         for (int c = lane; c < nrhs; c += 32) B[(int64_t)(k0 + r) * nrhs + c] *= rc;
         __syncwarp();
         for (int e = lane; e < r * nrhs; e += 32) {

@@ -66,6 +66,16 @@ __device__ __forceinline__ float to_float(double x) { return (float)x; }
 __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
 
+// Reciprocal of a pivot in the working precision, correctly rounded.  The
+// binary32 version stays on the FP32 pipe: on GB300 one FP64 division costs
+// several hundred cycles, which on the pivot's critical path dominated the
+// 64-step diagonal-block kernels.
+__device__ __forceinline__ double pivot_rcp(double p) { return 1.0 / p; }
+__device__ __forceinline__ float pivot_rcp(float p) { return __frcp_rn(p); }
+// A zero or non-finite pivot (tested in the working precision).
+template <typename T>
+__device__ __forceinline__ bool pivot_bad(T p) { return !(p != T(0)) || !isfinite(p); }
+
 // Record the first device-side failure in a status block (first writer wins).
 __device__ __forceinline__ void set_status(DevStatus *st, int code, int where) {
   if (st && atomicCAS(&st->code, 0, code) == 0) st->where = where;

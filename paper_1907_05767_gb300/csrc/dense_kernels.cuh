@@ -40,6 +40,26 @@ inline MatView<T> band_view(T *ab, int64_t ldab, int64_t kl, int64_t ku) {
   return MatView<T>{ab + kl, ldab - 1, kl, ku};
 }
 
+// Stage an NB x NB tile into shared memory (row stride S) with all of the
+// thread's global loads issued before the first store, so one memory latency
+// is paid instead of NB*NB/NT of them.  get(i, j) returns element (i, j).
+template <int NB, int NT, int S, typename T, typename Get>
+__device__ __forceinline__ void stage_tile(T *dst, Get get) {
+  constexpr int L = NB * NB / NT;
+  static_assert(L * NT == NB * NB, "tile must divide evenly");
+  T r[L];
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    const int e = threadIdx.x + NT * q;
+    r[q] = get(e / NB, e % NB);
+  }
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    const int e = threadIdx.x + NT * q;
+    dst[(e / NB) * S + e % NB] = r[q];
+  }
+}
+
 // Low-precision shadow copies of the factors that feed the tensor-core GEMMs:
 // lb (n x n, row-major) holds scale[0] * L, ut (n x n) holds scale[1] * U^T,
 // so both GEMM operands are K-major.  Null when the trailing updates run in the
@@ -53,118 +73,161 @@ struct Shadow {
 };
 
 // ---------------------------------------------------------------------------
-// Diagonal block: Doolittle on a w x w block (w <= NB), one CTA, block in
-// shared memory (identity beyond w).  Equal bi-vectorised ownership (Eq. 7):
-// thread (p, g) owns the column pair {p, NB-1-p} -- one long and one short
-// vector, so every pair meets the same number of rank-1 updates over the whole
-// elimination -- and the rows g, g+NG, g+2NG, ...
-// Step r reads column r and row r and writes only entries (i > r, j > r), so
-// one barrier per step suffices: the multiplier of row i is formed on the fly
-// as a_ir * (1/a_rr) and stored in place in one pass at the end (column r is
-// never written after step r).  The FP64 reciprocal of the next pivot is taken
-// once, by the thread that has just updated that pivot.
-// Then the two inverses (L11^{-1}, U11^{-1}) by the same right-looking,
-// hazard-free sweeps, both in one barrier per step, written to
+// Diagonal block: Doolittle on a w x w block (w <= NB = 64), one CTA of 256
+// threads, identity beyond w.  Equal bi-vectorised ownership (Eq. 7): lane p
+// of warp g holds, in registers, rows 8g .. 8g+7 of the column pair
+// {p, NB-1-p} -- one long and one short vector.  Step r needs only the pivot
+// row r and the column r, which their owners publish into double-buffered
+// shared vectors at the end of step r-1 (zero outside the active part, so
+// every thread runs the same unpredicated 16 multiply-adds per step), plus
+// the pivot's reciprocal: one barrier per step and no shared-memory traffic
+// on the block itself.  The multiplier of row i is formed on the fly as
+// a_ir * (1/a_rr) and stored in place at the end (Eq. 6a); column r is never
+// updated after step r.  Then the two inverses (L11^{-1}, U11^{-1}) by the
+// same register-resident, one-barrier-per-step sweeps, written to
 // inv[0..NB*NB) and inv[NB*NB..2*NB*NB) (row-major).
 // Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
-constexpr size_t diag_smem_bytes() { return 3 * sizeof(T) * NB * (NB + 1); }
+constexpr size_t diag_smem_bytes() { return sizeof(T) * ((size_t)NB * (NB + 1) + 8 * (size_t)NB); }
 
 template <typename T, int NB>
 constexpr size_t pair_smem_bytes() { return 2 * sizeof(T) * NB * (NB + 1); }
 
-// X = L^{-1} and Y = U^{-1} from the packed factors D (NB x NB, identity
-// padded) and the pivot reciprocals rcp; thread ownership as in the
-// factorisation.  Writes inv (2 * NB * NB).
+// X = L^{-1} and Y = U^{-1} from the packed factors D (NB x NB in shared
+// memory, identity padded) and the pivot reciprocals rcp; ownership as in
+// the factorisation.  X: rows i > k take -l_ik * (row k of X), k = 0..NB-1.
+// Y: with V = U diag(1/u) (unit upper), rows i < q take -v_iq * (row q of Y),
+// q = NB-1..0, so Y = V^{-1} and U^{-1} = diag(1/u) Y.  buf: 4*NB elements
+// of shared scratch.  Writes inv (2 * NB * NB).
 template <typename T, int NB, int NT>
-__device__ void triangle_inverses(T (*D)[NB + 1], T (*X)[NB + 1], T (*Y)[NB + 1], const T *rcp, T *inv) {
-  constexpr int NP = NB / 2, NG = NT / NP, RPT = NB / NG;
-  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
-  const int c0 = p, c1 = NB - 1 - p;
-  for (int e = threadIdx.x; e < NB * NB; e += NT) {
-    const int i = e / NB, j = e % NB;
-    X[i][j] = Y[i][j] = (i == j) ? T(1) : T(0);
+__device__ void triangle_inverses(T (*D)[NB + 1], T *buf, const T *rcp, T *inv) {
+  static_assert(NB == 64 && NT == 256, "one column pair per lane, 8 rows per warp");
+  constexpr int RPW = NB / (NT / 32);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int c0 = lane, c1 = NB - 1 - lane, i0 = g * RPW;
+  T *rx = buf, *ry = buf + 2 * NB;  // double-buffered row k of X, row q of Y
+  T x0[RPW], x1[RPW], y0[RPW], y1[RPW];
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {
+    x0[t] = y0[t] = (i0 + t == c0) ? T(1) : T(0);
+    x1[t] = y1[t] = (i0 + t == c1) ? T(1) : T(0);
+  }
+  if (threadIdx.x < NB) {
+    rx[threadIdx.x] = threadIdx.x == 0 ? T(1) : T(0);
+    ry[threadIdx.x] = threadIdx.x == NB - 1 ? T(1) : T(0);
   }
   __syncthreads();
   for (int s = 0; s < NB; ++s) {
-    // L^{-1}, step k = s: rows i > k, columns c <= k:  X[i][c] -= l_ik X[k][c]
-    const int k = s;
-    const T x0 = X[k][c0], x1 = X[k][c1];
-    // U^{-1}, step q = NB-1-s: rows i < q, columns c >= q:  Y[i][c] -= (u_iq / u_qq) Y[q][c]
-    const int q = NB - 1 - s;
-    const T y0 = Y[q][c0], y1 = Y[q][c1], rq = rcp[q];
+    const int b = (s & 1) * NB, nb = NB - b;
+    const int k = s, q = NB - 1 - s;
+    const T xk0 = rx[b + c0], xk1 = rx[b + c1];
+    const T yq0 = ry[b + c0], yq1 = ry[b + c1];
+    const T rq = rcp[q];
 #pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-      const int i = g + NG * t;
-      if (i > k) {
-        const T l = D[i][k];
-        if (c0 <= k) X[i][c0] -= l * x0;
-        if (c1 <= k && c1 != c0) X[i][c1] -= l * x1;
-      }
-      if (i < q) {
-        const T u = D[i][q] * rq;
-        if (c0 >= q) Y[i][c0] -= u * y0;
-        if (c1 >= q && c1 != c0) Y[i][c1] -= u * y1;
+    for (int t = 0; t < RPW; ++t) {
+      const int i = i0 + t;
+      const T l = i > k ? D[i][k] : T(0);
+      const T v = i < q ? D[i][q] * rq : T(0);
+      x0[t] -= l * xk0;
+      x1[t] -= l * xk1;
+      y0[t] -= v * yq0;
+      y1[t] -= v * yq1;
+    }
+    if (s + 1 < NB) {
+      const int kn = k + 1, qn = q - 1;
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        if (i0 + t == kn) {
+          rx[nb + c0] = x0[t];
+          rx[nb + c1] = x1[t];
+        }
+        if (i0 + t == qn) {
+          ry[nb + c0] = y0[t];
+          ry[nb + c1] = y1[t];
+        }
       }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < NB * NB; e += NT) {
-    const int i = e / NB, j = e % NB;
-    inv[e] = X[i][j];
-    inv[NB * NB + e] = Y[i][j] * rcp[i];  // rows of U^{-1} take their pivot's reciprocal last
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {
+    const int i = i0 + t;
+    inv[i * NB + c0] = x0[t];
+    inv[i * NB + c1] = x1[t];
+    inv[NB * NB + i * NB + c0] = y0[t] * rcp[i];  // rows of U^{-1} take their pivot's reciprocal last
+    inv[NB * NB + i * NB + c1] = y1[t] * rcp[i];
   }
 }
 
 template <typename T, int NB, int NT>
 __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
-  constexpr int NP = NB / 2;
-  constexpr int NG = NT / NP;
-  constexpr int RPT = NB / NG;
-  static_assert(NT % NP == 0 && NB % NG == 0, "shape");
+  static_assert(NB == 64 && NT == 256, "one column pair per lane, 8 rows per warp");
+  constexpr int RPW = NB / (NT / 32);
   extern __shared__ __align__(16) unsigned char dsm[];
   T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
-  T(*Y)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + 2 * sizeof(T) * NB * (NB + 1));
-  __shared__ T rcp[NB];  // FP64 pivot reciprocals, rounded to T
+  T *buf = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
+  T *rowb = buf, *colb = buf + 2 * NB;  // double-buffered pivot row / column
+  __shared__ T rcp[NB];                 // pivot reciprocals
   __shared__ int bad;
-  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
-  const int c0 = p, c1 = NB - 1 - p;
-  for (int e = threadIdx.x; e < NB * NB; e += NT) {
-    const int i = e / NB, j = e % NB;
-    D[i][j] = (i < w && j < w) ? A.get(k0 + i, k0 + j) : (i == j ? T(1) : T(0));
-  }
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int c0 = lane, c1 = NB - 1 - lane, i0 = g * RPW;
+  stage_tile<NB, NT, NB + 1>(&D[0][0], [&](int i, int j) {
+    return (i < w && j < w) ? A.get(k0 + i, k0 + j) : (i == j ? T(1) : T(0));
+  });
   __syncthreads();
+  T v0[RPW], v1[RPW];
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {
+    v0[t] = D[i0 + t][c0];
+    v1[t] = D[i0 + t][c1];
+  }
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    rowb[j] = j > 0 ? D[0][j] : T(0);
+    colb[j] = j > 0 ? D[j][0] : T(0);
+  }
   if (threadIdx.x == 0) {
-    const double pv = (double)D[0][0];
-    rcp[0] = (T)(1.0 / pv);
-    bad = (!(pv != 0.0) || !isfinite(pv)) ? 0 : NB;
+    const T pv = D[0][0];
+    rcp[0] = pivot_rcp(pv);
+    bad = (w > 0 && pivot_bad(pv)) ? 0 : NB;
   }
   __syncthreads();
   for (int r = 0; r + 1 < NB; ++r) {
+    const int b = (r & 1) * NB, nb = NB - b;
     const T rc = rcp[r];
-    const T u0 = D[r][c0], u1 = D[r][c1];
+    const T u0 = rowb[b + c0], u1 = rowb[b + c1];
 #pragma unroll
-    for (int t = 0; t < RPT; ++t) {
-      const int i = g + NG * t;
-      if (i > r) {
-        const T l = D[i][r] * rc;  // Eq. 6a
-        if (c0 > r) D[i][c0] -= l * u0;  // Eq. 6c
-        if (c1 > r && c1 != c0) D[i][c1] -= l * u1;
+    for (int t = 0; t < RPW; ++t) {
+      const T l = colb[b + i0 + t] * rc;  // Eq. 6a (0 for rows <= r)
+      v0[t] -= l * u0;                    // Eq. 6c (u is 0 for columns <= r)
+      v1[t] -= l * u1;
+    }
+    // Publish row r+1 (right of its pivot), column r+1 (below it) and the pivot.
+    const int rn = r + 1;
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      if (i0 + t == rn) {
+        rowb[nb + c0] = c0 > rn ? v0[t] : T(0);
+        rowb[nb + c1] = c1 > rn ? v1[t] : T(0);
+        if (c0 == rn || c1 == rn) {
+          const T pv = c0 == rn ? v0[t] : v1[t];
+          rcp[rn] = pivot_rcp(pv);
+          if (rn < w && pivot_bad(pv)) atomicMin(&bad, rn);
+        }
       }
     }
-    // The owner of entry (r+1, r+1) has just produced the next pivot.
-    if (g == (r + 1) % NG && (c0 == r + 1 || c1 == r + 1)) {
-      const double pv = (double)D[r + 1][r + 1];
-      rcp[r + 1] = (T)(1.0 / pv);
-      if (r + 1 < w && (!(pv != 0.0) || !isfinite(pv))) atomicMin(&bad, r + 1);
+    if (c0 == rn || c1 == rn) {
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) colb[nb + i0 + t] = i0 + t > rn ? (c0 == rn ? v0[t] : v1[t]) : T(0);
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < NB * NB; e += NT) {  // multipliers in place (Eq. 6a)
-    const int i = e / NB, j = e % NB;
-    if (i > j) D[i][j] *= rcp[j];
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {  // multipliers in place (Eq. 6a)
+    const int i = i0 + t;
+    D[i][c0] = i > c0 ? v0[t] * rcp[c0] : v0[t];
+    D[i][c1] = i > c1 ? v1[t] * rcp[c1] : v1[t];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < NB * NB; e += NT) {
@@ -172,7 +235,7 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     if (i < w && j < w) A.put(k0 + i, k0 + j, D[i][j]);
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
-  if (inv) triangle_inverses<T, NB, NT>(D, X, Y, rcp, inv);
+  if (inv) triangle_inverses<T, NB, NT>(D, buf, rcp, inv);
 }
 
 // ---------------------------------------------------------------------------
@@ -193,11 +256,8 @@ __global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w
   const int64_t r0 = r_begin + (int64_t)blockIdx.x * NB;
   const int h = (int)min64(NB, r_end - r0);
   const T *uinv = inv + NB * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += 256) {
-    const int i = e / NB, k = e % NB;
-    Ui[i][k] = uinv[e];
-    At[i][k] = (i < h && k < w) ? A.get(r0 + i, k0 + k) : T(0);
-  }
+  stage_tile<NB, 256, NB + 1>(&Ui[0][0], [&](int i, int k) { return uinv[i * NB + k]; });
+  stage_tile<NB, 256, NB + 1>(&At[0][0], [&](int i, int k) { return (i < h && k < w) ? A.get(r0 + i, k0 + k) : T(0); });
   __syncthreads();
   const int i = threadIdx.x >> 2, jq = threadIdx.x & 3;
   T out[NB / 4];
@@ -238,11 +298,8 @@ __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h
   T(*Li)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
   const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
   const int wc = (int)min64(NB, c_end - c0);
-  for (int e = threadIdx.x; e < NB * NB; e += 256) {
-    const int k = e / NB, j = e % NB;
-    Li[k][j] = inv[e];
-    At[k][j] = (k < h && j < wc) ? A.get(r0 + k, c0 + j) : T(0);
-  }
+  stage_tile<NB, 256, NB + 1>(&Li[0][0], [&](int k, int j) { return inv[k * NB + j]; });
+  stage_tile<NB, 256, NB + 1>(&At[0][0], [&](int k, int j) { return (k < h && j < wc) ? A.get(r0 + k, c0 + j) : T(0); });
   __syncthreads();
   const int i = threadIdx.x >> 2, jq = threadIdx.x & 3;
   T out[NB / 4];

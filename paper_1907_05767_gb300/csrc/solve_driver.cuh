@@ -62,8 +62,8 @@ template <typename T, bool UPPER>
 ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
                       DevStatus *st, cudaStream_t s) {
   constexpr int RC = TrsvCfg<T>::RC;
-  constexpr size_t smem = trsvp_smem_bytes<T, kNB, RC>();
-  auto kern = k_trsv_persistent<T, kNB, RC, UPPER>;
+  constexpr size_t smem = trsvl_smem_bytes<T, kNB, RC>();
+  auto kern = k_trsv_left<T, kNB, RC, UPPER>;
   static int resident = [&] {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;

@@ -17,52 +17,57 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t n, T *dinv) {
   extern __shared__ __align__(16) unsigned char dsm[];
   T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
-  T(*Y)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + 2 * sizeof(T) * NB * (NB + 1));
+  T *buf = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
   __shared__ T rcp[NB];
   const int64_t i0 = (int64_t)blockIdx.x * NB;
   const int hb = (int)min64(NB, n - i0);
-  for (int e = threadIdx.x; e < NB * NB; e += 4 * NB) {
-    const int r = e / NB, k = e % NB;
-    D[r][k] = (r < hb && k < hb) ? F.get(i0 + r, i0 + k) : (r == k ? T(1) : T(0));
-  }
+  stage_tile<NB, 4 * NB, NB + 1>(&D[0][0], [&](int r, int k) {
+    return (r < hb && k < hb) ? F.get(i0 + r, i0 + k) : (r == k ? T(1) : T(0));
+  });
   __syncthreads();
-  for (int r = threadIdx.x; r < NB; r += 4 * NB) rcp[r] = (T)(1.0 / (double)D[r][r]);  // one FP64 division each
+  for (int r = threadIdx.x; r < NB; r += 4 * NB) rcp[r] = pivot_rcp(D[r][r]);
   __syncthreads();
-  triangle_inverses<T, NB, 4 * NB>(D, X, Y, rcp, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
+  triangle_inverses<T, NB, 4 * NB>(D, buf, rcp, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
 }
 
 // ---------------------------------------------------------------------------
 // Block substitution in one cooperative launch per triangle (Eq. 1: LY = B,
-// then UX = Y).  Steps s = 0..nblk-1 visit the row blocks in solve order
-// (increasing for L, decreasing for U); each chunk of RC right-hand sides is
-// an independent chain of CTAs.  CTA h of a chain owns the steps s = h (mod G)
-// and keeps those blocks of B up to date in global memory.  The critical path
-// is: block s published -> its owner-of-(s+1) folds it into block s+1 and
-// solves that block through the diagonal-block inverse (tile products, no
-// sequential chain) -> publishes.  So the owner of s+1 loads everything that
-// does not depend on block s (the coupling block of the factor, the inverse,
-// its own B block) before it waits, and folds block s into its other blocks
-// only after publishing.  Flags are per step; every wait is bounded and gives
-// up once the workspace status reports an error.  All CTAs must be
-// co-resident: the driver launches at most the occupancy limit, cooperatively.
-// Dynamic shared memory: trsvp_smem_bytes<T, NB, RC>().
+// then UX = Y), left-looking.  Steps t = 0..nblk-1 visit the row blocks in
+// solve order (increasing for L, decreasing for U); each chunk of RC
+// right-hand sides is an independent chain of CTAs.  CTA h of a chain owns
+// the steps t = h (mod G) and takes them in order: for its block t it folds
+// the published blocks s < t into a register accumulator, acc -= F(t,s) X_s,
+// in the order they were published, then X_t = D_t^{-1} acc (a tile product
+// with the diagonal-block inverse) and releases flag t.  Only the owner ever
+// touches block t of B, nothing is written back between folds, and a CTA
+// never works on a later block while its current one could advance, so the
+// critical path per step is: flag t-1 seen -> X_{t-1} read from L2 -> one
+// 64 x 64 x RC fold -> one 64 x 64 x RC solve -> store + release.  The next
+// factor tile is fetched into registers while the current fold runs (and
+// while the CTA waits).  Every wait is bounded and gives up once the
+// workspace status reports an error.  All CTAs must be co-resident: the driver
+// launches at most the occupancy limit, cooperatively.
+// Dynamic shared memory: trsvl_smem_bytes<T, NB, RC>().
 // ---------------------------------------------------------------------------
+template <typename T, int NB>
+__host__ __device__ constexpr int trsvl_stride() { return NB + 16 / (int)sizeof(T); }  // 16-byte rows
+
 template <typename T, int NB, int RC>
-constexpr size_t trsvp_smem_bytes() {
-  return sizeof(T) * (3 * NB * (RC + 1) + 2 * NB * (NB + 1));
+constexpr size_t trsvl_smem_bytes() {
+  return sizeof(T) * (2 * (size_t)NB * trsvl_stride<T, NB>() + 2 * (size_t)NB * (RC + 1));
 }
 
 template <typename T, int NB, int RC, bool UPPER>
 __global__ void __launch_bounds__(256)
-    k_trsv_persistent(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
-                      DevStatus *st) {
+    k_trsv_left(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags, DevStatus *st) {
+  constexpr int NT = 256, FS = trsvl_stride<T, NB>();
+  constexpr int PASS = NT / RC, OPT = NB / PASS, LPT = NB * NB / NT;
+  static_assert(NT % RC == 0 && NB % PASS == 0 && (NB * NB) % NT == 0, "shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*Y)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw);                           // block of step s
-  T(*acc)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
-  T(*Bo)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + 2 * sizeof(T) * NB * (RC + 1));  // own B block
-  T(*Fb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + 3 * sizeof(T) * NB * (RC + 1));
-  T(*Di)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * (3 * NB * (RC + 1) + NB * (NB + 1)));
+  T(*Fb)[FS] = reinterpret_cast<T(*)[FS]>(smem_raw);                               // F(t, s)
+  T(*Di)[FS] = reinterpret_cast<T(*)[FS]>(smem_raw + sizeof(T) * NB * FS);         // D_t^{-1}
+  T(*Xs)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + 2 * sizeof(T) * NB * FS);  // X_s
+  T(*Ac)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * (2 * NB * FS + NB * (RC + 1)));
   __shared__ int s_ok;
   if (st && st->done) return;  // refinement already converged
   const int nblk = ceil_div(n, NB);
@@ -73,100 +78,76 @@ __global__ void __launch_bounds__(256)
   const int c0 = chunk * RC, wc = min(RC, nrhs - c0);
   int *fl = flags + (int64_t)chunk * nblk;
   auto blk = [&](int s) { return UPPER ? nblk - 1 - s : s; };
-  // Steps s+1 .. s+reach depend on the block of step s (a band limits reach);
-  // at least step s+1, whose diagonal block is solved right after its fold.
+  // Blocks s >= t - reach couple into block t (a band limits reach).
   const int reach = (int)max64(1, min64((UPPER ? F.ku + NB - 1 : F.kl + NB - 1) / NB, (int64_t)nblk));
-  constexpr int PASS = 256 / RC;  // rows covered per pass of the thread block
   const int tc = threadIdx.x % RC, tr = threadIdx.x / RC;
 
-  auto load_f = [&](int s, int t) {  // Fb <- F(blk(t), blk(s))
+  T fr[LPT];  // factor tile in flight
+  auto fetch_f = [&](int t, int s) {
     const int64_t i0 = (int64_t)blk(t) * NB, j0 = (int64_t)blk(s) * NB;
     const int hi = (int)min64(NB, n - i0), hj = (int)min64(NB, n - j0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) {
-      const int r = e / NB, k = e % NB;
-      Fb[r][k] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+      const int e = threadIdx.x + NT * q, r = e / NB, k = e % NB;
+      fr[q] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
     }
   };
-  auto load_b = [&](int t) {  // Bo <- B_blk(t)
+
+  for (int t = h; t < nblk; t += G) {
     const int64_t i0 = (int64_t)blk(t) * NB;
     const int hi = (int)min64(NB, n - i0);
-    for (int r = tr; r < NB; r += PASS) Bo[r][tc] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
-  };
-  auto load_dinv = [&](int t) {
-    const T *di = dinv + (int64_t)blk(t) * 2 * NB * NB + (UPPER ? NB * NB : 0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) Di[e / NB][e % NB] = di[e];
-  };
-  auto fold = [&]() {  // acc <- Bo - Fb * Y
-    for (int r = tr; r < NB; r += PASS) {
-      T a = Bo[r][tc];
-#pragma unroll 16
-      for (int k = 0; k < NB; ++k) a -= Fb[r][k] * Y[k][tc];
-      acc[r][tc] = a;
+    const int sb = max(0, t - reach);
+    T acc[OPT];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int r = tr + PASS * q;
+      acc[q] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
     }
-  };
-  auto store_acc = [&](int t) {
-    const int64_t i0 = (int64_t)blk(t) * NB;
-    const int hi = (int)min64(NB, n - i0);
-    for (int r = tr; r < hi; r += PASS)
-      if (tc < wc) B[(i0 + r) * ldb + c0 + tc] = acc[r][tc];
-  };
-  // B_blk(t) = D^{-1} acc, then release flag t.
-  auto solve_publish = [&](int t) {
-    const int64_t i0 = (int64_t)blk(t) * NB;
-    const int hi = (int)min64(NB, n - i0);
-    for (int r = tr; r < hi; r += PASS) {
-      T a = T(0);
+    {
+      const T *di = dinv + (int64_t)blk(t) * 2 * NB * NB + (UPPER ? NB * NB : 0);
+      stage_tile<NB, NT, FS>(&Di[0][0], [&](int r, int k) { return di[r * NB + k]; });
+    }
+    if (sb < t) fetch_f(t, sb);
+    for (int s = sb; s < t; ++s) {
+      if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[s], 1, st, kSpinLimit, s);
+      __syncthreads();  // flag seen; the previous fold is done with Fb and Xs
+      if (!s_ok) return;
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        const int e = threadIdx.x + NT * q;
+        Fb[e / NB][e % NB] = fr[q];
+      }
+      {
+        const int64_t j0 = (int64_t)blk(s) * NB;
+        const int hj = (int)min64(NB, n - j0);
+        for (int k = tr; k < NB; k += PASS)
+          Xs[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
+      }
+      if (s + 1 < t) fetch_f(t, s + 1);
+      __syncthreads();
 #pragma unroll 16
-      for (int k = 0; k < NB; ++k) a += Di[r][k] * acc[k][tc];
-      if (tc < wc) B[(i0 + r) * ldb + c0 + tc] = a;
+      for (int k = 0; k < NB; ++k) {
+        const T xk = Xs[k][tc];
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) acc[q] -= Fb[tr + PASS * q][k] * xk;
+      }
+    }
+    // X_t = D_t^{-1} acc.  (Di and Ac are free: the previous block ended
+    // with a barrier after its solve.)
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) Ac[tr + PASS * q][tc] = acc[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int r = tr + PASS * q;
+      T x = T(0);
+#pragma unroll 16
+      for (int k = 0; k < NB; ++k) x += Di[r][k] * Ac[k][tc];
+      if (r < hi && tc < wc) B[(i0 + r) * ldb + c0 + tc] = x;
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) st_release(&fl[t], 1);
-  };
-
-  if (h == 0) {  // step 0: its block has no updates to receive
-    load_b(0);
-    load_dinv(0);
-    __syncthreads();
-    for (int r = tr; r < NB; r += PASS) acc[r][tc] = Bo[r][tc];
-    __syncthreads();
-    solve_publish(0);
-  }
-  for (int s = 0; s + 1 < nblk; ++s) {
-    const int last = (int)min64(nblk - 1, (int64_t)s + reach);
-    int t = s + 1 + (((h - (s + 1)) % G) + G) % G;  // first step > s owned by this CTA
-    if (t > last) continue;                          // nothing of ours depends on step s
-    const bool critical = t == s + 1;
-    if (critical) {  // independent of block s: fetch while its owner is still working
-      load_f(s, t);
-      load_b(t);
-      load_dinv(t);
-    }
-    if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[s], 1, st, kSpinLimit, s);
-    __syncthreads();
-    if (!s_ok) return;
-    {
-      const int64_t j0 = (int64_t)blk(s) * NB;
-      const int hj = (int)min64(NB, n - j0);
-      for (int k = tr; k < NB; k += PASS) Y[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
-    }
-    __syncthreads();
-    if (critical) {
-      fold();
-      __syncthreads();
-      solve_publish(t);  // every earlier step has already been folded into block t
-      t += G;
-    }
-    for (; t <= last; t += G) {
-      load_f(s, t);
-      load_b(t);
-      __syncthreads();
-      fold();
-      __syncthreads();
-      store_acc(t);
-      __syncthreads();
-    }
   }
 }
 
