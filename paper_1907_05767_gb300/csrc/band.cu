@@ -64,8 +64,8 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
   return EBV_OK;
 }
 
-// R = B - A X for a row-band A, double-float accumulation as in the dense
-// residual.  One warp per row; the lanes stride over the row's band.
+// R = B - A X for a row-band A, multi-word binary32 accumulation as in the
+// dense residual.  One warp per row; the lanes stride over the row's band.
 __global__ void __launch_bounds__(256)
     k_band_residual_df(const double *ab, int64_t ldab, int64_t n, int64_t kl, int64_t ku, const float *xhi,
                        const float *xlo, int nrhs, const double *B, int64_t ldb, double *R, int64_t ldr,

@@ -223,12 +223,14 @@ __device__ __forceinline__ void two_prod_f(float a, float b, float &p, float &e)
 // A double-float (h, l) pair is not enough: once a large term (the diagonal
 // of a dominant row) has entered, each TwoSum error of h is ~2^-25 |h|, the
 // low word grows to ~sqrt(k) 2^-25 |h| after k terms and its own binary32
-// rounding random-walks to ~1e-13 |h| and beyond.  TripleF gives every
-// first-order quantity an error-free level: the products go into h by TwoSum,
-// the TwoSum errors of h and the product errors / cross terms (both
-// ~2^-24 |a x|) go into m by TwoSum, and only second-order errors
-// (~2^-48 |partial sums|) reach the plain word l.  About 25 binary32
-// operations per multiply-add, with no FP64 instruction in the loop.
+// rounding random-walks to ~1e-13 |h| and beyond.  (Restarting the pair every
+// 16 terms and merging it into a triple still leaves ~2^-43 |h| in the block
+// that holds the large term.)  TripleF gives every first-order quantity an
+// error-free level: the products go into h by TwoSum, the TwoSum errors of h
+// and the product errors / cross terms (both ~2^-24 |a x|) go into m by
+// TwoSum, and only second-order errors (~2^-48 |partial sums|) reach the
+// plain word l.  About 25 binary32 operations per multiply-add, with no FP64
+// instruction in the loop.
 struct TripleF {
   float h, m, l;
   __device__ __forceinline__ void zero() { h = m = l = 0.f; }
@@ -256,21 +258,23 @@ struct TripleF {
   __device__ __forceinline__ double value() const { return (double)h + ((double)m + (double)l); }
 };
 
-// R = B - A X with A in FP64, evaluated in double-float arithmetic (pairs of
-// binary32 with error-free TwoSum / FMA-based TwoProduct, i.e. about 48
-// significant bits) so the FP64 ALU, ~75x slower than FP32 on GB300, is
-// touched once per output.  CTA tile: RB rows x RC right-hand sides; K staged
-// through shared memory in KC-wide slabs.  Also folds max_i |R_ic| per column
-// into rmax (as ordered bit patterns).
+// R = B - A X with A in FP64, evaluated in binary32 multi-word arithmetic
+// (TripleF above) so the FP64 ALU, ~75x slower than
+// FP32 on GB300, is touched once per output.  CTA tile: RB rows x RC
+// right-hand sides; K staged through shared memory in KC-wide slabs, the next
+// slab's loads in flight while the current one is consumed.  Also folds
+// max_i |R_ic| per column into rmax (as ordered bit patterns).
 template <int RB, int RC, int KC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_residual_df(const double *A, int64_t lda, int64_t n, const float *xhi, const float *xlo, int nrhs,
                   const double *B, int64_t ldb, double *R, int64_t ldr, unsigned long long *rmax,
                   const DevStatus *st) {
   constexpr int NT = 256;
   constexpr int ROWS_PER_PASS = NT / RC;
   constexpr int OPT = RB / ROWS_PER_PASS;  // outputs per thread
+  constexpr int LA = RB * KC / NT, LX = KC * RC / NT;
   static_assert(NT % RC == 0 && RB % ROWS_PER_PASS == 0, "shape");
+  static_assert(LA * NT == RB * KC && LX * NT == KC * RC, "slab must divide evenly");
   __shared__ float ah[RB][KC + 1], al[RB][KC + 1];
   __shared__ float xh[KC][RC + 1], xl[KC][RC + 1];
   __shared__ unsigned long long cmax[RC];
@@ -283,24 +287,40 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int q = 0; q < OPT; ++q) acc[q].zero();
   if (threadIdx.x < RC) cmax[threadIdx.x] = 0ull;
-  for (int64_t k0 = 0; k0 < n; k0 += KC) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < RB * KC; e += NT) {
-      const int i = e / KC, k = e % KC;
+  double pa[LA];
+  float pxh[LX], pxl[LX];
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int e = threadIdx.x + NT * u, i = e / KC, k = e % KC;
       const int64_t gi = r0 + i, gk = k0 + k;
-      float h = 0.f, l = 0.f;
-      if (gi < n && gk < n) split_f64(A[gi * lda + gk], h, l);
-      ah[i][k] = h;
-      al[i][k] = l;
+      pa[u] = (gi < n && gk < n) ? A[gi * lda + gk] : 0.0;
     }
-    for (int e = threadIdx.x; e < KC * RC; e += NT) {
-      const int k = e / RC, cc = e % RC;
+#pragma unroll
+    for (int u = 0; u < LX; ++u) {
+      const int e = threadIdx.x + NT * u, k = e / RC, cc = e % RC;
       const int64_t gk = k0 + k;
       const bool ok = gk < n && c0 + cc < nrhs;
-      xh[k][cc] = ok ? xhi[gk * nrhs + c0 + cc] : 0.f;
-      xl[k][cc] = ok ? xlo[gk * nrhs + c0 + cc] : 0.f;
+      pxh[u] = ok ? xhi[gk * nrhs + c0 + cc] : 0.f;
+      pxl[u] = ok ? xlo[gk * nrhs + c0 + cc] : 0.f;
+    }
+  };
+  fetch(0);
+  for (int64_t k0 = 0; k0 < n; k0 += KC) {
+    __syncthreads();  // the previous slab has been consumed
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int e = threadIdx.x + NT * u;
+      split_f64(pa[u], ah[e / KC][e % KC], al[e / KC][e % KC]);
+    }
+#pragma unroll
+    for (int u = 0; u < LX; ++u) {
+      const int e = threadIdx.x + NT * u;
+      xh[e / RC][e % RC] = pxh[u];
+      xl[e / RC][e % RC] = pxl[u];
     }
     __syncthreads();
+    if (k0 + KC < n) fetch(k0 + KC);
 #pragma unroll 4
     for (int k = 0; k < KC; ++k) {
       const float xhk = xh[k][c], xlk = xl[k][c];
