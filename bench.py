@@ -304,7 +304,8 @@ def run_gpu(args, rank, world, dist):
         pass
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_work, dom_cnt) = dom
-    roofline = roofline_for(dom_name, dom_ms, dom_work, dom_cnt, peaks, args)
+    roofline = roofline_for(dom_name, dom_ms, dom_work, dom_cnt, peaks, args,
+                            active=int(rep_np["iters"]) + 1 if dom_name == "residual" else None)
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_kstop > 0:
@@ -341,7 +342,7 @@ def run_gpu(args, rank, world, dist):
     return line
 
 
-def roofline_for(name, ms, work, cnt, peaks, args):
+def roofline_for(name, ms, work, cnt, peaks, args, active=None):
     if cnt == 0 or ms <= 0:
         return None
     per_launch_ms = ms / cnt
@@ -358,13 +359,18 @@ def roofline_for(name, ms, work, cnt, peaks, args):
                 "frac": achieved / peak, "traffic": None, "peak_source": src, "launches": cnt,
                 "avg_launch_ms": per_launch_ms}
     if name == "residual":
-        # double-float residual: ~12 FP32 instructions per multiply-add
-        peak = 75.1 * 2.0 / 12.0
-        achieved = work / (ms / 1e3) / 1e12
+        # Triple-binary32 residual: 25 FP32 instructions (FFMA/FADD/FMUL, one
+        # issue slot each) per FP64-accurate multiply-add, so the ALU bound is
+        # (75.1e12 / 2) FFMA/s / 25 * 2 flops = 75.1 / 25 TFLOP/s FP64-equivalent.
+        # Launches after the stop test has passed exit at once: only `active`
+        # of them evaluate a residual, each 2 n^2 nrhs flops.
+        peak = 75.1 / 25.0
+        act = active if active else cnt
+        achieved = (work / cnt) * act / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64-equiv)",
                 "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FFMA 75.1 TF/s / 6 (12 FP32 ops per emulated FP64 multiply-add)",
-                "launches": cnt, "avg_launch_ms": per_launch_ms}
+                "peak_source": "measured FFMA 75.1 TF/s / 25 (FP32 instructions per emulated FP64 multiply-add)",
+                "launches": act, "avg_launch_ms": ms / act}
     achieved = work / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 75.1, "unit": "TFLOP/s",
             "frac": achieved / 75.1, "traffic": None, "peak_source": "measured FFMA probe", "launches": cnt,

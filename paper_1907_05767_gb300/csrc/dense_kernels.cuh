@@ -76,34 +76,72 @@ struct Shadow {
 // Diagonal block: Doolittle on a w x w block (w <= NB = 64), one CTA of 256
 // threads, identity beyond w.  Equal bi-vectorised ownership (Eq. 7): lane p
 // of warp g holds, in registers, rows 8g .. 8g+7 of the column pair
-// {p, NB-1-p} -- one long and one short vector.  Step r needs only the pivot
-// row r and the column r, which their owners publish into double-buffered
-// shared vectors at the end of step r-1 (zero outside the active part, so
-// every thread runs the same unpredicated 16 multiply-adds per step), plus
-// the pivot's reciprocal: one barrier per step and no shared-memory traffic
-// on the block itself.  The multiplier of row i is formed on the fly as
+// {p, NB-1-p} -- one long and one short vector.  Step r needs the pivot row r
+// (published by its owner warp into a double-buffered shared vector, zero up
+// to the pivot, with the pivot's reciprocal: one barrier per step) and the
+// column r below the pivot, which every warp already holds in one lane and
+// broadcasts by shuffles.  The multiplier of row i is formed on the fly as
 // a_ir * (1/a_rr) and stored in place at the end (Eq. 6a); column r is never
-// updated after step r.  Then the two inverses (L11^{-1}, U11^{-1}) by the
-// same register-resident, one-barrier-per-step sweeps, written to
-// inv[0..NB*NB) and inv[NB*NB..2*NB*NB) (row-major).
+// updated after step r, and warps whose rows are all above the pivot skip the
+// step.  Then the two inverses (L11^{-1}, U11^{-1}) by register-resident,
+// one-barrier-per-step sweeps, written to inv[0..NB*NB) and
+// inv[NB*NB..2*NB*NB) (row-major).
 // Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
-constexpr size_t diag_smem_bytes() { return sizeof(T) * ((size_t)NB * (NB + 1) + 8 * (size_t)NB); }
+__host__ __device__ constexpr int diag_tstride() { return NB + 16 / (int)sizeof(T); }  // 16-byte rows
 
 template <typename T, int NB>
-constexpr size_t pair_smem_bytes() { return 2 * sizeof(T) * NB * (NB + 1); }
+constexpr size_t diag_smem_bytes() {
+  return sizeof(T) * ((size_t)NB * (NB + 1) + 2 * (size_t)NB * diag_tstride<T, NB>() + 4 * (size_t)NB);
+}
 
-// X = L^{-1} and Y = U^{-1} from the packed factors D (NB x NB in shared
-// memory, identity padded) and the pivot reciprocals rcp; ownership as in
-// the factorisation.  X: rows i > k take -l_ik * (row k of X), k = 0..NB-1.
-// Y: with V = U diag(1/u) (unit upper), rows i < q take -v_iq * (row q of Y),
-// q = NB-1..0, so Y = V^{-1} and U^{-1} = diag(1/u) Y.  buf: 4*NB elements
-// of shared scratch.  Writes inv (2 * NB * NB).
+template <typename T, int NB>
+constexpr size_t pair_smem_bytes() { return 2 * sizeof(T) * NB * diag_tstride<T, NB>(); }
+
+// Eight consecutive elements from 16-byte-aligned shared memory.
+__device__ __forceinline__ void ld8(const float *p, float (&o)[8]) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+  o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w, o[4] = b.x, o[5] = b.y, o[6] = b.z, o[7] = b.w;
+}
+__device__ __forceinline__ void ld8(const double *p, double (&o)[8]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[u];
+    o[2 * u] = a.x, o[2 * u + 1] = a.y;
+  }
+}
+
+// v[t] for a warp-uniform index t (a select chain: no local-memory array).
+template <typename T, int N>
+__device__ __forceinline__ T pick(const T (&v)[N], int t) {
+  T r = v[0];
+#pragma unroll
+  for (int u = 1; u < N; ++u) r = (u == t) ? v[u] : r;
+  return r;
+}
+
+// Transposed, masked copies of the packed factors for the inverse sweeps:
+// LT[k][i] = l_ik (i > k, else 0) and VT[q][i] = u_iq / u_qq (i < q, else 0).
 template <typename T, int NB, int NT>
-__device__ void triangle_inverses(T (*D)[NB + 1], T *buf, const T *rcp, T *inv) {
+__device__ __forceinline__ void masked_factor_copies(T (*D)[NB + 1], const T *rcp, T *LT, T *VT) {
+  constexpr int TS = diag_tstride<T, NB>();
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int k = e / NB, i = e % NB;
+    LT[k * TS + i] = i > k ? D[i][k] : T(0);
+    VT[k * TS + i] = i < k ? D[i][k] * rcp[k] : T(0);
+  }
+}
+
+// X = L^{-1} and Y = U^{-1} from LT, VT (above) and the pivot reciprocals;
+// ownership as in the factorisation.  X: rows i > k take -l_ik * (row k of X),
+// k = 0..NB-1.  Y: with V = U diag(1/u) (unit upper), rows i < q take
+// -v_iq * (row q of Y), q = NB-1..0, so Y = V^{-1} and U^{-1} = diag(1/u) Y.
+// buf: 4*NB elements of shared scratch.  Writes inv (2 * NB * NB).
+template <typename T, int NB, int NT>
+__device__ void triangle_inverses(const T *LT, const T *VT, T *buf, const T *rcp, T *inv) {
   static_assert(NB == 64 && NT == 256, "one column pair per lane, 8 rows per warp");
-  constexpr int RPW = NB / (NT / 32);
+  constexpr int RPW = NB / (NT / 32), TS = diag_tstride<T, NB>();
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int c0 = lane, c1 = NB - 1 - lane, i0 = g * RPW;
   T *rx = buf, *ry = buf + 2 * NB;  // double-buffered row k of X, row q of Y
@@ -123,29 +161,25 @@ __device__ void triangle_inverses(T (*D)[NB + 1], T *buf, const T *rcp, T *inv) 
     const int k = s, q = NB - 1 - s;
     const T xk0 = rx[b + c0], xk1 = rx[b + c1];
     const T yq0 = ry[b + c0], yq1 = ry[b + c1];
-    const T rq = rcp[q];
+    T l[RPW], v[RPW];
+    ld8(LT + k * TS + i0, l);
+    ld8(VT + q * TS + i0, v);
 #pragma unroll
     for (int t = 0; t < RPW; ++t) {
-      const int i = i0 + t;
-      const T l = i > k ? D[i][k] : T(0);
-      const T v = i < q ? D[i][q] * rq : T(0);
-      x0[t] -= l * xk0;
-      x1[t] -= l * xk1;
-      y0[t] -= v * yq0;
-      y1[t] -= v * yq1;
+      x0[t] -= l[t] * xk0;
+      x1[t] -= l[t] * xk1;
+      y0[t] -= v[t] * yq0;
+      y1[t] -= v[t] * yq1;
     }
     if (s + 1 < NB) {
       const int kn = k + 1, qn = q - 1;
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) {
-        if (i0 + t == kn) {
-          rx[nb + c0] = x0[t];
-          rx[nb + c1] = x1[t];
-        }
-        if (i0 + t == qn) {
-          ry[nb + c0] = y0[t];
-          ry[nb + c1] = y1[t];
-        }
+      if (kn / RPW == g) {
+        rx[nb + c0] = pick(x0, kn - i0);
+        rx[nb + c1] = pick(x1, kn - i0);
+      }
+      if (qn / RPW == g) {
+        ry[nb + c0] = pick(y0, qn - i0);
+        ry[nb + c1] = pick(y1, qn - i0);
       }
     }
     __syncthreads();
@@ -163,12 +197,14 @@ __device__ void triangle_inverses(T (*D)[NB + 1], T *buf, const T *rcp, T *inv) 
 template <typename T, int NB, int NT>
 __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
   static_assert(NB == 64 && NT == 256, "one column pair per lane, 8 rows per warp");
-  constexpr int RPW = NB / (NT / 32);
+  constexpr int RPW = NB / (NT / 32), TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
   T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T *buf = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
-  T *rowb = buf, *colb = buf + 2 * NB;  // double-buffered pivot row / column
-  __shared__ T rcp[NB];                 // pivot reciprocals
+  T *LT = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
+  T *VT = LT + NB * TS;
+  T *buf = VT + NB * TS;
+  T *rowb = buf;          // double-buffered pivot row
+  __shared__ T rcp[NB];   // pivot reciprocals
   __shared__ int bad;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int c0 = lane, c1 = NB - 1 - lane, i0 = g * RPW;
@@ -182,11 +218,7 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     v0[t] = D[i0 + t][c0];
     v1[t] = D[i0 + t][c1];
   }
-  if (threadIdx.x < NB) {
-    const int j = threadIdx.x;
-    rowb[j] = j > 0 ? D[0][j] : T(0);
-    colb[j] = j > 0 ? D[j][0] : T(0);
-  }
+  if (threadIdx.x < NB) rowb[threadIdx.x] = threadIdx.x > 0 ? D[0][threadIdx.x] : T(0);
   if (threadIdx.x == 0) {
     const T pv = D[0][0];
     rcp[0] = pivot_rcp(pv);
@@ -195,31 +227,30 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
   __syncthreads();
   for (int r = 0; r + 1 < NB; ++r) {
     const int b = (r & 1) * NB, nb = NB - b;
-    const T rc = rcp[r];
-    const T u0 = rowb[b + c0], u1 = rowb[b + c1];
+    if (i0 + RPW - 1 > r) {  // warp-uniform: some of my rows are below the pivot
+      const T rc = rcp[r];
+      const T u0 = rowb[b + c0], u1 = rowb[b + c1];  // 0 for columns <= r
+      const int src = r < 32 ? r : NB - 1 - r;      // lane holding column r
+      const bool lo = r < 32;
 #pragma unroll
-    for (int t = 0; t < RPW; ++t) {
-      const T l = colb[b + i0 + t] * rc;  // Eq. 6a (0 for rows <= r)
-      v0[t] -= l * u0;                    // Eq. 6c (u is 0 for columns <= r)
-      v1[t] -= l * u1;
-    }
-    // Publish row r+1 (right of its pivot), column r+1 (below it) and the pivot.
-    const int rn = r + 1;
-#pragma unroll
-    for (int t = 0; t < RPW; ++t) {
-      if (i0 + t == rn) {
-        rowb[nb + c0] = c0 > rn ? v0[t] : T(0);
-        rowb[nb + c1] = c1 > rn ? v1[t] : T(0);
+      for (int t = 0; t < RPW; ++t) {
+        T l = __shfl_sync(0xffffffffu, lo ? v0[t] : v1[t], src) * rc;  // Eq. 6a
+        if (i0 <= r) l = (i0 + t > r) ? l : T(0);                       // the warp holding row r
+        v0[t] -= l * u0;                                                 // Eq. 6c
+        v1[t] -= l * u1;
+      }
+      // Publish row r+1 right of its pivot, and the pivot's reciprocal.
+      const int rn = r + 1;
+      if (rn / RPW == g) {
+        const T a0 = pick(v0, rn - i0), a1 = pick(v1, rn - i0);
+        rowb[nb + c0] = c0 > rn ? a0 : T(0);
+        rowb[nb + c1] = c1 > rn ? a1 : T(0);
         if (c0 == rn || c1 == rn) {
-          const T pv = c0 == rn ? v0[t] : v1[t];
+          const T pv = c0 == rn ? a0 : a1;
           rcp[rn] = pivot_rcp(pv);
           if (rn < w && pivot_bad(pv)) atomicMin(&bad, rn);
         }
       }
-    }
-    if (c0 == rn || c1 == rn) {
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) colb[nb + i0 + t] = i0 + t > rn ? (c0 == rn ? v0[t] : v1[t]) : T(0);
     }
     __syncthreads();
   }
@@ -235,7 +266,53 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     if (i < w && j < w) A.put(k0 + i, k0 + j, D[i][j]);
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
-  if (inv) triangle_inverses<T, NB, NT>(D, buf, rcp, inv);
+  if (inv) {
+    masked_factor_copies<T, NB, NT>(D, rcp, LT, VT);
+    __syncthreads();
+    triangle_inverses<T, NB, NT>(LT, VT, buf, rcp, inv);
+  }
+}
+
+// L21 = A21 U11^{-1} and U12 = L11^{-1} A12 are 64 x 64 x 64 tile products
+// against the diagonal-block inverses.  tile_product: C = P Q for P, Q in
+// shared memory (row stride TS, 16-byte rows); thread (ti, tj) accumulates
+// rows ti + 16a (a < 4) by the four consecutive columns 4tj .. 4tj+3, so each
+// k costs four broadcast loads of P, one vector load of Q and 16 fused
+// multiply-adds.  The result goes back to shared memory (over Q's buffer
+// once every thread is done reading).
+template <typename T, int NB, int TS>
+__device__ __forceinline__ void tile_product(const T *P, T *Q) {
+  static_assert(NB == 64, "tile mapping assumes 64 x 64 and 256 threads");
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  T c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) c[a][b] = T(0);
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    T q[4];
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(Q + k * TS + 4 * tj);
+      q[0] = v.x, q[1] = v.y, q[2] = v.z, q[3] = v.w;
+    } else {
+      const double2 v0 = *reinterpret_cast<const double2 *>(Q + k * TS + 4 * tj);
+      const double2 v1 = *reinterpret_cast<const double2 *>(Q + k * TS + 4 * tj + 2);
+      q[0] = v0.x, q[1] = v0.y, q[2] = v1.x, q[3] = v1.y;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const T p = P[(ti + 16 * a) * TS + k];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) c[a][b] += p * q[b];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Q[(ti + 16 * a) * TS + 4 * tj + b] = c[a][b];
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -250,35 +327,24 @@ template <typename T, typename SH, int NB>
 __global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w, int64_t r_begin, int64_t r_end,
                                                  const T *inv, Shadow<SH> sh) {
   static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
-  T(*At)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T(*Ui)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  T *At = reinterpret_cast<T *>(dsm);
+  T *Ui = At + NB * TS;
   const int64_t r0 = r_begin + (int64_t)blockIdx.x * NB;
   const int h = (int)min64(NB, r_end - r0);
   const T *uinv = inv + NB * NB;
-  stage_tile<NB, 256, NB + 1>(&Ui[0][0], [&](int i, int k) { return uinv[i * NB + k]; });
-  stage_tile<NB, 256, NB + 1>(&At[0][0], [&](int i, int k) { return (i < h && k < w) ? A.get(r0 + i, k0 + k) : T(0); });
+  stage_tile<NB, 256, TS>(Ui, [&](int i, int k) { return uinv[i * NB + k]; });
+  stage_tile<NB, 256, TS>(At, [&](int i, int k) { return (i < h && k < w) ? A.get(r0 + i, k0 + k) : T(0); });
   __syncthreads();
-  const int i = threadIdx.x >> 2, jq = threadIdx.x & 3;
-  T out[NB / 4];
-#pragma unroll
-  for (int q = 0; q < NB / 4; ++q) out[q] = T(0);
-#pragma unroll 8
-  for (int k = 0; k < NB; ++k) {
-    const T a = At[i][k];
-#pragma unroll
-    for (int q = 0; q < NB / 4; ++q) out[q] += a * Ui[k][jq + 4 * q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NB / 4; ++q) At[i][jq + 4 * q] = out[q];
-  __syncthreads();
+  tile_product<T, NB, TS>(At, Ui);  // Ui <- At * Ui
   const float s = sh.lb ? sh.scale[0] : 1.f;
   for (int e = threadIdx.x; e < NB * NB; e += 256) {
     const int ii = e / NB, k = e % NB;
     if (ii < h && k < w) {
-      A.put(r0 + ii, k0 + k, At[ii][k]);
-      if (sh.lb) sh.lb[(r0 + ii) * sh.ld + k0 + k] = from_float<SH>((float)At[ii][k] * s);
+      const T v = Ui[ii * TS + k];
+      A.put(r0 + ii, k0 + k, v);
+      if (sh.lb) sh.lb[(r0 + ii) * sh.ld + k0 + k] = from_float<SH>((float)v * s);
     }
   }
 }
@@ -293,37 +359,25 @@ template <typename T, typename SH, int NB>
 __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h, int64_t c_begin, int64_t c_end,
                                                  const T *inv, Shadow<SH> sh) {
   static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
-  T(*At)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T(*Li)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm + sizeof(T) * NB * (NB + 1));
+  T *At = reinterpret_cast<T *>(dsm);
+  T *Li = At + NB * TS;
   const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
   const int wc = (int)min64(NB, c_end - c0);
-  stage_tile<NB, 256, NB + 1>(&Li[0][0], [&](int k, int j) { return inv[k * NB + j]; });
-  stage_tile<NB, 256, NB + 1>(&At[0][0], [&](int k, int j) { return (k < h && j < wc) ? A.get(r0 + k, c0 + j) : T(0); });
+  stage_tile<NB, 256, TS>(Li, [&](int k, int j) { return inv[k * NB + j]; });
+  stage_tile<NB, 256, TS>(At, [&](int k, int j) { return (k < h && j < wc) ? A.get(r0 + k, c0 + j) : T(0); });
   __syncthreads();
-  const int i = threadIdx.x >> 2, jq = threadIdx.x & 3;
-  T out[NB / 4];
-#pragma unroll
-  for (int q = 0; q < NB / 4; ++q) out[q] = T(0);
-#pragma unroll 8
-  for (int k = 0; k < NB; ++k) {
-    const T l = Li[i][k];
-#pragma unroll
-    for (int q = 0; q < NB / 4; ++q) out[q] += l * At[k][jq + 4 * q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NB / 4; ++q) At[i][jq + 4 * q] = out[q];
-  __syncthreads();
+  tile_product<T, NB, TS>(Li, At);  // At <- Li * At
   for (int e = threadIdx.x; e < NB * NB; e += 256) {
     const int k = e / NB, j = e % NB;
-    if (k < h && j < wc) A.put(r0 + k, c0 + j, At[k][j]);
+    if (k < h && j < wc) A.put(r0 + k, c0 + j, At[k * TS + j]);
   }
   if (sh.ut) {
     const float s = sh.scale[1];
     for (int e = threadIdx.x; e < NB * NB; e += 256) {
       const int j = e / NB, k = e % NB;
-      if (k < h && j < wc) sh.ut[(c0 + j) * sh.ld + r0 + k] = from_float<SH>((float)At[k][j] * s);
+      if (k < h && j < wc) sh.ut[(c0 + j) * sh.ld + r0 + k] = from_float<SH>((float)At[k * TS + j] * s);
     }
   }
 }

@@ -17,7 +17,9 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t n, T *dinv) {
   extern __shared__ __align__(16) unsigned char dsm[];
   T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T *buf = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
+  T *LT = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
+  T *VT = LT + NB * diag_tstride<T, NB>();
+  T *buf = VT + NB * diag_tstride<T, NB>();
   __shared__ T rcp[NB];
   const int64_t i0 = (int64_t)blockIdx.x * NB;
   const int hb = (int)min64(NB, n - i0);
@@ -27,7 +29,9 @@ __global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t 
   __syncthreads();
   for (int r = threadIdx.x; r < NB; r += 4 * NB) rcp[r] = pivot_rcp(D[r][r]);
   __syncthreads();
-  triangle_inverses<T, NB, 4 * NB>(D, buf, rcp, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
+  masked_factor_copies<T, NB, 4 * NB>(D, rcp, LT, VT);
+  __syncthreads();
+  triangle_inverses<T, NB, 4 * NB>(LT, VT, buf, rcp, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
 }
 
 // ---------------------------------------------------------------------------
