@@ -171,6 +171,13 @@ struct Factorizer {
                                                                                          leaf_inv(r0), sh);
       return launch_ok();
     }
+    if (h <= kTrsmMaxBlocks * kNB) {
+      prof::Scope ps(s, prof::kPanel, 1.0 * h * h * (ch - cl));
+      k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks>
+          <<<ceil_div(ch - cl, kNB), 256, trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>(), s>>>(A, r0, (int)h, cl, ch,
+                                                                                                 inv, sh);
+      return launch_ok();
+    }
     const int64_t h1 = split(h);
     EBV_TRY(trsm_ll(r0, h1, cl, ch));
     EBV_TRY(gemm(r0 + h1, cl, r0, h - h1, ch - cl, h1));

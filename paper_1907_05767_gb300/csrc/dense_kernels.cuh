@@ -274,21 +274,16 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
 }
 
 // L21 = A21 U11^{-1} and U12 = L11^{-1} A12 are 64 x 64 x 64 tile products
-// against the diagonal-block inverses.  tile_product: C = P Q for P, Q in
+// against the diagonal-block inverses.  tile_fma: c +/-= P Q for P, Q in
 // shared memory (row stride TS, 16-byte rows); thread (ti, tj) accumulates
 // rows ti + 16a (a < 4) by the four consecutive columns 4tj .. 4tj+3, so each
 // k costs four broadcast loads of P, one vector load of Q and 16 fused
-// multiply-adds.  The result goes back to shared memory (over Q's buffer
-// once every thread is done reading).
-template <typename T, int NB, int TS>
-__device__ __forceinline__ void tile_product(const T *P, T *Q) {
+// multiply-adds.  tile_product: Q <- P Q (the result goes back over Q's
+// buffer once every thread is done reading).
+template <typename T, int NB, int TS, bool SUB>
+__device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[4][4]) {
   static_assert(NB == 64, "tile mapping assumes 64 x 64 and 256 threads");
   const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
-  T c[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) c[a][b] = T(0);
 #pragma unroll 8
   for (int k = 0; k < NB; ++k) {
     T q[4];
@@ -304,14 +299,36 @@ __device__ __forceinline__ void tile_product(const T *P, T *Q) {
     for (int a = 0; a < 4; ++a) {
       const T p = P[(ti + 16 * a) * TS + k];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) c[a][b] += p * q[b];
+      for (int b = 0; b < 4; ++b) c[a][b] = SUB ? c[a][b] - p * q[b] : c[a][b] + p * q[b];
     }
   }
-  __syncthreads();
+}
+template <typename T, int TS>
+__device__ __forceinline__ void tile_regs(const T *S, T (&c)[4][4]) {
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) Q[(ti + 16 * a) * TS + 4 * tj + b] = c[a][b];
+    for (int b = 0; b < 4; ++b) c[a][b] = S[(ti + 16 * a) * TS + 4 * tj + b];
+}
+template <typename T, int TS>
+__device__ __forceinline__ void tile_put(T *S, const T (&c)[4][4]) {
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) S[(ti + 16 * a) * TS + 4 * tj + b] = c[a][b];
+}
+template <typename T, int NB, int TS>
+__device__ __forceinline__ void tile_product(const T *P, T *Q) {
+  T c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) c[a][b] = T(0);
+  tile_fma<T, NB, TS, false>(P, Q, c);
+  __syncthreads();
+  tile_put<T, TS>(Q, c);
   __syncthreads();
 }
 
@@ -382,6 +399,68 @@ __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h
   }
 }
 
+// ---------------------------------------------------------------------------
+// U12 = L11^{-1} A12 for h <= MAXB * NB rows in one launch (Eq. 6b for the
+// U vectors of several leaf blocks at once): a left-looking blocked forward
+// substitution over the 64-row blocks of L11, one 64-column strip per CTA.
+// Block j: acc = A_j - sum_{i<j} L_ji U_i (the finished U_i stay in shared
+// memory), U_j = L_jj^{-1} acc through the leaf's inverse; all in the
+// working precision.  Replaces the recursive split of small TRSMs (a leaf
+// launch and a low-precision GEMM per level) by one launch.  Also writes the
+// scaled low-precision shadow of U^T.
+// Dynamic shared memory: trsm_multi_smem_bytes<T, NB, MAXB>().
+// ---------------------------------------------------------------------------
+template <typename T, int NB, int MAXB>
+constexpr size_t trsm_multi_smem_bytes() { return sizeof(T) * (MAXB + 2) * (size_t)NB * diag_tstride<T, NB>(); }
+
+template <typename T, typename SH, int NB, int MAXB>
+__global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0, int h, int64_t c_begin,
+                                                       int64_t c_end, const T *inv, Shadow<SH> sh) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>();
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T *U = reinterpret_cast<T *>(dsm);  // MAXB finished / current U blocks
+  T *Lt = U + MAXB * NB * TS;         // L_ji
+  T *Li = Lt + NB * TS;               // L_jj^{-1}
+  const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
+  const int wc = (int)min64(NB, c_end - c0);
+  const int nbk = ceil_div(h, NB);
+  for (int j = 0; j < nbk; ++j) {
+    const int64_t rj = r0 + (int64_t)j * NB;
+    const int hj = min(NB, h - j * NB);
+    T *Uj = U + j * NB * TS;
+    const T *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
+    stage_tile<NB, 256, TS>(Uj, [&](int k, int c) { return (k < hj && c < wc) ? A.get(rj + k, c0 + c) : T(0); });
+    stage_tile<NB, 256, TS>(Li, [&](int k, int c) { return linv[k * NB + c]; });
+    __syncthreads();
+    T acc[4][4];
+    tile_regs<T, TS>(Uj, acc);
+    for (int i = 0; i < j; ++i) {
+      const int64_t ri = r0 + (int64_t)i * NB;
+      stage_tile<NB, 256, TS>(Lt, [&](int k, int c) { return k < hj ? A.get(rj + k, ri + c) : T(0); });
+      __syncthreads();
+      tile_fma<T, NB, TS, true>(Lt, U + i * NB * TS, acc);
+      __syncthreads();
+    }
+    tile_put<T, TS>(Uj, acc);
+    __syncthreads();
+    tile_product<T, NB, TS>(Li, Uj);  // U_j = L_jj^{-1} acc
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int k = e / NB, c = e % NB;
+      if (k < hj && c < wc) A.put(rj + k, c0 + c, Uj[k * TS + c]);
+    }
+    if (sh.ut) {
+      const float s = sh.scale[1];
+      for (int e = threadIdx.x; e < NB * NB; e += 256) {
+        const int c = e / NB, k = e % NB;
+        if (k < hj && c < wc) sh.ut[(c0 + c) * sh.ld + rj + k] = from_float<SH>((float)Uj[k * TS + c] * s);
+      }
+    }
+  }
+}
+
+constexpr int kTrsmMaxBlocks = 4;  // rows of the one-launch TRSM: up to 4 leaves
+
 // Opt the leaf kernels into more than 48 KB of dynamic shared memory (FP64
 // tiles need 66.5 KB); once per process and instantiation.
 template <typename T, typename SH>
@@ -395,6 +474,10 @@ ebv_status_t prepare_leaf_kernels() {
       e = cudaFuncSetAttribute(k_trsm_ru<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_trsm_ll<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>());
     return e;
   }();
   return err == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
