@@ -243,7 +243,7 @@ EBV_API ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs, c
  * to start at zero): calls whose work overlaps on the GPU (other streams,
  * other host threads without ordering) race and give undefined results.
  */
-#define EBV_STATIC_SCRATCH_BYTES ((size_t)9 << 20)
+#define EBV_STATIC_SCRATCH_BYTES ((size_t)12 << 20)
 #define EBV_STATIC_MAX_N 4096
 #define EBV_STATIC_MAX_NRHS 32
 EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu,

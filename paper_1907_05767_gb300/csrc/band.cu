@@ -133,8 +133,10 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
   if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
   EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
   if (n == 0 || nrhs == 0) return EBV_OK;
-  auto residual = [&](const float *xhi, const float *xlo, const double *bs, double *r, unsigned long long *rmax,
-                      DevStatus *st) -> ebv_status_t {
+  auto residual = [&](const double *x, int64_t ldx, float *xhi, float *xlo, const double *bs, double *r,
+                      unsigned long long *rmax, DevStatus *st, bool) -> ebv_status_t {
+    k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldx, n, (int)nrhs, xhi, xlo, st);
+    EBV_TRY(launch_ok());
     prof::Scope ps(s, prof::kResidual, 2.0 * n * (d->kl + d->ku + 1) * nrhs);
     k_band_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(a_orig, d->ld, n, d->kl, d->ku, xhi, xlo, (int)nrhs, bs,
                                                        nrhs, r, nrhs, rmax, st);

@@ -221,7 +221,7 @@ DenseFactorLayout factor_layout(int64_t n, ebv_prec_t prec) {
 
 size_t dense_factor_ws(int64_t n, ebv_prec_t prec) { return factor_layout(n, prec).total; }
 size_t dense_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
-  return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
+  return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4, true).total;
 }
 
 ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
@@ -269,23 +269,34 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   return f.rlu(0, n);
 }
 
+// R = B - A X for the dense refinement: on the tensor cores (exact digit
+// splitting) where TMA is available, else the triple-binary32 SIMT kernel.
+static ebv_status_t dense_residual(const double *a, int64_t lda, int64_t n, const double *x, int64_t ldx, int64_t nrhs,
+                            const double *b, double *r, unsigned long long *rmax, char *w, const DenseSolveLayout &L,
+                            bool first, DevStatus *st, cudaStream_t s) {
+  if (tc_available())
+    return residual_tc(a, lda, n, x, ldx, nrhs, b, nrhs, r, nrhs, rmax, w + L.tcres, !first, st, s);
+  float *xhi = (float *)(w + L.xhi), *xlo = (float *)(w + L.xlo);
+  k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldx, n, (int)nrhs, xhi, xlo, st);
+  EBV_TRY(launch_ok());
+  constexpr int RB = 32, RC = 32, KC = 32;
+  dim3 grid(ceil_div(n, RB), ceil_div(nrhs, RC));
+  prof::Scope ps(s, prof::kResidual, 2.0 * n * n * nrhs);
+  k_residual_df<RB, RC, KC><<<grid, 256, 0, s>>>(a, lda, n, xhi, xlo, (int)nrhs, b, nrhs, r, nrhs, rmax, st);
+  return launch_ok();
+}
+
 // R = B - A X with the refinement's residual kernel (testing hook).
 ebv_status_t debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b, int64_t nrhs,
                             double *r, void *ws, size_t ws_bytes, cudaStream_t s) {
-  const DenseSolveLayout L = solve_layout(n, nrhs, 8);
+  const DenseSolveLayout L = solve_layout(n, nrhs, 8, true);
   if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
   char *w = (char *)ws;
   DevStatus *st = (DevStatus *)w;
   EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
-  float *xhi = (float *)(w + L.xhi), *xlo = (float *)(w + L.xlo);
   unsigned long long *rmax = (unsigned long long *)(w + L.rmax);
   EBV_CU(cudaMemsetAsync(rmax, 0, nrhs * 8, s));
-  k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, nrhs, n, (int)nrhs, xhi, xlo, st);
-  EBV_TRY(launch_ok());
-  constexpr int RB = 32, RC = 32, KC = 32;
-  dim3 grid(ceil_div(n, RB), ceil_div(nrhs, RC));
-  k_residual_df<RB, RC, KC><<<grid, 256, 0, s>>>(a, lda, n, xhi, xlo, (int)nrhs, b, nrhs, r, nrhs, rmax, st);
-  return launch_ok();
+  return dense_residual(a, lda, n, x, nrhs, nrhs, b, r, rmax, w, L, true, st, s);
 }
 
 ebv_status_t dense_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
@@ -293,19 +304,14 @@ ebv_status_t dense_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, c
                          size_t ws_bytes, cudaStream_t s) {
   const int64_t n = d->n;
   const bool fp64 = prec == EBV_FP64;
-  const DenseSolveLayout L = solve_layout(n, nrhs, fp64 ? 8 : 4);
+  const DenseSolveLayout L = solve_layout(n, nrhs, fp64 ? 8 : 4, true);
   if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
   EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
   if (n == 0 || nrhs == 0) return EBV_OK;
   char *w = (char *)ws;
-  auto residual = [&](const float *xhi, const float *xlo, const double *bs, double *r, unsigned long long *rmax,
-                      DevStatus *st) -> ebv_status_t {
-    constexpr int RB = 32, RC = 32, KC = 32;
-    dim3 grid(ceil_div(n, RB), ceil_div(nrhs, RC));
-    prof::Scope ps(s, prof::kResidual, 2.0 * n * n * nrhs);
-    k_residual_df<RB, RC, KC><<<grid, 256, 0, s>>>(a_orig, d->ld, n, xhi, xlo, (int)nrhs, bs, nrhs, r, nrhs, rmax,
-                                                    st);
-    return launch_ok();
+  auto residual = [&](const double *x, int64_t ldx, float *, float *, const double *bs, double *r,
+                      unsigned long long *rmax, DevStatus *st, bool first) -> ebv_status_t {
+    return dense_residual(a_orig, d->ld, n, x, ldx, nrhs, bs, r, rmax, w, L, first, st, s);
   };
   const bool b_double = prec != EBV_FP32;
   if (fp64)

@@ -1,6 +1,7 @@
 // Internal interfaces between the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -41,6 +42,18 @@ ebv_status_t tc_update(int op, float *C, int64_t ldc, const void *lb, const void
                        const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
                        DevStatus *st, cudaStream_t s);
 bool tc_available();
+// 2-D tensor map of a bfloat16 matrix (cols contiguous, row stride ld_elems)
+// with the given box and swizzle (128, 64, 32 or 0 bytes).
+bool make_map_bf16(CUtensorMap *map, const void *base, int64_t cols, int64_t rows, int64_t ld_elems, int box_cols,
+                   int box_rows, int swizzle_bytes);
+
+// FP64-accurate R = B - A X on the tensor cores (exact digit splitting).
+// ws: residual_tc_ws(n, nrhs) bytes; rows_ready: the per-row exponents of A
+// are already in ws from an earlier call with the same A.
+size_t residual_tc_ws(int64_t n, int64_t nrhs);
+ebv_status_t residual_tc(const double *A, int64_t lda, int64_t n, const double *X, int64_t ldx, int64_t nrhs,
+                         const double *B, int64_t ldb, double *R, int64_t ldr, unsigned long long *rmax, void *ws,
+                         bool rows_ready, DevStatus *st, cudaStream_t s);
 ebv_status_t simt_update(int op, float *C, int64_t ldc, const void *lb, const void *ut, int64_t ldsh,
                          const float *scale, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K,
                          cudaStream_t s);

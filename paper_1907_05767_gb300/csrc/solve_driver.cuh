@@ -18,12 +18,13 @@ struct TrsvCfg {
 };
 
 struct DenseSolveLayout {
-  size_t dinv, flags, bsave, r, corr, xhi, xlo, rmax, bmax, total;
+  size_t dinv, flags, bsave, r, corr, xhi, xlo, rmax, bmax, tcres, total;
 };
 
 // Solve workspace: status block, inverses of the diagonal blocks of both
-// factors, per-step flags of the two substitutions, refinement buffers.
-DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize) {
+// factors, per-step flags of the two substitutions, refinement buffers (and,
+// for the dense path, the tensor-core residual's exponents and digit planes).
+DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize, bool tc_residual = false) {
   DenseSolveLayout L{};
   size_t off = kStatusBytes;
   const size_t nn = (size_t)n * (size_t)std::max<int64_t>(nrhs, 1);
@@ -38,6 +39,7 @@ DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize) {
   L.xlo = off; off = align256(off + nn * 4);
   L.rmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
   L.bmax = off; off = align256(off + (size_t)std::max<int64_t>(nrhs, 1) * 8);
+  L.tcres = off; off = align256(off + (tc_residual ? residual_tc_ws(n, std::max<int64_t>(nrhs, 1)) : 0));
   L.total = off;
   return L;
 }
@@ -143,9 +145,7 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
   const int max_iter = std::max(0, refine->max_iter);
   for (int it = 0; it <= max_iter; ++it) {
     EBV_CU(cudaMemsetAsync(rmax, 0, nrhs * 8, s));
-    k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, n, nr, xhi, xlo, st);
-    EBV_TRY(launch_ok());
-    EBV_TRY(residual(xhi, xlo, bsave, r, rmax, st));
+    EBV_TRY(residual(x, ldb, xhi, xlo, bsave, r, rmax, st, it == 0));
     k_ir_check<<<1, 1, 0, s>>>(rmax, bmax, nr, it, max_iter, refine->tol, st, rep);
     EBV_TRY(launch_ok());
     if (it == max_iter) break;

@@ -1,7 +1,9 @@
-"""The refinement residual (double-float evaluation of B - A X) against the
-oracle's Dot2 residual.  Bound: the products are exact, the dropped and rounded
-low-order terms are each below 2^-47 |a_ij x_j|, so |r_dev - r| stays within
-~2^-44 * sum_j |a_ij x_j| (a few units of the FP64 working precision)."""
+"""The refinement residual B - A X (tensor-core evaluation by exact digit
+splitting) against the oracle's Dot2 residual.  Bound: every digit product and
+every 1024-column partial sum is exact; what is dropped (digit pairs of weight
+below 2^-60 and the fixed-point truncation of A and X at 2^-59 of their row /
+column scale) stays far below 2^-44 * sum_j |a_ij x_j| for these
+diagonally dominant rows, i.e. a few units of the FP64 working precision."""
 import numpy as np
 import pytest
 import torch
