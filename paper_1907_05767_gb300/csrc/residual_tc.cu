@@ -23,11 +23,12 @@
 // needs for the systems it targets (rows whose largest entry is comparable
 // to their dot product, as in diagonally dominant A).
 //
-// Kernel (one CTA per 128 rows x 32 right-hand sides, 13 warps):
-//   warps 5..12  convert: FP64 tile of A (128 x 32 per stage) -> ten digit
-//                planes in shared memory, 64-byte swizzled K-major rows;
-//   warp 4       allocates TMEM, TMA-loads the ten digit planes of X for the
-//                stage, issues the 110 MMAs (M=128, N=32, K=16) per stage;
+// Kernel (one CTA per 128 rows x 32 right-hand sides, 21 warps):
+//   warps 5..20  convert: FP64 tile of A (128 x 32 per stage) -> ten digit
+//                planes in shared memory, 64-byte swizzled K-major rows
+//                (their first thread also TMA-loads the stage's X planes);
+//   warp 4       allocates TMEM and issues, per stage and A digit, one MMA
+//                over all its X digits (M=128, N<=256, K=16: 24 per stage);
 //   warps 0..3   drain the ten diagonals every 1024 columns (TMEM lane =
 //                row) and write R = B - A X and the column maxima of |R|.
 // Two stages of 100 KB; every mbarrier wait is bounded.
@@ -51,18 +52,20 @@ constexpr int RT_S = 10;        // digit planes of A and of X
 constexpr int RT_D = 10;        // diagonals s + t = 0 .. RT_D-1
 constexpr int RT_CHUNK = 1024;  // columns per exact TMEM accumulation
 constexpr int RT_STAGES = 2;
-constexpr int RT_EPI_WARPS = 4, RT_MMA_WARP = 4, RT_CONV_WARP0 = 5, RT_CONV_WARPS = 8;
+constexpr int RT_EPI_WARPS = 4, RT_MMA_WARP = 4, RT_CONV_WARP0 = 5, RT_CONV_WARPS = 16;
 constexpr int RT_THREADS = 32 * (RT_CONV_WARP0 + RT_CONV_WARPS);
 constexpr int RT_CONV_THREADS = 32 * RT_CONV_WARPS;
+constexpr int RT_JOBS = RT_M * (RT_K / 8) / RT_CONV_THREADS;  // 8-column row pieces per converter thread
+static_assert(RT_JOBS * RT_CONV_THREADS == RT_M * (RT_K / 8), "converter jobs must divide evenly");
 constexpr int RT_APLANE = RT_M * RT_K * 2;  // 8 KB
 constexpr int RT_XPLANE = RT_N * RT_K * 2;  // 2 KB
 constexpr int RT_STAGE_BYTES = RT_S * (RT_APLANE + RT_XPLANE);
 constexpr int RT_BAR_BYTES = 512;                   // mbarriers, TMEM address, flags, column maxima
 constexpr int RT_SMEM = 1024 /* alignment slack */ + RT_STAGES * RT_STAGE_BYTES + RT_BAR_BYTES;
-constexpr int RT_TM_M = RT_D * RT_N, RT_TM_L = RT_TM_M + RT_N;  // TMEM columns of the middle / low words
+constexpr int RT_TM_H = RT_D * RT_N, RT_TM_M = RT_TM_H + RT_N, RT_TM_L = RT_TM_M + RT_N;  // accumulator words
 constexpr int RT_TMEM_COLS = 512;
 constexpr int kNonFinite = 1 << 20;  // exponent flag of a row / column holding Inf or NaN
-static_assert((RT_D + 2) * RT_N <= RT_TMEM_COLS, "diagonal and output accumulators must fit in TMEM");
+static_assert((RT_D + 3) * RT_N <= RT_TMEM_COLS, "diagonal and output accumulators must fit in TMEM");
 static_assert(RT_CHUNK % RT_K == 0, "chunk = whole stages");
 
 // 32 * (2^48 + 2^42 + ... + 2^0): adding it turns the low nine base-64 digits
@@ -91,10 +94,12 @@ __device__ __forceinline__ long long fixed59(double a, int fmax) {
 }
 
 // Balanced digit s of Q (digit 0 most significant) from qb = Q + kDigitBias,
-// as a float (exact).
+// as a float (exact).  u = d + 32 in [0, 64] becomes a float without a
+// conversion instruction: the bits 0x4B000000 | u are the float 2^23 + u.
 __device__ __forceinline__ float digit_of(long long qb, int s) {
-  if (s == 0) return (float)(int)(qb >> 54);
-  return (float)((int)((unsigned long long)qb >> (54 - 6 * s)) & 63) - 32.f;
+  const unsigned int u = s == 0 ? (unsigned int)((int)(qb >> 54) + 32)
+                                : (unsigned int)((unsigned long long)qb >> (54 - 6 * s)) & 63u;
+  return __uint_as_float(0x4B000000u | u) - 8388640.f;  // - (2^23 + 32)
 }
 // All ten digits of Q.
 __device__ __forceinline__ void digits10(long long q, float (&d)[RT_S]) {
@@ -174,7 +179,7 @@ __global__ void k_x_planes(const double *X, int64_t ldx, int64_t n, int64_t npad
 __global__ void __launch_bounds__(RT_THREADS, 1)
     k_residual_tc(const __grid_constant__ CUtensorMap tmX, const double *A, int64_t lda, int64_t n, int nrhs,
                   const int *rexp, const int *cexp, const double *B, int64_t ldb, double *R, int64_t ldr,
-                  unsigned long long *rmax, DevStatus *st) {
+                  unsigned long long *rmax, int vec, DevStatus *st) {
   extern __shared__ uint8_t smem_raw[];
   if (st && st->done) return;  // refinement converged: nothing to evaluate
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -222,33 +227,42 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   };
 
   if (warp >= RT_CONV_WARP0) {
-    // ---- converters: 4 threads per row, 8 columns each; rows ct/4 and ct/4 + 64.
+    // ---- converters: 4 threads per row, 8 columns each (RT_JOBS rows per thread).
     // Thread 0 also issues the stage's X-plane TMA once the stage is free.
     const int ct = threadIdx.x - 32 * RT_CONV_WARP0;
     const int grp = ct & 3;
-    int rows[2], fmax[2];
-    bool rok[2];
+    int rows[RT_JOBS], fmax[RT_JOBS];
+    bool rok[RT_JOBS];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      rows[u] = (ct >> 2) + 64 * u;
+    for (int u = 0; u < RT_JOBS; ++u) {
+      rows[u] = (ct >> 2) + (RT_CONV_THREADS / 4) * u;
       rok[u] = r0 + rows[u] < n;
       fmax[u] = rok[u] ? rexp[r0 + rows[u]] : 0;
       if (fmax[u] >= kNonFinite) rok[u] = false;  // the epilogue reports NaN for this row
     }
-    auto fetch = [&](int sti, double (&v)[2][8]) {
+    auto fetch = [&](int sti, double (&v)[RT_JOBS][8]) {
       const int64_t k0 = (int64_t)sti * RT_K + grp * 8;
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < RT_JOBS; ++u) {
         const double *src = A + (r0 + rows[u]) * lda + k0;
+        if (vec && rok[u] && k0 + 8 <= n) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[u][j] = (rok[u] && k0 + j < n) ? src[j] : 0.0;
+          for (int j = 0; j < 4; ++j) {
+            const double2 t = reinterpret_cast<const double2 *>(src)[j];
+            v[u][2 * j] = t.x;
+            v[u][2 * j + 1] = t.y;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[u][j] = (rok[u] && k0 + j < n) ? src[j] : 0.0;
+        }
       }
     };
-    double cur[2][8];
+    double cur[RT_JOBS][8];
     fetch(0, cur);
     for (int sti = 0; sti < nst; ++sti) {
       const int s = sti % RT_STAGES, u = sti / RT_STAGES;
-      double nxt[2][8];
+      double nxt[RT_JOBS][8];
       if (sti + 1 < nst) fetch(sti + 1, nxt);
       if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, abort_flag)) {
         fail(11);
@@ -261,7 +275,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         tma_load_2d(x_plane(s, RT_S / 2), &tmX, &full[s], sti * RT_K, y + (RT_S / 2) * RT_N);
       }
 #pragma unroll
-      for (int w = 0; w < 2; ++w) {
+      for (int w = 0; w < RT_JOBS; ++w) {
         long long qb[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) qb[j] = fixed59(cur[w][j], fmax[w]) + kDigitBias;
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       mbar_arrive(&full[s]);
       if (sti + 1 < nst) {
 #pragma unroll
-        for (int w = 0; w < 2; ++w)
+        for (int w = 0; w < RT_JOBS; ++w)
 #pragma unroll
           for (int j = 0; j < 8; ++j) cur[w][j] = nxt[w][j];
       }
@@ -295,8 +309,10 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   } else if (warp == RT_MMA_WARP) {
     if (lane == 0) {
       // ---- MMA issue: per stage and 16-column step, the 55 digit pairs ----
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RT_N >> 3) << 17) |
-                             ((uint32_t)(RT_M >> 4) << 24);  // bf16 x bf16 -> FP32, K-major, 128 x 32
+      // bf16 x bf16 -> FP32, both K-major, M = 128, N = nn.
+      auto idesc = [](int nn) {
+        return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nn >> 3) << 17) | ((uint32_t)(RT_M >> 4) << 24);
+      };
       int committed = -1;
       for (int sti = 0; sti < nst; ++sti) {
         const int s = sti % RT_STAGES, u = sti / RT_STAGES;
@@ -311,16 +327,21 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t a0 = smem_u32(a_plane(s, 0)), x0 = smem_u32(x_plane(s, 0));
+        // For A digit s, the X digits t = 0 .. RT_D-1-s are consecutive 32-row
+        // planes and their diagonals d = s + t consecutive 32-column TMEM
+        // blocks, so one MMA with N = 32 (RT_D - s) (split at N = 256) covers
+        // all pairs (s, t): A is read from shared memory once per digit.
 #pragma unroll
         for (int ks = 0; ks < RT_K / 16; ++ks) {
 #pragma unroll
-          for (int d = 0; d < RT_D; ++d) {
+          for (int sa = 0; sa < RT_S; ++sa) {
+            const uint64_t ad = sw64_desc(a0 + sa * RT_APLANE) + 2 * ks;
+            const uint32_t accum = (sc == 0 && ks == 0 && sa == 0) ? 0u : 1u;
 #pragma unroll
-            for (int sa = 0; sa <= d; ++sa) {
-              const uint64_t ad = sw64_desc(a0 + sa * RT_APLANE) + 2 * ks;
-              const uint64_t xd = sw64_desc(x0 + (d - sa) * RT_XPLANE) + 2 * ks;
-              const uint32_t accum = (sc == 0 && ks == 0 && sa == 0) ? 0u : 1u;
-              umma_f16(tmem + (uint32_t)(d * RT_N), ad, xd, idesc, accum);
+            for (int t0 = 0; t0 < RT_D - sa; t0 += 8) {
+              const int nt = min(8, RT_D - sa - t0);  // X planes in this MMA
+              const uint64_t xd = sw64_desc(x0 + t0 * RT_XPLANE) + 2 * ks;
+              umma_f16(tmem + (uint32_t)((sa + t0) * RT_N), ad, xd, idesc(nt * RT_N), accum);
             }
           }
         }
@@ -339,19 +360,17 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     const int q = warp;
     const int row = q * 32 + lane;
     const int64_t gi = r0 + row;
-    // Triple-binary32 accumulators per output: h in registers, the middle
-    // and low words in this row's TMEM lane (columns RT_TM_M.., RT_TM_L..):
-    // (h, m, l) += v exactly up to the rounding of l.
+    // Triple-binary32 accumulators per output, kept in this row's TMEM lane
+    // (columns RT_TM_H.., RT_TM_M.., RT_TM_L..): (h, m, l) += v exactly up to
+    // the rounding of l.
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    float hacc[RT_N];
-#pragma unroll
-    for (int c = 0; c < RT_N; ++c) hacc[c] = 0.f;
     {
       uint32_t z[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) z[j] = 0u;
 #pragma unroll
       for (int h = 0; h < RT_N / 16; ++h) {
+        tmem_st16(lane_base + RT_TM_H + 16 * h, z);
         tmem_st16(lane_base + RT_TM_M + 16 * h, z);
         tmem_st16(lane_base + RT_TM_L + 16 * h, z);
       }
@@ -365,28 +384,30 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         break;
       }
       tc_fence_after();
-#pragma unroll
-      for (int h = 0; h < RT_N / 16; ++h) {
-        uint32_t mw[16], lw[16];
-        tmem_ld16(lane_base + RT_TM_M + 16 * h, mw);
-        tmem_ld16(lane_base + RT_TM_L + 16 * h, lw);
+#pragma unroll 1
+      for (int h = 0; h < RT_N / 8; ++h) {
+        uint32_t hw[8], mw[8], lw[8];
+        tmem_ld8(lane_base + RT_TM_H + 8 * h, hw);
+        tmem_ld8(lane_base + RT_TM_M + 8 * h, mw);
+        tmem_ld8(lane_base + RT_TM_L + 8 * h, lw);
 #pragma unroll 1
         for (int d = 0; d < RT_D; ++d) {
           const float sc = __int_as_float((127 - 6 * d) << 23);  // 2^(-6d), exact
-          uint32_t r[16];
-          tmem_ld16(lane_base + (uint32_t)(d * RT_N + 16 * h), r);
+          uint32_t r[8];
+          tmem_ld8(lane_base + (uint32_t)(d * RT_N + 8 * h), r);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 8; ++j) {
             float s1, e1, t1, e2;
-            two_sum_f(hacc[16 * h + j], __uint_as_float(r[j]) * sc, s1, e1);
+            two_sum_f(__uint_as_float(hw[j]), __uint_as_float(r[j]) * sc, s1, e1);
             two_sum_f(__uint_as_float(mw[j]), e1, t1, e2);
-            hacc[16 * h + j] = s1;
+            hw[j] = __float_as_uint(s1);
             mw[j] = __float_as_uint(t1);
             lw[j] = __float_as_uint(__uint_as_float(lw[j]) + e2);
           }
         }
-        tmem_st16(lane_base + RT_TM_M + 16 * h, mw);
-        tmem_st16(lane_base + RT_TM_L + 16 * h, lw);
+        tmem_st8(lane_base + RT_TM_H + 8 * h, hw);
+        tmem_st8(lane_base + RT_TM_M + 8 * h, mw);
+        tmem_st8(lane_base + RT_TM_L + 8 * h, lw);
       }
       tc_fence_before();
       mbar_arrive(tempty);
@@ -394,15 +415,16 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     if (ok) {
       tc_fence_after();
       const int fe = gi < n ? rexp[gi] : 0;
-#pragma unroll
-      for (int h = 0; h < RT_N / 16; ++h) {
-        uint32_t mw[16], lw[16];
-        tmem_ld16(lane_base + RT_TM_M + 16 * h, mw);
-        tmem_ld16(lane_base + RT_TM_L + 16 * h, lw);
+#pragma unroll 1
+      for (int h = 0; h < RT_N / 8; ++h) {
+        uint32_t hw[8], mw[8], lw[8];
+        tmem_ld8(lane_base + RT_TM_H + 8 * h, hw);
+        tmem_ld8(lane_base + RT_TM_M + 8 * h, mw);
+        tmem_ld8(lane_base + RT_TM_L + 8 * h, lw);
         if (gi >= n) continue;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-        const int c = 16 * h + j;
+        for (int j = 0; j < 8; ++j) {
+        const int c = 8 * h + j;
         const int gc = cb * RT_N + c;
         if (gc < nrhs) {
           const int fc = cexp[gc];
@@ -411,7 +433,8 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             rv = __longlong_as_double(0x7FF8000000000000LL);  // NaN: A or X not finite
           } else {
             // (A X)_ic = value * 2^(E_i + F_c - 10), E = field - 1022
-            const double v = (double)hacc[c] + ((double)__uint_as_float(mw[j]) + (double)__uint_as_float(lw[j]));
+            const double v =
+                (double)__uint_as_float(hw[j]) + ((double)__uint_as_float(mw[j]) + (double)__uint_as_float(lw[j]));
             rv = B[gi * ldb + gc] - times_pow2(v, (fe - 1022) + (fc - 1022) - 10);
           }
           R[gi * ldr + gc] = rv;
@@ -483,7 +506,9 @@ ebv_status_t residual_tc(const double *A, int64_t lda, int64_t n, const double *
   EBV_TRY(launch_ok());
   prof::Scope ps(s, prof::kResidual, 2.0 * n * n * nrhs);
   dim3 grid(ceil_div(n, RT_M), L.nrb);
-  k_residual_tc<<<grid, RT_THREADS, RT_SMEM, s>>>(map, A, lda, n, (int)nrhs, rexp, cexp, B, ldb, R, ldr, rmax, st);
+  const int vec = (lda % 2 == 0) && ((uintptr_t)A % 16 == 0);  // 16-byte loads of A rows
+  k_residual_tc<<<grid, RT_THREADS, RT_SMEM, s>>>(map, A, lda, n, (int)nrhs, rexp, cexp, B, ldb, R, ldr, rmax, vec,
+                                                  st);
   return launch_ok();
 }
 
