@@ -43,21 +43,30 @@ inline MatView<T> band_view(T *ab, int64_t ldab, int64_t kl, int64_t ku) {
 // Stage an NB x NB tile into shared memory (row stride S) with all of the
 // thread's global loads issued before the first store, so one memory latency
 // is paid instead of NB*NB/NT of them.  get(i, j) returns element (i, j).
-template <int NB, int NT, int S, typename T, typename Get>
-__device__ __forceinline__ void stage_tile(T *dst, Get get) {
-  constexpr int L = NB * NB / NT;
-  static_assert(L * NT == NB * NB, "tile must divide evenly");
-  T r[L];
+// fetch_tile / put_tile are the two halves, for pipelines that keep the
+// next tile's loads in flight while the current one is used.
+template <int NB, int NT, typename T, typename Get>
+__device__ __forceinline__ void fetch_tile(T (&r)[NB * NB / NT], Get get) {
+  static_assert((NB * NB / NT) * NT == NB * NB, "tile must divide evenly");
 #pragma unroll
-  for (int q = 0; q < L; ++q) {
+  for (int q = 0; q < NB * NB / NT; ++q) {
     const int e = threadIdx.x + NT * q;
     r[q] = get(e / NB, e % NB);
   }
+}
+template <int NB, int NT, int S, typename T>
+__device__ __forceinline__ void put_tile(T *dst, const T (&r)[NB * NB / NT]) {
 #pragma unroll
-  for (int q = 0; q < L; ++q) {
+  for (int q = 0; q < NB * NB / NT; ++q) {
     const int e = threadIdx.x + NT * q;
     dst[(e / NB) * S + e % NB] = r[q];
   }
+}
+template <int NB, int NT, int S, typename T, typename Get>
+__device__ __forceinline__ void stage_tile(T *dst, Get get) {
+  T r[NB * NB / NT];
+  fetch_tile<NB, NT>(r, get);
+  put_tile<NB, NT, S>(dst, r);
 }
 
 // Low-precision shadow copies of the factors that feed the tensor-core GEMMs:
@@ -425,23 +434,42 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
   const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
   const int wc = (int)min64(NB, c_end - c0);
   const int nbk = ceil_div(h, NB);
+  // Tile stream, in the order it is consumed: per block j, A_j (this CTA's
+  // strip), L_j0 .. L_j,j-1, then L_jj^{-1}.  The next tile's loads are in
+  // flight while the current one is being multiplied.
+  T pf[NB * NB / 256];
+  auto fetch = [&](int j, int pos) {
+    const int64_t rj = r0 + (int64_t)j * NB;
+    const int hj = min(NB, h - j * NB);
+    if (pos == 0) {
+      fetch_tile<NB, 256>(pf, [&](int k, int c) { return (k < hj && c < wc) ? A.get(rj + k, c0 + c) : T(0); });
+    } else if (pos <= j) {
+      const int64_t ri = r0 + (int64_t)(pos - 1) * NB;
+      fetch_tile<NB, 256>(pf, [&](int k, int c) { return k < hj ? A.get(rj + k, ri + c) : T(0); });
+    } else {
+      const T *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
+      fetch_tile<NB, 256>(pf, [&](int k, int c) { return linv[k * NB + c]; });
+    }
+  };
+  fetch(0, 0);
   for (int j = 0; j < nbk; ++j) {
     const int64_t rj = r0 + (int64_t)j * NB;
     const int hj = min(NB, h - j * NB);
     T *Uj = U + j * NB * TS;
-    const T *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
-    stage_tile<NB, 256, TS>(Uj, [&](int k, int c) { return (k < hj && c < wc) ? A.get(rj + k, c0 + c) : T(0); });
-    stage_tile<NB, 256, TS>(Li, [&](int k, int c) { return linv[k * NB + c]; });
+    put_tile<NB, 256, TS>(Uj, pf);
+    fetch(j, 1);  // L_j0, or L_jj^{-1} when j == 0
     __syncthreads();
     T acc[4][4];
     tile_regs<T, TS>(Uj, acc);
     for (int i = 0; i < j; ++i) {
-      const int64_t ri = r0 + (int64_t)i * NB;
-      stage_tile<NB, 256, TS>(Lt, [&](int k, int c) { return k < hj ? A.get(rj + k, ri + c) : T(0); });
+      __syncthreads();  // the previous product is done with Lt
+      put_tile<NB, 256, TS>(Lt, pf);
+      fetch(j, i + 2);
       __syncthreads();
       tile_fma<T, NB, TS, true>(Lt, U + i * NB * TS, acc);
-      __syncthreads();
     }
+    put_tile<NB, 256, TS>(Li, pf);
+    if (j + 1 < nbk) fetch(j + 1, 0);
     tile_put<T, TS>(Uj, acc);
     __syncthreads();
     tile_product<T, NB, TS>(Li, Uj);  // U_j = L_jj^{-1} acc
