@@ -92,8 +92,11 @@ struct Shadow {
 // broadcasts by shuffles.  The multiplier of row i is formed on the fly as
 // a_ir * (1/a_rr) and stored in place at the end (Eq. 6a); column r is never
 // updated after step r, and warps whose rows are all above the pivot skip the
-// step.  Then the two inverses (L11^{-1}, U11^{-1}) by register-resident,
-// one-barrier-per-step sweeps, written to inv[0..NB*NB) and
+// step.  The same steps also build the two inverses the off-diagonal blocks
+// need: X = L11^{-1} (rows i > r take -l_ir times row r of X) and
+// W = (V^T)^{-1} with V = diag(u)^{-1} U11 (rows i > r take -u_ri/u_rr times
+// row r of W), since column r of L and row r of U are final at step r;
+// U11^{-1} = (diag(1/u) W)^T.  Written to inv[0..NB*NB) and
 // inv[NB*NB..2*NB*NB) (row-major).
 // Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
@@ -206,14 +209,14 @@ __device__ void triangle_inverses(const T *LT, const T *VT, T *buf, const T *rcp
 template <typename T, int NB, int NT>
 __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
   static_assert(NB == 64 && NT == 256, "one column pair per lane, 8 rows per warp");
-  constexpr int RPW = NB / (NT / 32), TS = diag_tstride<T, NB>();
+  constexpr int RPW = NB / (NT / 32);
   extern __shared__ __align__(16) unsigned char dsm[];
   T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T *LT = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
-  T *VT = LT + NB * TS;
-  T *buf = VT + NB * TS;
-  T *rowb = buf;          // double-buffered pivot row
-  __shared__ T rcp[NB];   // pivot reciprocals
+  T *buf = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
+  T *rowb = buf;           // double-buffered pivot row of U (zero up to the pivot)
+  T *rowx = buf + 2 * NB;  // double-buffered row k of X = L^{-1}
+  T *roww = buf + 4 * NB;  // double-buffered row k of W = (V^T)^{-1}, V = diag(u)^{-1} U
+  __shared__ T rcp[NB];    // pivot reciprocals
   __shared__ int bad;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int c0 = lane, c1 = NB - 1 - lane, i0 = g * RPW;
@@ -221,13 +224,20 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     return (i < w && j < w) ? A.get(k0 + i, k0 + j) : (i == j ? T(1) : T(0));
   });
   __syncthreads();
-  T v0[RPW], v1[RPW];
+  // v: the block (Eq. 6); x: L^{-1}; y: W -- all three from the identity.
+  T v0[RPW], v1[RPW], x0[RPW], x1[RPW], y0[RPW], y1[RPW];
 #pragma unroll
   for (int t = 0; t < RPW; ++t) {
     v0[t] = D[i0 + t][c0];
     v1[t] = D[i0 + t][c1];
+    x0[t] = y0[t] = (i0 + t == c0) ? T(1) : T(0);
+    x1[t] = y1[t] = (i0 + t == c1) ? T(1) : T(0);
   }
-  if (threadIdx.x < NB) rowb[threadIdx.x] = threadIdx.x > 0 ? D[0][threadIdx.x] : T(0);
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    rowb[j] = j > 0 ? D[0][j] : T(0);
+    rowx[j] = roww[j] = j == 0 ? T(1) : T(0);
+  }
   if (threadIdx.x == 0) {
     const T pv = D[0][0];
     rcp[0] = pivot_rcp(pv);
@@ -239,21 +249,35 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     if (i0 + RPW - 1 > r) {  // warp-uniform: some of my rows are below the pivot
       const T rc = rcp[r];
       const T u0 = rowb[b + c0], u1 = rowb[b + c1];  // 0 for columns <= r
-      const int src = r < 32 ? r : NB - 1 - r;      // lane holding column r
+      const T xr0 = rowx[b + c0], xr1 = rowx[b + c1];
+      const T yr0 = roww[b + c0], yr1 = roww[b + c1];
+      T ur[RPW];
+      ld8(rowb + b + i0, ur);  // u_ri for my rows i (0 for i <= r)
+      const int src = r < 32 ? r : NB - 1 - r;  // lane holding column r
       const bool lo = r < 32;
 #pragma unroll
       for (int t = 0; t < RPW; ++t) {
         T l = __shfl_sync(0xffffffffu, lo ? v0[t] : v1[t], src) * rc;  // Eq. 6a
         if (i0 <= r) l = (i0 + t > r) ? l : T(0);                       // the warp holding row r
+        const T vr = ur[t] * rc;                                         // v_ri = u_ri / u_rr
         v0[t] -= l * u0;                                                 // Eq. 6c
         v1[t] -= l * u1;
+        x0[t] -= l * xr0;  // X = L^{-1}: row i -= l_ir * row r
+        x1[t] -= l * xr1;
+        y0[t] -= vr * yr0;  // W = (V^T)^{-1}: row i -= v_ri * row r
+        y1[t] -= vr * yr1;
       }
-      // Publish row r+1 right of its pivot, and the pivot's reciprocal.
+      // Publish row r+1: of U right of its pivot, of X and of W; and the pivot's reciprocal.
       const int rn = r + 1;
       if (rn / RPW == g) {
-        const T a0 = pick(v0, rn - i0), a1 = pick(v1, rn - i0);
+        const int tn = rn - i0;
+        const T a0 = pick(v0, tn), a1 = pick(v1, tn);
         rowb[nb + c0] = c0 > rn ? a0 : T(0);
         rowb[nb + c1] = c1 > rn ? a1 : T(0);
+        rowx[nb + c0] = pick(x0, tn);
+        rowx[nb + c1] = pick(x1, tn);
+        roww[nb + c0] = pick(y0, tn);
+        roww[nb + c1] = pick(y1, tn);
         if (c0 == rn || c1 == rn) {
           const T pv = c0 == rn ? a0 : a1;
           rcp[rn] = pivot_rcp(pv);
@@ -276,9 +300,23 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
   if (inv) {
-    masked_factor_copies<T, NB, NT>(D, rcp, LT, VT);
+    // L^{-1} straight from registers; U^{-1} = (diag(1/u) W)^T, i.e.
+    // U^{-1}(c, i) = W(i, c) / u_ii, transposed through shared memory.
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int i = i0 + t;
+      inv[i * NB + c0] = x0[t];
+      inv[i * NB + c1] = x1[t];
+    }
+    __syncthreads();  // D has been written back
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int i = i0 + t;
+      D[c0][i] = y0[t] * rcp[i];
+      D[c1][i] = y1[t] * rcp[i];
+    }
     __syncthreads();
-    triangle_inverses<T, NB, NT>(LT, VT, buf, rcp, inv);
+    for (int e = threadIdx.x; e < NB * NB; e += NT) inv[NB * NB + e] = D[e / NB][e % NB];
   }
 }
 

@@ -139,14 +139,15 @@ __global__ void k_row_expmax(const double *A, int64_t lda, int64_t n, int *rexp)
   if (lane == 0) rexp[i] = m == 2047 ? kNonFinite : m;
 }
 
-// Per-column maximum exponent field of X (cexp zeroed beforehand).
+// Per-column maximum exponent field of X (cexp zeroed beforehand): one row
+// per thread, a warp maximum per column, one atomic per warp and column.
 __global__ void k_col_expmax(const double *X, int64_t ldx, int64_t n, int nrhs, int *cexp) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * nrhs;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = e / nrhs;
-    const int c = (int)(e % nrhs);
-    const int f = exp_field(X[k * ldx + c]);
-    atomicMax(&cexp[c], f == 2047 ? kNonFinite : f);
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = 0; c < nrhs; ++c) {
+    int f = k < n ? exp_field(X[k * ldx + c]) : 0;
+    f = f == 2047 ? kNonFinite : f;
+    for (int off = 16; off > 0; off >>= 1) f = max(f, __shfl_xor_sync(0xffffffffu, f, off));
+    if ((threadIdx.x & 31) == 0 && f > 0) atomicMax(&cexp[c], f);
   }
 }
 
@@ -498,8 +499,7 @@ ebv_status_t residual_tc(const double *A, int64_t lda, int64_t n, const double *
     EBV_TRY(launch_ok());
   }
   EBV_CU(cudaMemsetAsync(cexp, 0, (size_t)L.nrb * RT_N * 4, s));
-  const int g = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (n * nrhs + 255) / 256));
-  k_col_expmax<<<g, 256, 0, s>>>(X, ldx, n, (int)nrhs, cexp);
+  k_col_expmax<<<ceil_div(n, 256), 256, 0, s>>>(X, ldx, n, (int)nrhs, cexp);
   EBV_TRY(launch_ok());
   const int gp = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (L.npad * L.nrb * RT_N + 255) / 256));
   k_x_planes<<<gp, 256, 0, s>>>(X, ldx, n, L.npad, (int)nrhs, L.nrb, cexp, xp);
