@@ -221,7 +221,7 @@ def ebv_solve(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tens
 
 
 # Limits of ebv_solve_static (its workspace is a fixed device array).
-STATIC_SCRATCH_BYTES = 12 << 20
+STATIC_SCRATCH_BYTES = 16 << 20
 STATIC_MAX_N = 4096
 STATIC_MAX_NRHS = 32
 

@@ -100,7 +100,7 @@ __device__ __forceinline__ bool bounded_wait_geq(const int *flag, int want, DevS
   for (long long it = 0; it < polls; ++it) {
     if (ld_acquire(flag) >= want) return true;
     if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) return false;
-    __nanosleep(64);
+    if (it >= 32) __nanosleep(64);  // a short hot spin first: the flag is usually close
   }
   set_status(st, EBV_ERR_TIMEOUT, where);
   return false;

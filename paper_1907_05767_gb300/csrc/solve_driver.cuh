@@ -30,7 +30,7 @@ DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize, bool tc_res
   const size_t nn = (size_t)n * (size_t)std::max<int64_t>(nrhs, 1);
   const size_t nblk = (size_t)std::max<int64_t>(1, (n + kNB - 1) / kNB);
   const size_t nchunk = (size_t)std::max<int64_t>(1, (nrhs + 7) / 8);  // RC >= 8 for every type
-  L.dinv = off; off = align256(off + nblk * 2 * kNB * kNB * tsize);
+  L.dinv = off; off = align256(off + nblk * 4 * kNB * kNB * tsize);
   L.flags = off; off = align256(off + 2 * nchunk * nblk * sizeof(int));
   L.bsave = off; off = align256(off + nn * 8);
   L.r = off; off = align256(off + nn * 8);
@@ -52,7 +52,7 @@ ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
   static const cudaError_t attr = cudaFuncSetAttribute(
       k_diag_inverses<T, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem_bytes<T, kNB>());
   if (attr != cudaSuccess) return EBV_ERR_CUDA;
-  prof::Scope ps(s, prof::kTrsv, 2.0 * ceil_div(n, kNB) * kNB * kNB * kNB / 3.0);
+  prof::Scope ps(s, prof::kTrsv, 2.0 * ceil_div(n, kNB) * kNB * kNB * kNB * (2.0 / 3.0 + 4.0));
   k_diag_inverses<T, kNB><<<ceil_div(n, kNB), 4 * kNB, diag_smem_bytes<T, kNB>(), s>>>(F, n, dinv);
   return launch_ok();
 }

@@ -9,9 +9,12 @@ namespace ebv {
 namespace {  // internal linkage: every translation unit gets its own kernels
 
 // ---------------------------------------------------------------------------
-// Inverses of the diagonal blocks of the packed factors (block b: L_bb^{-1}
-// then U_bb^{-1} at dinv + b * 2 * NB * NB), one CTA per block, so that each
-// diagonal solve of the substitution is a tile product.
+// Per diagonal block b of the packed factors, at dinv + b * 4 * NB * NB:
+// L_bb^{-1}, U_bb^{-1}, L_bb^{-1} L_b,b-1 and U_bb^{-1} U_b,b+1 (zero where
+// the neighbour block does not exist).  One CTA per block.  The inverses make
+// each diagonal solve of the substitution a tile product; the coupling
+// products let a substitution step fold its predecessor and solve in one
+// product: x_b = L_bb^{-1} acc - (L_bb^{-1} L_b,b-1) x_{b-1}.
 // Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
@@ -32,7 +35,29 @@ __global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t 
   __syncthreads();
   masked_factor_copies<T, NB, 4 * NB>(D, rcp, LT, VT);
   __syncthreads();
-  triangle_inverses<T, NB, 4 * NB>(LT, VT, buf, rcp, dinv + (int64_t)blockIdx.x * 2 * NB * NB);
+  T *slot = dinv + (int64_t)blockIdx.x * 4 * NB * NB;
+  triangle_inverses<T, NB, 4 * NB>(LT, VT, buf, rcp, slot);
+  __syncthreads();  // the inverses are in global memory, visible to this CTA
+  constexpr int TS = diag_tstride<T, NB>();
+  const int nblk = ceil_div(n, NB);
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {  // 0: L_bb^{-1} L_b,b-1   1: U_bb^{-1} U_b,b+1
+    const int nb = (int)blockIdx.x + (side == 0 ? -1 : 1);
+    T *out = slot + (2 + side) * NB * NB;
+    if (nb < 0 || nb >= nblk) {
+      for (int e = threadIdx.x; e < NB * NB; e += 4 * NB) out[e] = T(0);
+      continue;
+    }
+    const int64_t j0 = (int64_t)nb * NB;
+    const int hj = (int)min64(NB, n - j0);
+    const T *inv = slot + side * NB * NB;
+    stage_tile<NB, 4 * NB, TS>(LT, [&](int r, int k) { return inv[r * NB + k]; });
+    stage_tile<NB, 4 * NB, TS>(VT, [&](int r, int k) { return (r < hb && k < hj) ? F.get(i0 + r, j0 + k) : T(0); });
+    __syncthreads();
+    tile_product<T, NB, TS>(LT, VT);
+    for (int e = threadIdx.x; e < NB * NB; e += 4 * NB) out[e] = VT[(e / NB) * TS + e % NB];
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -108,12 +133,17 @@ __global__ void __launch_bounds__(256)
       const int r = tr + PASS * q;
       acc[q] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
     }
-    {
-      const T *di = dinv + (int64_t)blk(t) * 2 * NB * NB + (UPPER ? NB * NB : 0);
-      stage_tile<NB, NT, FS>(&Di[0][0], [&](int r, int k) { return di[r * NB + k]; });
-    }
-    if (sb < t) fetch_f(t, sb);
-    for (int s = sb; s < t; ++s) {
+    const T *slot = dinv + (int64_t)blk(t) * 4 * NB * NB;
+    const T *gmat = slot + (UPPER ? 3 : 2) * NB * NB;  // D_t^{-1} F(t, t-1)
+    auto fetch_g = [&]() {
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) fr[q] = gmat[threadIdx.x + NT * q];
+    };
+    stage_tile<NB, NT, FS>(&Di[0][0], [&](int r, int k) { return slot[(UPPER ? NB * NB : 0) + r * NB + k]; });
+    // Blocks s < t-1 are folded here; block t-1 goes through D_t^{-1} F(t, t-1).
+    if (sb < t - 1) fetch_f(t, sb);
+    else if (t >= 1) fetch_g();
+    for (int s = sb; s < t - 1; ++s) {
       if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[s], 1, st, kSpinLimit, s);
       __syncthreads();  // flag seen; the previous fold is done with Fb and Xs
       if (!s_ok) return;
@@ -128,7 +158,8 @@ __global__ void __launch_bounds__(256)
         for (int k = tr; k < NB; k += PASS)
           Xs[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
       }
-      if (s + 1 < t) fetch_f(t, s + 1);
+      if (s + 1 < t - 1) fetch_f(t, s + 1);
+      else fetch_g();
       __syncthreads();
 #pragma unroll 16
       for (int k = 0; k < NB; ++k) {
@@ -137,22 +168,55 @@ __global__ void __launch_bounds__(256)
         for (int q = 0; q < OPT; ++q) acc[q] -= Fb[tr + PASS * q][k] * xk;
       }
     }
-    // X_t = D_t^{-1} acc.  (Di and Ac are free: the previous block ended
-    // with a barrier after its solve.)
+    // y = D_t^{-1} acc, before block t-1 is needed.  (Di and Ac are free: the
+    // previous block ended with a barrier after its last use of them.)
 #pragma unroll
     for (int q = 0; q < OPT; ++q) Ac[tr + PASS * q][tc] = acc[q];
     __syncthreads();
+    T y[OPT];
 #pragma unroll
     for (int q = 0; q < OPT; ++q) {
       const int r = tr + PASS * q;
       T x = T(0);
 #pragma unroll 16
       for (int k = 0; k < NB; ++k) x += Di[r][k] * Ac[k][tc];
-      if (r < hi && tc < wc) B[(i0 + r) * ldb + c0 + tc] = x;
+      y[q] = x;
     }
-    __threadfence();
+    if (t >= 1) {  // x_t = y - (D_t^{-1} F(t, t-1)) x_{t-1}
+      if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[t - 1], 1, st, kSpinLimit, t - 1);
+      __syncthreads();
+      if (!s_ok) return;
+#pragma unroll
+      for (int q = 0; q < LPT; ++q) {
+        const int e = threadIdx.x + NT * q;
+        Fb[e / NB][e % NB] = fr[q];
+      }
+      {
+        const int64_t j0 = (int64_t)blk(t - 1) * NB;
+        const int hj = (int)min64(NB, n - j0);
+        for (int k = tr; k < NB; k += PASS)
+          Xs[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
+      }
+      __syncthreads();
+#pragma unroll 16
+      for (int k = 0; k < NB; ++k) {
+        const T xk = Xs[k][tc];
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) y[q] -= Fb[tr + PASS * q][k] * xk;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int r = tr + PASS * q;
+      if (r < hi && tc < wc) B[(i0 + r) * ldb + c0 + tc] = y[q];
+    }
+    // The barrier orders every thread's stores of x_t before thread 0's
+    // gpu-scope fence, which makes them visible before the flag (cumulativity).
     __syncthreads();
-    if (threadIdx.x == 0) st_release(&fl[t], 1);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(&fl[t], 1);
+    }
   }
 }
 
