@@ -172,10 +172,17 @@ struct Factorizer {
       return launch_ok();
     }
     if (h <= kTrsmMaxBlocks * kNB) {
+      // Narrower column strips when there are few columns: more CTAs, each
+      // with a shorter chain of tile products.
       prof::Scope ps(s, prof::kPanel, 1.0 * h * h * (ch - cl));
-      k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks>
-          <<<ceil_div(ch - cl, kNB), 256, trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>(), s>>>(A, r0, (int)h, cl, ch,
-                                                                                                 inv, sh);
+      constexpr size_t smem = trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
+      const int64_t N = ch - cl;
+      if (N >= 64 * 148)
+        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64><<<ceil_div(N, 64), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
+      else if (N >= 32 * 148)
+        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32><<<ceil_div(N, 32), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
+      else
+        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16><<<ceil_div(N, 16), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
       return launch_ok();
     }
     const int64_t h1 = split(h);

@@ -327,10 +327,19 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
 // k costs four broadcast loads of P, one vector load of Q and 16 fused
 // multiply-adds.  tile_product: Q <- P Q (the result goes back over Q's
 // buffer once every thread is done reading).
-template <typename T, int NB, int TS, bool SUB>
-__device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[4][4]) {
-  static_assert(NB == 64, "tile mapping assumes 64 x 64 and 256 threads");
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+// Column strips narrower than 64 (CW = 32 or 16) keep the same 256 threads
+// on fewer outputs each: rows ti + (1024/CW) a (a < CW/16), columns
+// 4tj .. 4tj+3 with tj < CW/4.
+template <int CW>
+struct StripMap {
+  static constexpr int RPT = CW / 16, RS = 1024 / CW, CG = CW / 4;
+  static_assert(CW == 64 || CW == 32 || CW == 16, "strip width");
+};
+template <typename T, int NB, int TS, bool SUB, int CW = 64>
+__device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[StripMap<CW>::RPT][4]) {
+  static_assert(NB == 64, "tile mapping assumes 64-row tiles and 256 threads");
+  using M = StripMap<CW>;
+  const int ti = threadIdx.x / M::CG, tj = threadIdx.x % M::CG;
 #pragma unroll 8
   for (int k = 0; k < NB; ++k) {
     T q[4];
@@ -343,39 +352,41 @@ __device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[4][4]) {
       q[0] = v0.x, q[1] = v0.y, q[2] = v1.x, q[3] = v1.y;
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const T p = P[(ti + 16 * a) * TS + k];
+    for (int a = 0; a < M::RPT; ++a) {
+      const T p = P[(ti + M::RS * a) * TS + k];
 #pragma unroll
       for (int b = 0; b < 4; ++b) c[a][b] = SUB ? c[a][b] - p * q[b] : c[a][b] + p * q[b];
     }
   }
 }
-template <typename T, int TS>
-__device__ __forceinline__ void tile_regs(const T *S, T (&c)[4][4]) {
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+template <typename T, int TS, int CW = 64>
+__device__ __forceinline__ void tile_regs(const T *S, T (&c)[StripMap<CW>::RPT][4]) {
+  using M = StripMap<CW>;
+  const int ti = threadIdx.x / M::CG, tj = threadIdx.x % M::CG;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < M::RPT; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) c[a][b] = S[(ti + 16 * a) * TS + 4 * tj + b];
+    for (int b = 0; b < 4; ++b) c[a][b] = S[(ti + M::RS * a) * TS + 4 * tj + b];
 }
-template <typename T, int TS>
-__device__ __forceinline__ void tile_put(T *S, const T (&c)[4][4]) {
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+template <typename T, int TS, int CW = 64>
+__device__ __forceinline__ void tile_put(T *S, const T (&c)[StripMap<CW>::RPT][4]) {
+  using M = StripMap<CW>;
+  const int ti = threadIdx.x / M::CG, tj = threadIdx.x % M::CG;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < M::RPT; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) S[(ti + 16 * a) * TS + 4 * tj + b] = c[a][b];
+    for (int b = 0; b < 4; ++b) S[(ti + M::RS * a) * TS + 4 * tj + b] = c[a][b];
 }
-template <typename T, int NB, int TS>
+template <typename T, int NB, int TS, int CW = 64>
 __device__ __forceinline__ void tile_product(const T *P, T *Q) {
-  T c[4][4];
+  T c[StripMap<CW>::RPT][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < StripMap<CW>::RPT; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) c[a][b] = T(0);
-  tile_fma<T, NB, TS, false>(P, Q, c);
+  tile_fma<T, NB, TS, false, CW>(P, Q, c);
   __syncthreads();
-  tile_put<T, TS>(Q, c);
+  tile_put<T, TS, CW>(Q, c);
   __syncthreads();
 }
 
@@ -460,7 +471,7 @@ __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h
 template <typename T, int NB, int MAXB>
 constexpr size_t trsm_multi_smem_bytes() { return sizeof(T) * (MAXB + 2) * (size_t)NB * diag_tstride<T, NB>(); }
 
-template <typename T, typename SH, int NB, int MAXB>
+template <typename T, typename SH, int NB, int MAXB, int CW>
 __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0, int h, int64_t c_begin,
                                                        int64_t c_end, const T *inv, Shadow<SH> sh) {
   static_assert(NB == 64, "tile mapping assumes 64");
@@ -469,8 +480,8 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
   T *U = reinterpret_cast<T *>(dsm);  // MAXB finished / current U blocks
   T *Lt = U + MAXB * NB * TS;         // L_ji
   T *Li = Lt + NB * TS;               // L_jj^{-1}
-  const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
-  const int wc = (int)min64(NB, c_end - c0);
+  const int64_t c0 = c_begin + (int64_t)blockIdx.x * CW;
+  const int wc = (int)min64(CW, c_end - c0);
   const int nbk = ceil_div(h, NB);
   // Tile stream, in the order it is consumed: per block j, A_j (this CTA's
   // strip), L_j0 .. L_j,j-1, then L_jj^{-1}.  The next tile's loads are in
@@ -497,27 +508,27 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
     put_tile<NB, 256, TS>(Uj, pf);
     fetch(j, 1);  // L_j0, or L_jj^{-1} when j == 0
     __syncthreads();
-    T acc[4][4];
-    tile_regs<T, TS>(Uj, acc);
+    T acc[StripMap<CW>::RPT][4];
+    tile_regs<T, TS, CW>(Uj, acc);
     for (int i = 0; i < j; ++i) {
       __syncthreads();  // the previous product is done with Lt
       put_tile<NB, 256, TS>(Lt, pf);
       fetch(j, i + 2);
       __syncthreads();
-      tile_fma<T, NB, TS, true>(Lt, U + i * NB * TS, acc);
+      tile_fma<T, NB, TS, true, CW>(Lt, U + i * NB * TS, acc);
     }
     put_tile<NB, 256, TS>(Li, pf);
     if (j + 1 < nbk) fetch(j + 1, 0);
-    tile_put<T, TS>(Uj, acc);
+    tile_put<T, TS, CW>(Uj, acc);
     __syncthreads();
-    tile_product<T, NB, TS>(Li, Uj);  // U_j = L_jj^{-1} acc
-    for (int e = threadIdx.x; e < NB * NB; e += 256) {
-      const int k = e / NB, c = e % NB;
+    tile_product<T, NB, TS, CW>(Li, Uj);  // U_j = L_jj^{-1} acc
+    for (int e = threadIdx.x; e < NB * CW; e += 256) {
+      const int k = e / CW, c = e % CW;
       if (k < hj && c < wc) A.put(rj + k, c0 + c, Uj[k * TS + c]);
     }
     if (sh.ut) {
       const float s = sh.scale[1];
-      for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      for (int e = threadIdx.x; e < NB * CW; e += 256) {
         const int c = e / NB, k = e % NB;
         if (k < hj && c < wc) sh.ut[(c0 + c) * sh.ld + rj + k] = from_float<SH>((float)Uj[k * TS + c] * s);
       }
@@ -540,10 +551,16 @@ ebv_status_t prepare_leaf_kernels() {
       e = cudaFuncSetAttribute(k_trsm_ru<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_trsm_ll<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int tb = (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>());
+      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
     return e;
   }();
   return err == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
