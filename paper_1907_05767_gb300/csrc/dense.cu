@@ -177,12 +177,22 @@ struct Factorizer {
       prof::Scope ps(s, prof::kPanel, 1.0 * h * h * (ch - cl));
       constexpr size_t smem = trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
       const int64_t N = ch - cl;
-      if (N >= 64 * 148)
+      if (N >= 64 * 148) {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64><<<ceil_div(N, 64), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
-      else if (N >= 32 * 148)
+      } else if constexpr (sizeof(T) == 4) {  // binary32: everything resident in shared memory
+        if (N >= 32 * 148)
+          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 32>
+              <<<ceil_div(N, 32), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 32>(), s>>>(A, r0, (int)h, cl, ch, inv,
+                                                                                         sh);
+        else
+          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 16>
+              <<<ceil_div(N, 16), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 16>(), s>>>(A, r0, (int)h, cl, ch, inv,
+                                                                                         sh);
+      } else if (N >= 32 * 148) {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32><<<ceil_div(N, 32), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
-      else
+      } else {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16><<<ceil_div(N, 16), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
+      }
       return launch_ok();
     }
     const int64_t h1 = split(h);

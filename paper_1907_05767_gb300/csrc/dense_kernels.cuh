@@ -335,7 +335,7 @@ struct StripMap {
   static constexpr int RPT = CW / 16, RS = 1024 / CW, CG = CW / 4;
   static_assert(CW == 64 || CW == 32 || CW == 16, "strip width");
 };
-template <typename T, int NB, int TS, bool SUB, int CW = 64>
+template <typename T, int NB, int TS, bool SUB, int CW = 64, int QS = TS>  // P rows: stride TS; Q rows: QS
 __device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[StripMap<CW>::RPT][4]) {
   static_assert(NB == 64, "tile mapping assumes 64-row tiles and 256 threads");
   using M = StripMap<CW>;
@@ -344,11 +344,11 @@ __device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[StripMap
   for (int k = 0; k < NB; ++k) {
     T q[4];
     if constexpr (sizeof(T) == 4) {
-      const float4 v = *reinterpret_cast<const float4 *>(Q + k * TS + 4 * tj);
+      const float4 v = *reinterpret_cast<const float4 *>(Q + k * QS + 4 * tj);
       q[0] = v.x, q[1] = v.y, q[2] = v.z, q[3] = v.w;
     } else {
-      const double2 v0 = *reinterpret_cast<const double2 *>(Q + k * TS + 4 * tj);
-      const double2 v1 = *reinterpret_cast<const double2 *>(Q + k * TS + 4 * tj + 2);
+      const double2 v0 = *reinterpret_cast<const double2 *>(Q + k * QS + 4 * tj);
+      const double2 v1 = *reinterpret_cast<const double2 *>(Q + k * QS + 4 * tj + 2);
       q[0] = v0.x, q[1] = v0.y, q[2] = v1.x, q[3] = v1.y;
     }
 #pragma unroll
@@ -538,6 +538,119 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
 
 constexpr int kTrsmMaxBlocks = 4;  // rows of the one-launch TRSM: up to 4 leaves
 
+// The same TRSM with everything resident in shared memory (binary32, strips
+// of CW <= 32 columns): every tile of L11 it needs -- L_ji (i < j) and the
+// leaf inverses L_jj^{-1} -- and the strip of A12 are copied in at once with
+// cp.async, so the CTA pays one memory latency instead of one per tile; then
+// the blocked forward substitution runs from shared memory only.
+// Dynamic shared memory: trsm_res_smem_bytes<NB, MAXB, CW>().
+template <int NB, int MAXB, int CW>
+constexpr size_t trsm_res_smem_bytes() {
+  return sizeof(float) * ((size_t)(MAXB * (MAXB + 1) / 2) * NB * diag_tstride<float, NB>() +
+                          (size_t)MAXB * NB * (CW + 4));
+}
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+template <typename SH, int NB, int MAXB, int CW>
+__global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int64_t r0, int h, int64_t c_begin,
+                                                          int64_t c_end, const float *inv, Shadow<SH> sh) {
+  static_assert(NB == 64 && CW <= 32, "64-row tiles, narrow strips");
+  constexpr int TS = diag_tstride<float, NB>(), US = CW + 4;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float *Lbase = reinterpret_cast<float *>(dsm);                      // tiles of L11, packed by (j, i)
+  float *U = Lbase + (MAXB * (MAXB + 1) / 2) * NB * TS;              // MAXB blocks of 64 x CW
+  auto ltile = [&](int j, int i) { return Lbase + (j * (j + 1) / 2 + i) * NB * TS; };  // i == j: the inverse
+  const int64_t c0 = c_begin + (int64_t)blockIdx.x * CW;
+  const int wc = (int)min64(CW, c_end - c0);
+  const int nbk = ceil_div(h, NB);
+  // One batch of asynchronous copies: strip of A12, L_ji, L_jj^{-1}.
+  for (int j = 0; j < nbk; ++j) {
+    const int64_t rj = r0 + (int64_t)j * NB;
+    const int hj = min(NB, h - j * NB);
+    float *Uj = U + j * NB * US;
+    for (int e = threadIdx.x; e < NB * CW; e += 256) {
+      const int k = e / CW, c = e % CW;
+      if (k < hj && c < wc) cp_async4(Uj + k * US + c, A.base + (rj + k) * A.ld + c0 + c);
+      else Uj[k * US + c] = 0.f;
+    }
+    for (int i = 0; i < j; ++i) {
+      float *Lt = ltile(j, i);
+      const int64_t ri = r0 + (int64_t)i * NB;
+      for (int e = threadIdx.x; e < NB * NB; e += 256) {
+        const int k = e / NB, c = e % NB;
+        if (k < hj) cp_async4(Lt + k * TS + c, A.base + (rj + k) * A.ld + ri + c);
+        else Lt[k * TS + c] = 0.f;
+      }
+    }
+    const float *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
+    float *Li = ltile(j, j);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) cp_async4(Li + (e / NB) * TS + e % NB, linv + e);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int j = 0; j < nbk; ++j) {
+    float *Uj = U + j * NB * US;
+    float acc[StripMap<CW>::RPT][4];
+    tile_regs<float, US, CW>(Uj, acc);
+    for (int i = 0; i < j; ++i) tile_fma<float, NB, TS, true, CW, US>(ltile(j, i), U + i * NB * US, acc);
+    __syncthreads();  // everyone has read Uj
+    tile_put<float, US, CW>(Uj, acc);
+    __syncthreads();
+    float out[StripMap<CW>::RPT][4];
+#pragma unroll
+    for (int a = 0; a < StripMap<CW>::RPT; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) out[a][b] = 0.f;
+    // U_j = L_jj^{-1} acc (P rows of stride TS, Q rows of stride US)
+    {
+      using M = StripMap<CW>;
+      const float *P = ltile(j, j);
+      const int ti = threadIdx.x / M::CG, tj = threadIdx.x % M::CG;
+#pragma unroll 8
+      for (int k = 0; k < NB; ++k) {
+        const float4 v = *reinterpret_cast<const float4 *>(Uj + k * US + 4 * tj);
+#pragma unroll
+        for (int a = 0; a < M::RPT; ++a) {
+          const float p = P[(ti + M::RS * a) * TS + k];
+          out[a][0] += p * v.x;
+          out[a][1] += p * v.y;
+          out[a][2] += p * v.z;
+          out[a][3] += p * v.w;
+        }
+      }
+    }
+    __syncthreads();
+    tile_put<float, US, CW>(Uj, out);
+    __syncthreads();
+  }
+  for (int j = 0; j < nbk; ++j) {
+    const int64_t rj = r0 + (int64_t)j * NB;
+    const int hj = min(NB, h - j * NB);
+    const float *Uj = U + j * NB * US;
+    for (int e = threadIdx.x; e < NB * CW; e += 256) {
+      const int k = e / CW, c = e % CW;
+      if (k < hj && c < wc) A.put(rj + k, c0 + c, Uj[k * US + c]);
+    }
+    if (sh.ut) {
+      const float s = sh.scale[1];
+      for (int e = threadIdx.x; e < NB * CW; e += 256) {
+        const int c = e / NB, k = e % NB;
+        if (k < hj && c < wc) sh.ut[(c0 + c) * sh.ld + rj + k] = from_float<SH>(Uj[k * US + c] * s);
+      }
+    }
+  }
+}
+
+
+
 // Opt the leaf kernels into more than 48 KB of dynamic shared memory (FP64
 // tiles need 66.5 KB); once per process and instantiation.
 template <typename T, typename SH>
@@ -561,6 +674,16 @@ ebv_status_t prepare_leaf_kernels() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+    if constexpr (sizeof(T) == 4) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 32>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 32>());
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 16>());
+    }
     return e;
   }();
   return err == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
