@@ -38,7 +38,7 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
     const int w = (int)std::min<int64_t>(kNB, n - c0);
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diag_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, inv);
+      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, inv);
       EBV_TRY(launch_ok());
     }
     const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);

@@ -138,7 +138,7 @@ struct Factorizer {
     constexpr size_t smem = pair_smem_bytes<T, kNB>();
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diag_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, leaf_inv(c0));
+      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, leaf_inv(c0));
       EBV_TRY(launch_ok());
     }
     const int64_t rb = c0 + w, re = n;

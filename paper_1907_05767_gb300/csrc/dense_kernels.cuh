@@ -82,23 +82,13 @@ struct Shadow {
 };
 
 // ---------------------------------------------------------------------------
-// Diagonal block: Doolittle on a w x w block (w <= NB = 64), one CTA of 256
-// threads, identity beyond w.  Equal bi-vectorised ownership (Eq. 7): lane p
-// of warp g holds, in registers, rows 8g .. 8g+7 of the column pair
-// {p, NB-1-p} -- one long and one short vector.  Step r needs the pivot row r
-// (published by its owner warp into a double-buffered shared vector, zero up
-// to the pivot, with the pivot's reciprocal: one barrier per step) and the
-// column r below the pivot, which every warp already holds in one lane and
-// broadcasts by shuffles.  The multiplier of row i is formed on the fly as
-// a_ir * (1/a_rr) and stored in place at the end (Eq. 6a); column r is never
-// updated after step r, and warps whose rows are all above the pivot skip the
-// step.  The same steps also build the two inverses the off-diagonal blocks
-// need: X = L11^{-1} (rows i > r take -l_ir times row r of X) and
-// W = (V^T)^{-1} with V = diag(u)^{-1} U11 (rows i > r take -u_ri/u_rr times
-// row r of W), since column r of L and row r of U are final at step r;
-// U11^{-1} = (diag(1/u) W)^T.  Written to inv[0..NB*NB) and
-// inv[NB*NB..2*NB*NB) (row-major).
-// Dynamic shared memory: diag_smem_bytes<T, NB>().
+// Register-resident sweeps over one 64 x 64 diagonal block, one CTA of 256
+// threads: lane p of warp g holds rows 8g .. 8g+7 of the column pair
+// {p, NB-1-p} (the equal long/short pairing of Eq. 7).  triangle_inverses
+// builds L11^{-1} and U11^{-1} from packed factors with one barrier per step
+// (the substitution's preparation kernel uses it); the factorisation itself
+// is the blocked kernel further down.
+// Dynamic shared memory of the sweeps: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
 __host__ __device__ constexpr int diag_tstride() { return NB + 16 / (int)sizeof(T); }  // 16-byte rows
@@ -206,117 +196,226 @@ __device__ void triangle_inverses(const T *LT, const T *VT, T *buf, const T *rcp
   }
 }
 
+// ---------------------------------------------------------------------------
+// Diagonal block, blocked: the 64 x 64 block as 4 x 4 sub-blocks of 16.  For
+// each diagonal sub-block kb: one warp factors it in registers (warp_lu16:
+// Doolittle with the EbV column pairs {p, 15-p}, Eq. 6a-c and Eq. 7, pivot
+// row and multipliers exchanged by shuffles, no block barrier), two warps
+// invert its triangles, then all warps apply 16 x 16 tile products: the L
+// blocks below (A_ik U_kk^{-1}), the U blocks right of it (L_kk^{-1} A_kj)
+// and the trailing update A_ij -= L_ik U_kj.  The full inverses L11^{-1},
+// U11^{-1} then follow block-diagonal by block-diagonal:
+//   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj,   Y_ij = -Y_ii sum_{k=i+1}^{j} U_ik Y_kj.
+// About twenty barriers in all instead of one per pivot.
+// Dynamic shared memory: diagb_smem_bytes<T, NB>().
+// ---------------------------------------------------------------------------
+constexpr int kSB = 16;  // sub-block order
+
+template <typename T, int NB>
+constexpr size_t diagb_smem_bytes() {
+  return sizeof(T) * (3 * (size_t)NB * (NB + 1) + 8 * (size_t)kSB * (kSB + 1));
+}
+
+// c (this lane's 8 entries of a 16 x 16 tile: row lane/2, columns
+// 8*(lane%2) .. +7) +/-= P Q, P and Q 16 x 16 tiles in shared memory.
+template <typename T, bool SUB>
+__device__ __forceinline__ void wtile_fma(const T *P, int ps, const T *Q, int qs, T (&c)[8]) {
+  const int lane = threadIdx.x & 31, r = lane >> 1, cb = (lane & 1) * 8;
+#pragma unroll
+  for (int k = 0; k < kSB; ++k) {
+    const T p = P[r * ps + k];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j] = SUB ? c[j] - p * Q[k * qs + cb + j] : c[j] + p * Q[k * qs + cb + j];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void wtile_get(const T *S, int ss, T (&c)[8]) {
+  const int lane = threadIdx.x & 31, r = lane >> 1, cb = (lane & 1) * 8;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) c[j] = S[r * ss + cb + j];
+}
+template <typename T>
+__device__ __forceinline__ void wtile_put(T *S, int ss, const T (&c)[8]) {
+  const int lane = threadIdx.x & 31, r = lane >> 1, cb = (lane & 1) * 8;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) S[r * ss + cb + j] = c[j];
+}
+
+// One warp: Doolittle on the 16 x 16 sub-block at (o, o) of D (row stride
+// ld), in place.  Lane (g, p) = (lane / 8, lane % 8) holds rows g, g+4, g+8,
+// g+12 of the column pair {p, 15-p}.  rcp[o..o+15] receives the pivot
+// reciprocals; the first zero / non-finite pivot below w goes to *bad.
+template <typename T>
+__device__ __forceinline__ void warp_lu16(T *D, int ld, int o, T *rcp, int w, int *bad) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, p = lane & 7, g = lane >> 3;
+  const int c0 = p, c1 = kSB - 1 - p;
+  T v0[4], v1[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    v0[t] = D[(o + g + 4 * t) * ld + o + c0];
+    v1[t] = D[(o + g + 4 * t) * ld + o + c1];
+  }
+  T rc0 = T(0), rc1 = T(0);
+#pragma unroll
+  for (int r = 0; r < kSB; ++r) {
+    const int tr = r >> 2, gr = r & 3;
+    const int ps = r < 8 ? r : kSB - 1 - r;  // pair holding column r
+    const T pv = __shfl_sync(FULL, r < 8 ? v0[tr] : v1[tr], gr * 8 + ps);
+    const T rc = pivot_rcp(pv);
+    if (c0 == r) rc0 = rc;
+    if (c1 == r) rc1 = rc;
+    if (lane == 0) {
+      rcp[o + r] = rc;
+      if (o + r < w && pivot_bad(pv)) atomicMin(bad, o + r);
+    }
+    if (r == kSB - 1) break;
+    T u0 = __shfl_sync(FULL, v0[tr], gr * 8 + p);  // row r, my columns
+    T u1 = __shfl_sync(FULL, v1[tr], gr * 8 + p);
+    u0 = c0 > r ? u0 : T(0);
+    u1 = c1 > r ? u1 : T(0);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      T l = __shfl_sync(FULL, r < 8 ? v0[t] : v1[t], g * 8 + ps) * rc;  // Eq. 6a, my rows
+      l = (g + 4 * t > r) ? l : T(0);
+      v0[t] -= l * u0;  // Eq. 6c
+      v1[t] -= l * u1;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int i = g + 4 * t;
+    D[(o + i) * ld + o + c0] = i > c0 ? v0[t] * rc0 : v0[t];
+    D[(o + i) * ld + o + c1] = i > c1 ? v1[t] * rc1 : v1[t];
+  }
+}
+
+// One warp: inverse of the unit lower (lower = true) or upper triangle of the
+// factored 16 x 16 sub-block at (o, o) of D, written to the same place of Z.
+// Lower: rows i > k take -l_ik (row k).  Upper: rows i < k take
+// -(u_ik / u_kk) (row k), k descending, then row i is scaled by 1 / u_ii.
+template <typename T, bool LOWER>
+__device__ __forceinline__ void warp_tri_inv16(const T *D, T *Z, int ld, int o, const T *rcp) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, p = lane & 7, g = lane >> 3;
+  const int c0 = p, c1 = kSB - 1 - p;
+  T z0[4], z1[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    z0[t] = (g + 4 * t == c0) ? T(1) : T(0);
+    z1[t] = (g + 4 * t == c1) ? T(1) : T(0);
+  }
+#pragma unroll
+  for (int s = 0; s < kSB; ++s) {
+    const int k = LOWER ? s : kSB - 1 - s;
+    const int tk = k >> 2, gk = k & 3;
+    const T zk0 = __shfl_sync(FULL, z0[tk], gk * 8 + p);  // row k of Z, my columns
+    const T zk1 = __shfl_sync(FULL, z1[tk], gk * 8 + p);
+    const T rk = rcp[o + k];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = g + 4 * t;
+      T f = D[(o + i) * ld + o + k];
+      f = LOWER ? (i > k ? f : T(0)) : (i < k ? f * rk : T(0));
+      z0[t] -= f * zk0;
+      z1[t] -= f * zk1;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int i = g + 4 * t;
+    const T sc = LOWER ? T(1) : rcp[o + i];
+    Z[(o + i) * ld + o + c0] = z0[t] * sc;
+    Z[(o + i) * ld + o + c1] = z1[t] * sc;
+  }
+}
+
 template <typename T, int NB, int NT>
 __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
-  static_assert(NB == 64 && NT == 256, "one column pair per lane, 8 rows per warp");
-  constexpr int RPW = NB / (NT / 32);
+  static_assert(NB == 64 && NT == 256, "4 x 4 sub-blocks of 16, 8 warps");
+  constexpr int LD = NB + 1, NSB = NB / kSB;
   extern __shared__ __align__(16) unsigned char dsm[];
-  T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
-  T *buf = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
-  T *rowb = buf;           // double-buffered pivot row of U (zero up to the pivot)
-  T *rowx = buf + 2 * NB;  // double-buffered row k of X = L^{-1}
-  T *roww = buf + 4 * NB;  // double-buffered row k of W = (V^T)^{-1}, V = diag(u)^{-1} U
-  __shared__ T rcp[NB];    // pivot reciprocals
+  T *D = reinterpret_cast<T *>(dsm);  // the block, then its packed factors
+  T *X = D + NB * LD;                 // L11^{-1}
+  T *Y = X + NB * LD;                 // U11^{-1}
+  T *scratch = Y + NB * LD;           // one 16 x 17 tile per warp
+  __shared__ T rcp[NB];
   __shared__ int bad;
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int c0 = lane, c1 = NB - 1 - lane, i0 = g * RPW;
-  stage_tile<NB, NT, NB + 1>(&D[0][0], [&](int i, int j) {
+  const int warp = threadIdx.x >> 5;
+  T *S = scratch + warp * kSB * (kSB + 1);
+  auto blk = [&](T *M, int bi, int bj) { return M + (bi * kSB) * LD + bj * kSB; };
+  stage_tile<NB, NT, LD>(D, [&](int i, int j) {
     return (i < w && j < w) ? A.get(k0 + i, k0 + j) : (i == j ? T(1) : T(0));
   });
+  for (int e = threadIdx.x; e < NB * LD; e += NT) X[e] = Y[e] = T(0);
+  if (threadIdx.x == 0) bad = NB;
   __syncthreads();
-  // v: the block (Eq. 6); x: L^{-1}; y: W -- all three from the identity.
-  T v0[RPW], v1[RPW], x0[RPW], x1[RPW], y0[RPW], y1[RPW];
+  for (int kb = 0; kb < NSB; ++kb) {
+    const int o = kb * kSB;
+    if (warp == 0) warp_lu16(D, LD, o, rcp, w, &bad);
+    __syncthreads();
+    if (warp == 0) warp_tri_inv16<T, true>(D, X, LD, o, rcp);
+    if (warp == 1) warp_tri_inv16<T, false>(D, Y, LD, o, rcp);
+    __syncthreads();
+    if (kb + 1 == NSB) break;
+    // L blocks below (A_ik U_kk^{-1}) and U blocks right (L_kk^{-1} A_kj), one warp each.
+    const int nrest = NSB - 1 - kb;
+    if (warp < 2 * nrest) {
+      const bool lower = warp < nrest;
+      const int m = kb + 1 + (lower ? warp : warp - nrest);
+      T c[8];
 #pragma unroll
-  for (int t = 0; t < RPW; ++t) {
-    v0[t] = D[i0 + t][c0];
-    v1[t] = D[i0 + t][c1];
-    x0[t] = y0[t] = (i0 + t == c0) ? T(1) : T(0);
-    x1[t] = y1[t] = (i0 + t == c1) ? T(1) : T(0);
-  }
-  if (threadIdx.x < NB) {
-    const int j = threadIdx.x;
-    rowb[j] = j > 0 ? D[0][j] : T(0);
-    rowx[j] = roww[j] = j == 0 ? T(1) : T(0);
-  }
-  if (threadIdx.x == 0) {
-    const T pv = D[0][0];
-    rcp[0] = pivot_rcp(pv);
-    bad = (w > 0 && pivot_bad(pv)) ? 0 : NB;
-  }
-  __syncthreads();
-  for (int r = 0; r + 1 < NB; ++r) {
-    const int b = (r & 1) * NB, nb = NB - b;
-    if (i0 + RPW - 1 > r) {  // warp-uniform: some of my rows are below the pivot
-      const T rc = rcp[r];
-      const T u0 = rowb[b + c0], u1 = rowb[b + c1];  // 0 for columns <= r
-      const T xr0 = rowx[b + c0], xr1 = rowx[b + c1];
-      const T yr0 = roww[b + c0], yr1 = roww[b + c1];
-      T ur[RPW];
-      ld8(rowb + b + i0, ur);  // u_ri for my rows i (0 for i <= r)
-      const int src = r < 32 ? r : NB - 1 - r;  // lane holding column r
-      const bool lo = r < 32;
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) {
-        T l = __shfl_sync(0xffffffffu, lo ? v0[t] : v1[t], src) * rc;  // Eq. 6a
-        if (i0 <= r) l = (i0 + t > r) ? l : T(0);                       // the warp holding row r
-        const T vr = ur[t] * rc;                                         // v_ri = u_ri / u_rr
-        v0[t] -= l * u0;                                                 // Eq. 6c
-        v1[t] -= l * u1;
-        x0[t] -= l * xr0;  // X = L^{-1}: row i -= l_ir * row r
-        x1[t] -= l * xr1;
-        y0[t] -= vr * yr0;  // W = (V^T)^{-1}: row i -= v_ri * row r
-        y1[t] -= vr * yr1;
-      }
-      // Publish row r+1: of U right of its pivot, of X and of W; and the pivot's reciprocal.
-      const int rn = r + 1;
-      if (rn / RPW == g) {
-        const int tn = rn - i0;
-        const T a0 = pick(v0, tn), a1 = pick(v1, tn);
-        rowb[nb + c0] = c0 > rn ? a0 : T(0);
-        rowb[nb + c1] = c1 > rn ? a1 : T(0);
-        rowx[nb + c0] = pick(x0, tn);
-        rowx[nb + c1] = pick(x1, tn);
-        roww[nb + c0] = pick(y0, tn);
-        roww[nb + c1] = pick(y1, tn);
-        if (c0 == rn || c1 == rn) {
-          const T pv = c0 == rn ? a0 : a1;
-          rcp[rn] = pivot_rcp(pv);
-          if (rn < w && pivot_bad(pv)) atomicMin(&bad, rn);
-        }
-      }
+      for (int j = 0; j < 8; ++j) c[j] = T(0);
+      if (lower) wtile_fma<T, false>(blk(D, m, kb), LD, blk(Y, kb, kb), LD, c);
+      else wtile_fma<T, false>(blk(X, kb, kb), LD, blk(D, kb, m), LD, c);
+      __syncwarp();
+      wtile_put(lower ? blk(D, m, kb) : blk(D, kb, m), LD, c);
     }
     __syncthreads();
-  }
-#pragma unroll
-  for (int t = 0; t < RPW; ++t) {  // multipliers in place (Eq. 6a)
-    const int i = i0 + t;
-    D[i][c0] = i > c0 ? v0[t] * rcp[c0] : v0[t];
-    D[i][c1] = i > c1 ? v1[t] * rcp[c1] : v1[t];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += NT) {
-    const int i = e / NB, j = e % NB;
-    if (i < w && j < w) A.put(k0 + i, k0 + j, D[i][j]);
+    // Trailing update A_ij -= L_ik U_kj, i, j > kb.
+    for (int q = warp; q < nrest * nrest; q += NT / 32) {
+      const int bi = kb + 1 + q / nrest, bj = kb + 1 + q % nrest;
+      T c[8];
+      wtile_get(blk(D, bi, bj), LD, c);
+      wtile_fma<T, true>(blk(D, bi, kb), LD, blk(D, kb, bj), LD, c);
+      wtile_put(blk(D, bi, bj), LD, c);
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
-  if (inv) {
-    // L^{-1} straight from registers; U^{-1} = (diag(1/u) W)^T, i.e.
-    // U^{-1}(c, i) = W(i, c) / u_ii, transposed through shared memory.
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int i = e / NB, j = e % NB;
+    if (i < w && j < w) A.put(k0 + i, k0 + j, D[i * LD + j]);
+  }
+  if (!inv) return;
+  // Off-diagonal blocks of the inverses, one block distance d at a time.
+  for (int d = 1; d < NSB; ++d) {
+    const int nb = NSB - d;  // blocks at this distance in each triangle
+    if (warp < 2 * nb) {
+      const bool lower = warp < nb;
+      const int j = lower ? warp : warp - nb;
+      T c[8];
 #pragma unroll
-    for (int t = 0; t < RPW; ++t) {
-      const int i = i0 + t;
-      inv[i * NB + c0] = x0[t];
-      inv[i * NB + c1] = x1[t];
-    }
-    __syncthreads();  // D has been written back
+      for (int q = 0; q < 8; ++q) c[q] = T(0);
+      if (lower) {  // X_{j+d, j} = -X_{j+d, j+d} sum_{k=j}^{j+d-1} L_{j+d, k} X_{k, j}
+        for (int k = j; k < j + d; ++k) wtile_fma<T, false>(blk(D, j + d, k), LD, blk(X, k, j), LD, c);
+      } else {  // Y_{j, j+d} = -Y_{j, j} sum_{k=j+1}^{j+d} U_{j, k} Y_{k, j+d}
+        for (int k = j + 1; k <= j + d; ++k) wtile_fma<T, false>(blk(D, j, k), LD, blk(Y, k, j + d), LD, c);
+      }
+      wtile_put(S, kSB + 1, c);
+      __syncwarp();
 #pragma unroll
-    for (int t = 0; t < RPW; ++t) {
-      const int i = i0 + t;
-      D[c0][i] = y0[t] * rcp[i];
-      D[c1][i] = y1[t] * rcp[i];
+      for (int q = 0; q < 8; ++q) c[q] = T(0);
+      if (lower) wtile_fma<T, true>(blk(X, j + d, j + d), LD, S, kSB + 1, c);
+      else wtile_fma<T, true>(blk(Y, j, j), LD, S, kSB + 1, c);
+      wtile_put(lower ? blk(X, j + d, j) : blk(Y, j, j + d), LD, c);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < NB * NB; e += NT) inv[NB * NB + e] = D[e / NB][e % NB];
+  }
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
+    const int i = e / NB, j = e % NB;
+    inv[e] = X[i * LD + j];
+    inv[NB * NB + e] = Y[i * LD + j];
   }
 }
 
@@ -659,7 +758,7 @@ ebv_status_t prepare_leaf_kernels() {
     const int bytes = (int)pair_smem_bytes<T, kNB>();
     cudaError_t e = cudaFuncSetAttribute(k_diag_factor<T, kNB, 4 * kNB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)diag_smem_bytes<T, kNB>());
+                                         (int)diagb_smem_bytes<T, kNB>());
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_trsm_ru<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
