@@ -243,7 +243,7 @@ EBV_API ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs, c
  * to start at zero): calls whose work overlaps on the GPU (other streams,
  * other host threads without ordering) race and give undefined results.
  */
-#define EBV_STATIC_SCRATCH_BYTES ((size_t)12 << 20)
+#define EBV_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 #define EBV_STATIC_MAX_N 4096
 #define EBV_STATIC_MAX_NRHS 32
 EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu,
@@ -301,11 +301,12 @@ EBV_API ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda,
  * ebv_debug_launch_count: kernels launched by this library so far (process-wide).
  * ebv_debug_profile(1) brackets every later launch with CUDA events on its
  * stream, per kernel class: 0 mixed-precision trailing update, 1 working-
- * precision trailing update, 2 panel (diagonal block, L21, U12), 3 block
- * substitutions, 4 refinement residual, 5 batched kernel, 6 adjoint, 7 other.
- * ebv_debug_profile_read fills, for the 8 classes, the summed device time in
+ * precision trailing update, 2 diagonal blocks, 3 block substitutions,
+ * 4 refinement residual, 5 batched kernel, 6 adjoint, 7 other, 8 L21 / U12
+ * tile products and blocked TRSMs.
+ * ebv_debug_profile_read fills, for the 9 classes, the summed device time in
  * ms, the summed algorithmic work (flops) and the launch count of the launches
- * recorded since the previous read (host arrays of 8; synchronises on the
+ * recorded since the previous read (host arrays of 9; synchronises on the
  * recorded events).  Profiling adds an event pair per launch; switch it off
  * for timed runs.
  */

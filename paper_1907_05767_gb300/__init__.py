@@ -89,7 +89,7 @@ _SIGNATURES = [
     ("ebv_debug_profile", None, [_I32]),
     ("ebv_debug_profile_read", _I32, [_VP, _VP, _VP]),
 ]
-PROFILE_CLASSES = ["lowp_gemm", "simt_gemm", "panel", "trsv", "residual", "batched", "adjoint", "other"]
+PROFILE_CLASSES = ["lowp_gemm", "simt_gemm", "panel", "trsv", "residual", "batched", "adjoint", "other", "trsm"]
 
 
 def launch_count() -> int:
@@ -103,9 +103,9 @@ def profile(enable: bool):
 def profile_read() -> dict:
     """{class: (ms, work, launches)} for launches recorded since the last read."""
     import numpy as np
-    ms = np.zeros(8)
-    work = np.zeros(8)
-    cnt = np.zeros(8, dtype=np.int64)
+    ms = np.zeros(len(PROFILE_CLASSES))
+    work = np.zeros(len(PROFILE_CLASSES))
+    cnt = np.zeros(len(PROFILE_CLASSES), dtype=np.int64)
     _check(lib().ebv_debug_profile_read(ms.ctypes.data, work.ctypes.data, cnt.ctypes.data), "profile_read")
     return {c: (float(ms[i]), float(work[i]), int(cnt[i])) for i, c in enumerate(PROFILE_CLASSES)}
 EXPORTED = [s[0] for s in _SIGNATURES]

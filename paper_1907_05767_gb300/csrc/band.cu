@@ -44,12 +44,12 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
     const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
     const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
     if (re > rb) {
-      prof::Scope ps(s, prof::kPanel, 2.0 * (re - rb) * w * w);
+      prof::Scope ps(s, prof::kTrsm, 2.0 * (re - rb) * w * w);
       k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
       EBV_TRY(launch_ok());
     }
     if (ce > cb) {
-      prof::Scope ps(s, prof::kPanel, 2.0 * w * w * (ce - cb));
+      prof::Scope ps(s, prof::kTrsm, 2.0 * w * w * (ce - cb));
       k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, kNB), 256, smem, s>>>(A, c0, w, cb, ce, inv, none);
       EBV_TRY(launch_ok());
     }

@@ -143,7 +143,7 @@ struct Factorizer {
     }
     const int64_t rb = c0 + w, re = n;
     if (re > rb) {
-      prof::Scope ps(s, prof::kPanel, 2.0 * (re - rb) * w * w);
+      prof::Scope ps(s, prof::kTrsm, 2.0 * (re - rb) * w * w);
       k_trsm_ru<T, SH, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
       EBV_TRY(launch_ok());
     }
@@ -166,7 +166,7 @@ struct Factorizer {
   ebv_status_t trsm_ll(int64_t r0, int64_t h, int64_t cl, int64_t ch) {
     if (ch <= cl || h <= 0) return EBV_OK;
     if (h <= kNB) {
-      prof::Scope ps(s, prof::kPanel, 2.0 * h * h * (ch - cl));
+      prof::Scope ps(s, prof::kTrsm, 2.0 * h * h * (ch - cl));
       k_trsm_ll<T, SH, kNB><<<ceil_div(ch - cl, kNB), 256, pair_smem_bytes<T, kNB>(), s>>>(A, r0, (int)h, cl, ch,
                                                                                          leaf_inv(r0), sh);
       return launch_ok();
@@ -174,7 +174,7 @@ struct Factorizer {
     if (h <= kTrsmMaxBlocks * kNB) {
       // Narrower column strips when there are few columns: more CTAs, each
       // with a shorter chain of tile products.
-      prof::Scope ps(s, prof::kPanel, 1.0 * h * h * (ch - cl));
+      prof::Scope ps(s, prof::kTrsm, 1.0 * h * h * (ch - cl));
       constexpr size_t smem = trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
       const int64_t N = ch - cl;
       if (N >= 64 * 148) {

@@ -18,13 +18,14 @@ namespace prof {
 enum Class : int {
   kLowpGemm = 0,   // tensor-core (or SIMT fallback) mixed-precision trailing update
   kSimtGemm = 1,   // working-precision trailing update
-  kPanel = 2,      // diagonal block + L21 / U12 leaf kernels
+  kPanel = 2,      // diagonal-block kernels
   kTrsv = 3,       // block substitutions
   kResidual = 4,   // refinement residual
   kBatched = 5,    // batched persistent kernel
   kAdjoint = 6,    // adjoint kernels
   kOther = 7,
-  kNumClasses = 8
+  kTrsm = 8,       // L21 / U12 tile products and blocked TRSMs (kPanel: the diagonal blocks)
+  kNumClasses = 9
 };
 
 bool enabled();
