@@ -359,17 +359,17 @@ def roofline_for(name, ms, work, cnt, peaks, args, active=None):
                 "frac": achieved / peak, "traffic": None, "peak_source": src, "launches": cnt,
                 "avg_launch_ms": per_launch_ms}
     if name == "residual":
-        # Triple-binary32 residual: 25 FP32 instructions (FFMA/FADD/FMUL, one
-        # issue slot each) per FP64-accurate multiply-add, so the ALU bound is
-        # (75.1e12 / 2) FFMA/s / 25 * 2 flops = 75.1 / 25 TFLOP/s FP64-equivalent.
-        # Launches after the stop test has passed exit at once: only `active`
-        # of them evaluate a residual, each 2 n^2 nrhs flops.
-        peak = 75.1 / 25.0
+        # Tensor-core residual: reads A (8 n^2 bytes, FP64) once per evaluation;
+        # reported against HBM bandwidth.  Launches after the stop test has
+        # passed exit at once: only `active` of them evaluate a residual.
         act = active if active else cnt
-        achieved = (work / cnt) * act / (ms / 1e3) / 1e12
-        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64-equiv)",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FFMA 75.1 TF/s / 25 (FP32 instructions per emulated FP64 multiply-add)",
+        n = args.n
+        bytes_per = 8.0 * n * n
+        achieved = bytes_per * act / (ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        src = "measured HBM copy" if "hbm_gbs" in peaks else "fallback"
+        return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": src,
                 "launches": act, "avg_launch_ms": ms / act}
     achieved = work / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 75.1, "unit": "TFLOP/s",

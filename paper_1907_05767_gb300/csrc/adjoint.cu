@@ -143,7 +143,7 @@ extern "C" ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs
   }
   if (!grad_a) return EBV_OK;
   static const cudaError_t attr =
-      cudaFuncSetAttribute(k_adjoint_outer, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set_smem(k_adjoint_outer, 200 * 1024);
   if (attr != cudaSuccess) return EBV_ERR_CUDA;
   prof::Scope ps(s, prof::kOther, 8.0 * batch * n * n);  // bytes written (HBM-bound step)
   dim3 grid((unsigned)((n + AROWS - 1) / AROWS), (unsigned)batch);

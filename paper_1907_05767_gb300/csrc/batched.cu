@@ -315,7 +315,7 @@ template <typename T>
 int resident_ctas() {
   static const int r = [] {
     constexpr int smem = (int)sizeof(BatchSmem<T, 32>);
-    if (cudaFuncSetAttribute(k_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (set_smem(k_batched<T>, smem) != cudaSuccess)
       return 0;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

@@ -49,6 +49,18 @@ inline ebv_status_t launch_ok() {
   return cudaGetLastError() == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
 }
 
+// Opt a kernel into `bytes` of dynamic shared memory (if > 0) with the
+// maximum shared-memory carveout.  Every kernel of the library asks for the
+// same carveout, so consecutive launches never make the SMs reconfigure their
+// L1 / shared-memory split between kernels.
+template <typename K>
+inline cudaError_t set_smem(K kernel, int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && bytes > 0) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 __host__ __device__ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }

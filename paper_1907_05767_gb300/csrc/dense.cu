@@ -205,6 +205,17 @@ struct Factorizer {
   ebv_status_t rlu(int64_t c0, int64_t w) {
     if (w <= kNB) return leaf(c0, (int)w);
     const int64_t w1 = split(w);
+    if (w <= 2 * kNB) {  // two leaves: U12 and the trailing update in one launch
+      EBV_TRY(leaf(c0, (int)w1));
+      {
+        const int64_t rows = n - c0 - w1;
+        prof::Scope ps(s, prof::kTrsm, 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
+        k_leaf_update<T, SH, kNB><<<ceil_div(rows, kNB), 256, leaf_update_smem_bytes<T, kNB>(), s>>>(
+            A, c0, (int)w1, (int)(w - w1), n, leaf_inv(c0), sh);
+        EBV_TRY(launch_ok());
+      }
+      return leaf(c0 + w1, (int)(w - w1));
+    }
     EBV_TRY(rlu(c0, w1));
     EBV_TRY(trsm_ll(c0, w1, c0 + w1, c0 + w));
     EBV_TRY(gemm(c0 + w1, c0 + w1, c0, n - c0 - w1, w - w1, w1));
@@ -267,6 +278,8 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   float *scale = (float *)(w + L.scale);
   EBV_CU(cudaMemsetAsync(scan, 0, 4, s));         // max |a_ij|, i != j: starts at +0
   EBV_CU(cudaMemsetAsync(scan + 1, 0x7F, 4, s));  // min |a_ii|: starts at 0x7F7F7F7F (3.4e38)
+  static const bool carveout = (set_smem(k_to_working, 0), set_smem(k_make_scale, 0), true);
+  (void)carveout;
   k_to_working<<<grid_for(n * n), 256, 0, s>>>((const double *)a, d->ld, n, (float *)lowp, scan, scan + 1);
   EBV_TRY(launch_ok());
   const int op = prec == EBV_MIXED_BF16 ? 0 : 1;

@@ -557,6 +557,61 @@ __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h
 }
 
 // ---------------------------------------------------------------------------
+// A two-leaf panel's middle step in one launch (recursion nodes of width
+// <= 128): U12 = L11^{-1} A12 for the w2 columns right of the left leaf, and
+// the trailing update A22 -= L21 U12 of every row below, in the working
+// precision.  CTA b owns the 64-row block b of A22; every CTA forms U12 (one
+// tile product) and CTA 0 also stores it (and its low-precision shadow).
+// Dynamic shared memory: leaf_update_smem_bytes<T, NB>().
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+constexpr size_t leaf_update_smem_bytes() { return 4 * sizeof(T) * (size_t)NB * diag_tstride<T, NB>(); }
+
+template <typename T, typename SH, int NB>
+__global__ void __launch_bounds__(256) k_leaf_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
+                                                     const T *inv, Shadow<SH> sh) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>();
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T *Li = reinterpret_cast<T *>(dsm);
+  T *U12 = Li + NB * TS;
+  T *L21 = U12 + NB * TS;
+  T *C = L21 + NB * TS;
+  const int64_t cb = c0 + w1;                        // first column (and row) of the right half
+  const int64_t r0 = cb + (int64_t)blockIdx.x * NB;  // this CTA's rows of A22
+  const int h = (int)min64(NB, n - r0);
+  stage_tile<NB, 256, TS>(Li, [&](int i, int k) { return inv[i * NB + k]; });
+  stage_tile<NB, 256, TS>(U12, [&](int k, int j) { return (k < w1 && j < w2) ? A.get(c0 + k, cb + j) : T(0); });
+  stage_tile<NB, 256, TS>(L21, [&](int i, int k) { return (i < h && k < w1) ? A.get(r0 + i, c0 + k) : T(0); });
+  stage_tile<NB, 256, TS>(C, [&](int i, int j) { return (i < h && j < w2) ? A.get(r0 + i, cb + j) : T(0); });
+  __syncthreads();
+  tile_product<T, NB, TS>(Li, U12);  // U12 = L11^{-1} A12 (Eq. 6b)
+  if (blockIdx.x == 0) {
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int k = e / NB, j = e % NB;
+      if (k < w1 && j < w2) A.put(c0 + k, cb + j, U12[k * TS + j]);
+    }
+    if (sh.ut) {
+      const float s = sh.scale[1];
+      for (int e = threadIdx.x; e < NB * NB; e += 256) {
+        const int j = e / NB, k = e % NB;
+        if (k < w1 && j < w2) sh.ut[(cb + j) * sh.ld + c0 + k] = from_float<SH>((float)U12[k * TS + j] * s);
+      }
+    }
+  }
+  T acc[4][4];
+  tile_regs<T, TS>(C, acc);
+  tile_fma<T, NB, TS, true>(L21, U12, acc);  // A22 -= L21 U12 (Eq. 6c, 64 steps aggregated)
+  __syncthreads();
+  tile_put<T, TS>(C, acc);
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int i = e / NB, j = e % NB;
+    if (i < h && j < w2) A.put(r0 + i, cb + j, C[i * TS + j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // U12 = L11^{-1} A12 for h <= MAXB * NB rows in one launch (Eq. 6b for the
 // U vectors of several leaf blocks at once): a left-looking blocked forward
 // substitution over the 64-row blocks of L11, one 64-column strip per CTA.
@@ -756,32 +811,25 @@ template <typename T, typename SH>
 ebv_status_t prepare_leaf_kernels() {
   static const cudaError_t err = [] {
     const int bytes = (int)pair_smem_bytes<T, kNB>();
-    cudaError_t e = cudaFuncSetAttribute(k_diag_factor<T, kNB, 4 * kNB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)diagb_smem_bytes<T, kNB>());
+    cudaError_t e = set_smem(k_diag_factor<T, kNB, 4 * kNB>, (int)diagb_smem_bytes<T, kNB>());
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_trsm_ru<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      e = set_smem(k_trsm_ru<T, SH, kNB>, bytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_trsm_ll<T, SH, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      e = set_smem(k_trsm_ll<T, SH, kNB>, bytes);
+    if (e == cudaSuccess)
+      e = set_smem(k_leaf_update<T, SH, kNB>, (int)leaf_update_smem_bytes<T, kNB>());
     const int tb = (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+      e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64>, tb);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+      e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32>, tb);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, tb);
+      e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16>, tb);
     if constexpr (sizeof(T) == 4) {
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 32>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 32>());
+        e = set_smem(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 32>, (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 32>());
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 16>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 16>());
+        e = set_smem(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 16>, (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 16>());
     }
     return e;
   }();

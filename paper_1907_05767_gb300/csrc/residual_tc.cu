@@ -484,7 +484,10 @@ ebv_status_t residual_tc(const double *A, int64_t lda, int64_t n, const double *
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_residual_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, RT_SMEM);
+    attr_err = set_smem(k_residual_tc, RT_SMEM);
+    if (attr_err == cudaSuccess) attr_err = set_smem(k_row_expmax, 0);
+    if (attr_err == cudaSuccess) attr_err = set_smem(k_col_expmax, 0);
+    if (attr_err == cudaSuccess) attr_err = set_smem(k_x_planes, 0);
   });
   if (attr_err != cudaSuccess) return EBV_ERR_CUDA;
   const ResidualTcLayout L = residual_tc_layout(n, nrhs);

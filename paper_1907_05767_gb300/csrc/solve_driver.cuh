@@ -49,8 +49,7 @@ inline int grid_for(int64_t elems) { return (int)std::min<int64_t>(4096, std::ma
 // Inverses of the diagonal blocks of the factors (once per solve call).
 template <typename T>
 ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_diag_inverses<T, kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem_bytes<T, kNB>());
+  static const cudaError_t attr = set_smem(k_diag_inverses<T, kNB>, (int)diag_smem_bytes<T, kNB>());
   if (attr != cudaSuccess) return EBV_ERR_CUDA;
   prof::Scope ps(s, prof::kTrsv, 2.0 * ceil_div(n, kNB) * kNB * kNB * kNB * (2.0 / 3.0 + 4.0));
   k_diag_inverses<T, kNB><<<ceil_div(n, kNB), 4 * kNB, diag_smem_bytes<T, kNB>(), s>>>(F, n, dinv);
@@ -68,7 +67,7 @@ ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, cons
   auto kern = k_trsv_left<T, kNB, RC, UPPER>;
   static int resident = [&] {
     int dev = 0, sms = 0, per_sm = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (set_smem(kern, (int)smem) != cudaSuccess) return 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
@@ -113,6 +112,9 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
   DevStatus *st = (DevStatus *)w;
   const int nr = (int)nrhs;
   T *dinv = (T *)(w + L.dinv);
+  static const bool carveout = (set_smem(k_narrow<T>, 0), set_smem(k_update_x<T>, 0), set_smem(k_colmax, 0),
+                                set_smem(k_ir_check, 0), set_smem(k_split_x, 0), true);
+  (void)carveout;
   int *flags = (int *)(w + L.flags);
   EBV_TRY(diag_inverses<T>(F, n, dinv, s));
   if (!refine) {

@@ -217,7 +217,7 @@ ebv_status_t launch_tc(int op, float *C, int64_t ldc, const void *lb, const void
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_tc_update<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<BN>());
+    attr_err = set_smem(k_tc_update<BN>, smem_bytes<BN>());
   });
   if (attr_err != cudaSuccess) return EBV_ERR_CUDA;
   CUtensorMap ma, mb;
