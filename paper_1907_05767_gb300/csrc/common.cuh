@@ -84,6 +84,14 @@ __device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
 // 64-step diagonal-block kernels.
 __device__ __forceinline__ double pivot_rcp(double p) { return 1.0 / p; }
 __device__ __forceinline__ float pivot_rcp(float p) { return __frcp_rn(p); }
+// The same for the short pivot chains of the 16 x 16 warp factorisations:
+// binary32 uses the SFU reciprocal refined by one Newton step (error a few
+// ulp, within the FP32 factors' tolerance), off the IEEE-division slow path.
+__device__ __forceinline__ double pivot_rcp_fast(double p) { return 1.0 / p; }
+__device__ __forceinline__ float pivot_rcp_fast(float p) {
+  const float r = __fdividef(1.f, p);
+  return fmaf(r, fmaf(-p, r, 1.f), r);  // one Newton step: r (2 - p r)
+}
 // A zero or non-finite pivot (tested in the working precision).
 template <typename T>
 __device__ __forceinline__ bool pivot_bad(T p) { return !(p != T(0)) || !isfinite(p); }

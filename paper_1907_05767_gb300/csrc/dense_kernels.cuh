@@ -250,6 +250,7 @@ __device__ __forceinline__ void warp_lu16(T *D, int ld, int o, T *rcp, int w, in
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, p = lane & 7, g = lane >> 3;
   const int c0 = p, c1 = kSB - 1 - p;
+  __syncwarp();  // a converged warp: every shuffle below is then a single step
   T v0[4], v1[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -257,18 +258,16 @@ __device__ __forceinline__ void warp_lu16(T *D, int ld, int o, T *rcp, int w, in
     v1[t] = D[(o + g + 4 * t) * ld + o + c1];
   }
   T rc0 = T(0), rc1 = T(0);
+  int first_bad = kSB;  // kept in registers: no shared-memory traffic on the pivot chain
 #pragma unroll
   for (int r = 0; r < kSB; ++r) {
     const int tr = r >> 2, gr = r & 3;
     const int ps = r < 8 ? r : kSB - 1 - r;  // pair holding column r
     const T pv = __shfl_sync(FULL, r < 8 ? v0[tr] : v1[tr], gr * 8 + ps);
-    const T rc = pivot_rcp(pv);
+    const T rc = pivot_rcp_fast(pv);
     if (c0 == r) rc0 = rc;
     if (c1 == r) rc1 = rc;
-    if (lane == 0) {
-      rcp[o + r] = rc;
-      if (o + r < w && pivot_bad(pv)) atomicMin(bad, o + r);
-    }
+    if (first_bad == kSB && o + r < w && pivot_bad(pv)) first_bad = r;
     if (r == kSB - 1) break;
     T u0 = __shfl_sync(FULL, v0[tr], gr * 8 + p);  // row r, my columns
     T u1 = __shfl_sync(FULL, v1[tr], gr * 8 + p);
@@ -288,6 +287,11 @@ __device__ __forceinline__ void warp_lu16(T *D, int ld, int o, T *rcp, int w, in
     D[(o + i) * ld + o + c0] = i > c0 ? v0[t] * rc0 : v0[t];
     D[(o + i) * ld + o + c1] = i > c1 ? v1[t] * rc1 : v1[t];
   }
+  if (g == 0) {  // lanes 0..7 hold the reciprocals of the column pairs {p, 15-p}
+    rcp[o + c0] = rc0;
+    rcp[o + c1] = rc1;
+  }
+  if (lane == 0 && first_bad < kSB) atomicMin(bad, o + first_bad);
 }
 
 // One warp: inverse of the unit lower (lower = true) or upper triangle of the
@@ -300,6 +304,7 @@ __device__ __forceinline__ void warp_tri_inv16(const T *D, T *Z, int ld, int o, 
   const int lane = threadIdx.x & 31, p = lane & 7, g = lane >> 3;
   const int c0 = p, c1 = kSB - 1 - p;
   T z0[4], z1[4];
+  __syncwarp();  // a converged warp: every shuffle below is then a single step
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     z0[t] = (g + 4 * t == c0) ? T(1) : T(0);
