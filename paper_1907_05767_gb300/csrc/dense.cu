@@ -179,14 +179,11 @@ struct Factorizer {
       const int64_t N = ch - cl;
       if (N >= 64 * 148) {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64><<<ceil_div(N, 64), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
-      } else if constexpr (sizeof(T) == 4) {  // binary32: everything resident in shared memory
-        if (N >= 32 * 148)
-          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 32>
-              <<<ceil_div(N, 32), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 32>(), s>>>(A, r0, (int)h, cl, ch, inv,
-                                                                                         sh);
-        else
-          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 16>
-              <<<ceil_div(N, 16), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 16>(), s>>>(A, r0, (int)h, cl, ch, inv,
+      } else if (sizeof(T) == 4 && A.ld % 4 == 0 && ((uintptr_t)A.base) % 16 == 0) {
+        // binary32 with 16-byte rows: everything resident in shared memory
+        if constexpr (sizeof(T) == 4)
+          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks>
+              <<<ceil_div(N, kResCW), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks>(), s>>>(A, r0, (int)h, cl, ch, inv,
                                                                                          sh);
       } else if (N >= 32 * 148) {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32><<<ceil_div(N, 32), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);

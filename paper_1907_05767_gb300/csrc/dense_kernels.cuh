@@ -698,34 +698,43 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
 constexpr int kTrsmMaxBlocks = 4;  // rows of the one-launch TRSM: up to 4 leaves
 
 // The same TRSM with everything resident in shared memory (binary32, strips
-// of CW <= 32 columns): every tile of L11 it needs -- L_ji (i < j) and the
-// leaf inverses L_jj^{-1} -- and the strip of A12 are copied in at once with
-// cp.async, so the CTA pays one memory latency instead of one per tile; then
-// the blocked forward substitution runs from shared memory only.
-// Dynamic shared memory: trsm_res_smem_bytes<NB, MAXB, CW>().
-template <int NB, int MAXB, int CW>
+// of 16 columns): every tile of L11 it needs -- L_ji (i < j) and the leaf
+// inverses L_jj^{-1} -- and the strip of A12 are copied in at once with
+// 16-byte cp.async, so the CTA pays one memory latency instead of one per
+// tile; then the blocked forward substitution runs from shared memory only.
+// Each product sum over K (sum_{i<j} L_ji U_i, then L_jj^{-1} acc) is split
+// across four groups of 64 threads, each with a 4 x 4 register block over a
+// quarter of K, and reduced through shared memory: a strip this narrow gives
+// one thread too few outputs to keep the FMA pipe busy otherwise.
+// Requires 16-byte aligned rows (ld % 4 == 0, aligned base); the driver
+// falls back to the streaming kernel otherwise.
+// Dynamic shared memory: trsm_res_smem_bytes<NB, MAXB>().
+constexpr int kResCW = 16, kResUS = kResCW + 4;  // strip width, its row stride
+template <int NB, int MAXB>
 constexpr size_t trsm_res_smem_bytes() {
   return sizeof(float) * ((size_t)(MAXB * (MAXB + 1) / 2) * NB * diag_tstride<float, NB>() +
-                          (size_t)MAXB * NB * (CW + 4));
+                          (size_t)MAXB * NB * kResUS + 4 * (size_t)NB * kResUS);
 }
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem)
+// 16-byte asynchronous copy; `bytes` (0..16) of them are read, the rest zero-filled.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(bytes)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
-template <typename SH, int NB, int MAXB, int CW>
+template <typename SH, int NB, int MAXB>
 __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int64_t r0, int h, int64_t c_begin,
                                                           int64_t c_end, const float *inv, Shadow<SH> sh) {
-  static_assert(NB == 64 && CW <= 32, "64-row tiles, narrow strips");
-  constexpr int TS = diag_tstride<float, NB>(), US = CW + 4;
+  static_assert(NB == 64, "64-row tiles");
+  constexpr int TS = diag_tstride<float, NB>(), CW = kResCW, US = kResUS;
   extern __shared__ __align__(16) unsigned char dsm[];
-  float *Lbase = reinterpret_cast<float *>(dsm);                      // tiles of L11, packed by (j, i)
-  float *U = Lbase + (MAXB * (MAXB + 1) / 2) * NB * TS;              // MAXB blocks of 64 x CW
+  float *Lbase = reinterpret_cast<float *>(dsm);           // tiles of L11, packed by (j, i)
+  float *U = Lbase + (MAXB * (MAXB + 1) / 2) * NB * TS;    // MAXB blocks of 64 x CW
+  float *red = U + MAXB * NB * US;                          // 4 partial 64 x CW sums
   auto ltile = [&](int j, int i) { return Lbase + (j * (j + 1) / 2 + i) * NB * TS; };  // i == j: the inverse
   const int64_t c0 = c_begin + (int64_t)blockIdx.x * CW;
   const int wc = (int)min64(CW, c_end - c0);
@@ -735,59 +744,92 @@ __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int6
     const int64_t rj = r0 + (int64_t)j * NB;
     const int hj = min(NB, h - j * NB);
     float *Uj = U + j * NB * US;
-    for (int e = threadIdx.x; e < NB * CW; e += 256) {
-      const int k = e / CW, c = e % CW;
-      if (k < hj && c < wc) cp_async4(Uj + k * US + c, A.base + (rj + k) * A.ld + c0 + c);
-      else Uj[k * US + c] = 0.f;
+    for (int e = threadIdx.x; e < NB * (CW / 4); e += 256) {
+      const int k = e / (CW / 4), c = 4 * (e % (CW / 4));
+      const int nb = (k < hj) ? 4 * max(0, min(4, wc - c)) : 0;
+      cp_async16(Uj + k * US + c, nb ? A.base + (rj + k) * A.ld + c0 + c : A.base, nb);
     }
     for (int i = 0; i < j; ++i) {
       float *Lt = ltile(j, i);
       const int64_t ri = r0 + (int64_t)i * NB;
-      for (int e = threadIdx.x; e < NB * NB; e += 256) {
-        const int k = e / NB, c = e % NB;
-        if (k < hj) cp_async4(Lt + k * TS + c, A.base + (rj + k) * A.ld + ri + c);
-        else Lt[k * TS + c] = 0.f;
+      for (int e = threadIdx.x; e < NB * (NB / 4); e += 256) {
+        const int k = e / (NB / 4), c = 4 * (e % (NB / 4));
+        cp_async16(Lt + k * TS + c, k < hj ? A.base + (rj + k) * A.ld + ri + c : A.base, k < hj ? 16 : 0);
       }
     }
     const float *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
     float *Li = ltile(j, j);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) cp_async4(Li + (e / NB) * TS + e % NB, linv + e);
+    for (int e = threadIdx.x; e < NB * (NB / 4); e += 256) {
+      const int k = e / (NB / 4), c = 4 * (e % (NB / 4));
+      cp_async16(Li + k * TS + c, linv + k * NB + c, 16);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int j = 0; j < nbk; ++j) {
-    float *Uj = U + j * NB * US;
-    float acc[StripMap<CW>::RPT][4];
-    tile_regs<float, US, CW>(Uj, acc);
-    for (int i = 0; i < j; ++i) tile_fma<float, NB, TS, true, CW, US>(ltile(j, i), U + i * NB * US, acc);
-    __syncthreads();  // everyone has read Uj
-    tile_put<float, US, CW>(Uj, acc);
-    __syncthreads();
-    float out[StripMap<CW>::RPT][4];
+  // Thread mapping of the split products: group q = tid / 64 takes a quarter
+  // of K; inside it thread t holds rows t/4 + 16a (a < 4), columns 4 (t % 4) .. +3.
+  const int q = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int pr = t >> 2, pc = 4 * (t & 3);
+  // Final mapping: thread tid holds row tid/4, columns 4 (tid % 4) .. +3.
+  const int fr = threadIdx.x >> 2, fc = 4 * (threadIdx.x & 3);
+  // out = sum over the np products P_m Q_m (P: 64 x 64, stride TS; Q: 64 x CW, stride US).
+  auto split_sum = [&](int np, auto P_of, auto Q_of, float (&out)[4]) {
+    float c[4][4];
 #pragma unroll
-    for (int a = 0; a < StripMap<CW>::RPT; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) out[a][b] = 0.f;
-    // U_j = L_jj^{-1} acc (P rows of stride TS, Q rows of stride US)
-    {
-      using M = StripMap<CW>;
-      const float *P = ltile(j, j);
-      const int ti = threadIdx.x / M::CG, tj = threadIdx.x % M::CG;
-#pragma unroll 8
-      for (int k = 0; k < NB; ++k) {
-        const float4 v = *reinterpret_cast<const float4 *>(Uj + k * US + 4 * tj);
+      for (int b = 0; b < 4; ++b) c[a][b] = 0.f;
+    const int kq = 16 * np;  // this group's share of the np * 64 terms
+    for (int kk = q * kq; kk < (q + 1) * kq; kk += 16) {
+      const float *P = P_of(kk >> 6);
+      const float *Q = Q_of(kk >> 6);
+      const int k0 = kk & 63;
 #pragma unroll
-        for (int a = 0; a < M::RPT; ++a) {
-          const float p = P[(ti + M::RS * a) * TS + k];
-          out[a][0] += p * v.x;
-          out[a][1] += p * v.y;
-          out[a][2] += p * v.z;
-          out[a][3] += p * v.w;
+      for (int k = k0; k < k0 + 16; ++k) {
+        const float4 v = *reinterpret_cast<const float4 *>(Q + k * US + pc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float p = P[(pr + 16 * a) * TS + k];
+          c[a][0] += p * v.x;
+          c[a][1] += p * v.y;
+          c[a][2] += p * v.z;
+          c[a][3] += p * v.w;
         }
       }
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      *reinterpret_cast<float4 *>(red + q * NB * US + (pr + 16 * a) * US + pc) =
+          make_float4(c[a][0], c[a][1], c[a][2], c[a][3]);
     __syncthreads();
-    tile_put<float, US, CW>(Uj, out);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) out[b] = 0.f;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const float4 v = *reinterpret_cast<const float4 *>(red + g * NB * US + fr * US + fc);
+      out[0] += v.x, out[1] += v.y, out[2] += v.z, out[3] += v.w;
+    }
+    __syncthreads();  // red is free again
+  };
+  for (int j = 0; j < nbk; ++j) {
+    float *Uj = U + j * NB * US;
+    float acc[4];
+    {
+      const float4 v = *reinterpret_cast<const float4 *>(Uj + fr * US + fc);
+      acc[0] = v.x, acc[1] = v.y, acc[2] = v.z, acc[3] = v.w;
+    }
+    if (j > 0) {  // acc = A_j - sum_{i<j} L_ji U_i
+      float sum[4];
+      split_sum(j, [&](int m) { return (const float *)ltile(j, m); }, [&](int m) { return (const float *)(U + m * NB * US); },
+                sum);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[b] -= sum[b];
+    }
+    *reinterpret_cast<float4 *>(Uj + fr * US + fc) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    __syncthreads();
+    float out[4];  // U_j = L_jj^{-1} acc
+    split_sum(1, [&](int) { return (const float *)ltile(j, j); }, [&](int) { return (const float *)Uj; }, out);
+    *reinterpret_cast<float4 *>(Uj + fr * US + fc) = make_float4(out[0], out[1], out[2], out[3]);
     __syncthreads();
   }
   for (int j = 0; j < nbk; ++j) {
@@ -807,8 +849,6 @@ __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int6
     }
   }
 }
-
-
 
 // Opt the leaf kernels into more than 48 KB of dynamic shared memory (FP64
 // tiles need 66.5 KB); once per process and instantiation.
@@ -832,9 +872,7 @@ ebv_status_t prepare_leaf_kernels() {
       e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16>, tb);
     if constexpr (sizeof(T) == 4) {
       if (e == cudaSuccess)
-        e = set_smem(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 32>, (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 32>());
-      if (e == cudaSuccess)
-        e = set_smem(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks, 16>, (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks, 16>());
+        e = set_smem(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks>, (int)trsm_res_smem_bytes<kNB, kTrsmMaxBlocks>());
     }
     return e;
   }();
