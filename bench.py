@@ -233,18 +233,18 @@ def run_gpu(args, rank, world, dist):
     prof = ebv.profile_read()
     ebv.profile(False)
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers: ebv_gesv_host
+    # copies A (column blocks, overlapped with the factorisation) and B in,
+    # factors, solves with refinement and copies X back.
     a_host = torch.from_numpy(a_np).pin_memory()
     b_host = torch.from_numpy(b_np).pin_memory()
     x_host = torch.empty_like(b_host).pin_memory()
-    a_dev2 = torch.empty_like(a)
+    rep_host = torch.zeros(32, dtype=torch.uint8).pin_memory()
+    ws_host_path = ebv.gesv_host_workspace(n, nrhs, prec)
 
     def e2e_step():
-        a_dev2.copy_(a_host, non_blocking=True)
-        x.copy_(b_host, non_blocking=True)
-        ebv.ebv_factor(a_dev2, prec, lowp=lowp, info=info, ws=ws)
-        ebv.ebv_solve(lowp, x, prec, a_orig=a_dev2, refine=(TOL, args.max_iter), report=rep, ws=ws, ld=n)
-        x_host.copy_(x, non_blocking=True)
+        ebv.ebv_gesv_host(a_host, b_host, x_host, prec=prec, refine=(TOL, args.max_iter), report_host=rep_host,
+                          ws=ws_host_path)
 
     e2e_step()
     barrier()
@@ -265,7 +265,9 @@ def run_gpu(args, rank, world, dist):
     barrier()
     e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
     e2e_val = world * flops / (e2e_ms / 1e3) / 1e9
-    del a_dev2
+    e2e_rep = ebv.read_report(rep_host)
+    e2e_err = float(np.abs(x_host.numpy() - x_true).max() / np.abs(x_true).max())
+    del ws_host_path
 
     # plain FP64 EbV on the same GPU (same matrix and right-hand sides)
     fp64 = None
@@ -334,7 +336,9 @@ def run_gpu(args, rank, world, dist):
         "kernel_classes_launches": {k: v[2] for k, v in prof.items() if v[2] > 0},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(a_np.nbytes + b_np.nbytes), "d2h_bytes_per_step": int(b_np.nbytes)},
+                "h2d_bytes_per_step": int(a_np.nbytes + b_np.nbytes), "d2h_bytes_per_step": int(b_np.nbytes),
+                "api": "ebv_gesv_host (host A, B -> host X)", "resid_final": e2e_rep["resid_final"],
+                "err_vs_x_true": e2e_err},
         "gpu_launches": int(launches),
         "clocks": clk,
         "input_gen_s": t_gen,

@@ -221,6 +221,40 @@ EBV_API ebv_status_t ebv_solve_adjoint(int64_t batch, int64_t n, int64_t nrhs, c
                                double *grad_a, ebv_stream_t stream);
 
 /*
+ * ebv_gesv_host -- X = A^{-1} B for A and B in HOST memory (Eq. 1 with the
+ * factorisation of Eq. 6-7 and refinement), mixed precisions only
+ * (EBV_MIXED_BF16 / EBV_MIXED_FP16), dense storage.  The host-to-device copy
+ * of A runs on an internal stream, column block by column block, and the
+ * factorisation starts on the first block while the rest is still in
+ * flight (the recursion reaches the columns of A from left to right); then B
+ * is solved and refined exactly as by ebv_factor + ebv_solve, and X is
+ * copied back to x_host.  Everything is ordered on `stream`: the results
+ * (x_host, *report_host, *info_host) are valid once the stream has
+ * completed.  Host buffers should be page-locked for the copies to overlap.
+ *
+ *   a_host      host double*, n x n, leading dimension desc->ld (not modified).
+ *   b_host      host double*, n x nrhs, leading dimension ldb (not modified).
+ *   x_host      host double*, n x nrhs, leading dimension ldb: receives X (may be b_host).
+ *   refine      as for ebv_solve (NULL: the unrefined mixed-precision solve).
+ *   report_host host ebv_refine_report_t (written when refine != NULL; may be NULL).
+ *   info_host   host int32 (may be NULL): 0 or the first bad pivot, as for ebv_factor.
+ *   ws          device workspace of ebv_gesv_host_workspace_size(desc, prec,
+ *               nrhs) bytes, 256-byte aligned: the device copies of A (FP64),
+ *               of the factors (FP32) and of B / X, and the factor / solve
+ *               workspaces.
+ * The first call on a device creates the internal stream and events (make it
+ * before any stream capture); later calls reuse them, so calls on one device
+ * must be ordered (e.g. one stream).  EBV_ERR_UNSUPPORTED for other
+ * precisions or band storage.
+ */
+EBV_API size_t ebv_gesv_host_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64_t nrhs);
+EBV_API ebv_status_t ebv_gesv_host(const ebv_desc_t *desc, ebv_prec_t prec, const double *a_host,
+                                   const double *b_host, double *x_host, int64_t nrhs, int64_t ldb,
+                                   const ebv_refine_t *refine,
+                                   ebv_refine_report_t *report_host, int32_t *info_host, void *ws, size_t ws_bytes,
+                                   ebv_stream_t stream);
+
+/*
  * ebv_solve_static -- ebv_solve without a caller-supplied workspace, for
  * callers that cannot allocate device memory (code running while someone
  * else captures the stream into a CUDA graph, loops whose memory is budgeted

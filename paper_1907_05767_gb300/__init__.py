@@ -70,6 +70,9 @@ _SIGNATURES = [
     ("ebv_factor", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _VP, _SZ, _VP]),
     ("ebv_solve", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _I64, _I64, ctypes.POINTER(Refine), _VP, _VP,
                          _SZ, _VP]),
+    ("ebv_gesv_host_workspace_size", _SZ, [ctypes.POINTER(Desc), _I32, _I64]),
+    ("ebv_gesv_host", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _I64, _I64, ctypes.POINTER(Refine), _VP,
+                             _VP, _VP, _SZ, _VP]),
     ("ebv_solve_static", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _VP, _I64, _I64, ctypes.POINTER(Refine), _VP,
                                 _VP]),
     ("ebv_batch_schedule_len", _I64, [_I64]),
@@ -218,6 +221,45 @@ def ebv_solve(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tens
                            ctypes.byref(ref) if ref is not None else None, _ptr(report), _ptr(ws), ws.numel(),
                            _stream(b.device)), "ebv_solve")
     return b
+
+
+def gesv_host_workspace(n, nrhs, prec="bf16", device="cuda") -> torch.Tensor:
+    d = _desc(n, n)
+    size = lib().ebv_gesv_host_workspace_size(ctypes.byref(d), _prec(prec), nrhs)
+    if size == 0:
+        raise ValueError("ebv_gesv_host supports dense mixed precisions only")
+    return torch.empty(size, dtype=torch.uint8, device=device)
+
+
+def ebv_gesv_host(a_host: torch.Tensor, b_host: torch.Tensor, x_host: torch.Tensor | None = None, prec="bf16",
+                  refine: tuple | None = (1e-12, 10), report_host: torch.Tensor | None = None,
+                  info_host: torch.Tensor | None = None, ws: torch.Tensor | None = None, device="cuda") -> torch.Tensor:
+    """Solve A X = B with A, B in (page-locked) host memory; X lands in
+    ``x_host`` (default: ``b_host``) once the current stream of ``device``
+    completes.  The copy of A overlaps the factorisation.  ``report_host``
+    (uint8, >= 24 bytes) and ``info_host`` (int32) are optional host outputs."""
+    if x_host is None:
+        x_host = b_host
+    for t in (a_host, b_host, x_host):
+        if t.is_cuda or t.dtype != torch.float64:
+            raise ValueError("float64 host tensors expected")
+    n = a_host.shape[0]
+    b2 = b_host if b_host.dim() == 2 else b_host.view(n, 1)
+    x2 = x_host if x_host.dim() == 2 else x_host.view(n, 1)
+    nrhs = b2.shape[1]
+    if x2.shape != b2.shape or x2.stride(0) != b2.stride(0):
+        raise ValueError("x_host must have the shape and row stride of b_host")
+    if ws is None:
+        ws = gesv_host_workspace(n, nrhs, prec, device)
+    d = _desc(n, a_host.stride(0))
+    ref = Refine(float(refine[0]), int(refine[1]), 0) if refine is not None else None
+    _check(lib().ebv_gesv_host(ctypes.byref(d), _prec(prec), ctypes.c_void_p(a_host.data_ptr()),
+                               ctypes.c_void_p(b2.data_ptr()), ctypes.c_void_p(x2.data_ptr()), nrhs, b2.stride(0),
+                               ctypes.byref(ref) if ref is not None else None,
+                               ctypes.c_void_p(report_host.data_ptr()) if report_host is not None else None,
+                               ctypes.c_void_p(info_host.data_ptr()) if info_host is not None else None,
+                               _ptr(ws), ws.numel(), _stream(torch.device(device))), "ebv_gesv_host")
+    return x_host
 
 
 # Limits of ebv_solve_static (its workspace is a fixed device array).

@@ -22,22 +22,64 @@ namespace {
 // Conversion of A to the FP32 working matrix and the power-of-two operand
 // scales of the half-precision tensor-core path.
 // ---------------------------------------------------------------------------
-__global__ void k_to_working(const double *a, int64_t lda, int64_t n, float *w, unsigned int *maxoff,
-                             unsigned int *mindiag) {
+// FP32 working copy of columns [c0, c1) of A (n x n, row-major, leading
+// dimension n for the copy), with the largest off-diagonal and smallest
+// diagonal magnitude folded into maxoff / mindiag.  Rows are strided over the
+// grid, columns over the threads (no index division).
+__global__ void k_to_working(const double *a, int64_t lda, int64_t n, int64_t c0, int64_t c1, float *w,
+                             unsigned int *maxoff, unsigned int *mindiag) {
   unsigned int lmax = 0u, lmin = 0x7F800000u;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, j = e % n;
-    const float v = (float)a[i * lda + j];
-    w[e] = v;
-    const unsigned int bits = __float_as_uint(fabsf(v));
-    if (i == j)
-      lmin = min(lmin, bits);
-    else
-      lmax = max(lmax, bits);
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double *src = a + i * lda;
+    float *dst = w + i * n;
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+      const float v = (float)src[j];
+      dst[j] = v;
+      const unsigned int bits = __float_as_uint(fabsf(v));
+      if (i == j)
+        lmin = min(lmin, bits);
+      else
+        lmax = max(lmax, bits);
+    }
   }
-  atomicMax(maxoff, lmax);
-  atomicMin(mindiag, lmin);
+  for (int off = 16; off > 0; off >>= 1) {
+    lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+    lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(maxoff, lmax);
+    atomicMin(mindiag, lmin);
+  }
 }
+
+// Converts the columns of A into the FP32 working copy in order, as the
+// factorisation first needs them.  With `ev` set, block b of cbw columns is
+// converted only after ev[b] (its host-to-device copy) has completed, so the
+// copy of the right part of A overlaps the factorisation of the left part.
+struct ColumnStager {
+  const double *a;
+  int64_t lda, n;
+  float *w;
+  unsigned int *scan;
+  cudaStream_t s;
+  const cudaEvent_t *ev;  // null: A is already on the device
+  int64_t cbw;
+  bool convert = true;    // false: the copies also wrote the working copy and the scan
+  int64_t done = 0;
+  ebv_status_t ensure(int64_t c_hi) {
+    c_hi = std::min<int64_t>(c_hi, n);
+    while (done < c_hi) {
+      const int64_t c1 = std::min<int64_t>(n, done + cbw);
+      if (ev) EBV_CU(cudaStreamWaitEvent(s, ev[done / cbw], 0));
+      if (convert) {
+        k_to_working<<<(int)std::min<int64_t>(n, 4096), 256, 0, s>>>(a, lda, n, done, c1, w, scan, scan + 1);
+        EBV_TRY(launch_ok());
+      }
+      done = c1;
+    }
+    return EBV_OK;
+  }
+};
 
 // scale = [sL, sU, 1/(sL sU), -].  bfloat16 shares FP32's exponent range and
 // needs no scaling.  For half, L and U entries are bounded here by the largest
@@ -127,6 +169,9 @@ struct Factorizer {
   int op;  // -1: working-precision SIMT updates; 0/1: bf16/half tensor-core updates
   DevStatus *st = nullptr;
   T *inv = nullptr;  // per leaf: L11^{-1} then U11^{-1} (2 * 64 * 64 entries)
+  ColumnStager *stg = nullptr;  // mixed precisions: makes columns available on first use
+
+  ebv_status_t need(int64_t c_hi) { return stg ? stg->ensure(c_hi) : EBV_OK; }
 
   static int64_t split(int64_t w) {  // leaf-aligned first half of a w-wide range
     const int64_t nb = (w + kNB - 1) / kNB;
@@ -136,6 +181,7 @@ struct Factorizer {
 
   ebv_status_t leaf(int64_t c0, int w) {
     constexpr size_t smem = pair_smem_bytes<T, kNB>();
+    EBV_TRY(need(c0 + w));
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
       k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, leaf_inv(c0));
@@ -152,6 +198,7 @@ struct Factorizer {
 
   ebv_status_t gemm(int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K) {
     if (M <= 0 || N <= 0 || K <= 0) return EBV_OK;
+    EBV_TRY(need(n0 + N));
     if (op >= 0)
       return lowp_update(op, (float *)A.base, A.ld, sh.lb, sh.ut, sh.ld, sh.scale, m0, n0, k0, M, N, K, st, s);
     using G = SimtGemm<T>;
@@ -165,6 +212,7 @@ struct Factorizer {
   // U(r0 .. r0+h, cl .. ch) = L(r0.., r0..)^{-1} A(r0.., cl..ch)
   ebv_status_t trsm_ll(int64_t r0, int64_t h, int64_t cl, int64_t ch) {
     if (ch <= cl || h <= 0) return EBV_OK;
+    EBV_TRY(need(ch));
     if (h <= kNB) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * h * h * (ch - cl));
       k_trsm_ll<T, SH, kNB><<<ceil_div(ch - cl, kNB), 256, pair_smem_bytes<T, kNB>(), s>>>(A, r0, (int)h, cl, ch,
@@ -204,6 +252,7 @@ struct Factorizer {
     const int64_t w1 = split(w);
     if (w <= 2 * kNB) {  // two leaves: U12 and the trailing update in one launch
       EBV_TRY(leaf(c0, (int)w1));
+      EBV_TRY(need(c0 + w));
       {
         const int64_t rows = n - c0 - w1;
         prof::Scope ps(s, prof::kTrsm, 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
@@ -249,6 +298,44 @@ size_t dense_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4, true).total;
 }
 
+// Mixed-precision factorisation of A (FP64, device, leading dimension lda)
+// into the FP32 working copy / factors `lowp` (leading dimension n).  ev /
+// cbw: see ColumnStager (null: all of A is already on the device).
+static ebv_status_t dense_factor_mixed(int64_t n, ebv_prec_t prec, const double *a, int64_t lda, float *lowp,
+                                      int32_t *info, char *w, const DenseFactorLayout &L, const cudaEvent_t *ev,
+                                      int64_t cbw, bool convert, cudaStream_t s) {
+  DevStatus *dst = (DevStatus *)w;
+  unsigned int *scan = (unsigned int *)(w + L.scan);
+  float *scale = (float *)(w + L.scale);
+  if (convert) {
+    EBV_CU(cudaMemsetAsync(scan, 0, 4, s));         // max |a_ij|, i != j: starts at +0
+    EBV_CU(cudaMemsetAsync(scan + 1, 0x7F, 4, s));  // min |a_ii|: starts at 0x7F7F7F7F (3.4e38)
+  }
+  static const bool carveout = (set_smem(k_to_working, 0), set_smem(k_make_scale, 0), true);
+  (void)carveout;
+  ColumnStager stg{a, lda, n, lowp, scan, s, ev, ev ? cbw : n, convert};
+  const int op = prec == EBV_MIXED_BF16 ? 0 : 1;
+  // bfloat16 needs no operand scaling; half's scale comes from all of A.
+  if (op == 1) EBV_TRY(stg.ensure(n));
+  k_make_scale<<<1, 1, 0, s>>>(op, scan, scan + 1, scale);
+  EBV_TRY(launch_ok());
+  float *inv = (float *)(w + L.inv);
+  if (op == 0) {
+    EBV_TRY((prepare_leaf_kernels<float, __nv_bfloat16>()));
+    Factorizer<float, __nv_bfloat16> f{
+        dense_view(lowp, n), n, info, s,
+        Shadow<__nv_bfloat16>{(__nv_bfloat16 *)(w + L.lb), (__nv_bfloat16 *)(w + L.ut), L.ldsh, scale}, 0, dst, inv,
+        &stg};
+    EBV_TRY(f.rlu(0, n));
+    return stg.ensure(n);
+  }
+  EBV_TRY((prepare_leaf_kernels<float, __half>()));
+  Factorizer<float, __half> f{dense_view(lowp, n), n, info, s,
+                              Shadow<__half>{(__half *)(w + L.lb), (__half *)(w + L.ut), L.ldsh, scale}, 1, dst, inv,
+                              &stg};
+  return f.rlu(0, n);
+}
+
 ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
                           size_t ws_bytes, cudaStream_t s) {
   const int64_t n = d->n;
@@ -270,30 +357,33 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
     Factorizer<float, float> f{dense_view((float *)a, d->ld), n, info, s, none, -1, dst, (float *)(w + L.inv)};
     return f.rlu(0, n);
   }
-  // Mixed precisions: FP32 working copy in `lowp`, low-precision shadows in ws.
-  unsigned int *scan = (unsigned int *)(w + L.scan);
-  float *scale = (float *)(w + L.scale);
-  EBV_CU(cudaMemsetAsync(scan, 0, 4, s));         // max |a_ij|, i != j: starts at +0
-  EBV_CU(cudaMemsetAsync(scan + 1, 0x7F, 4, s));  // min |a_ii|: starts at 0x7F7F7F7F (3.4e38)
-  static const bool carveout = (set_smem(k_to_working, 0), set_smem(k_make_scale, 0), true);
-  (void)carveout;
-  k_to_working<<<grid_for(n * n), 256, 0, s>>>((const double *)a, d->ld, n, (float *)lowp, scan, scan + 1);
-  EBV_TRY(launch_ok());
-  const int op = prec == EBV_MIXED_BF16 ? 0 : 1;
-  k_make_scale<<<1, 1, 0, s>>>(op, scan, scan + 1, scale);
-  EBV_TRY(launch_ok());
-  float *inv = (float *)(w + L.inv);
-  if (op == 0) {
-    EBV_TRY((prepare_leaf_kernels<float, __nv_bfloat16>()));
-    Factorizer<float, __nv_bfloat16> f{
-        dense_view((float *)lowp, n), n, info, s,
-        Shadow<__nv_bfloat16>{(__nv_bfloat16 *)(w + L.lb), (__nv_bfloat16 *)(w + L.ut), L.ldsh, scale}, 0, dst, inv};
-    return f.rlu(0, n);
-  }
-  EBV_TRY((prepare_leaf_kernels<float, __half>()));
-  Factorizer<float, __half> f{dense_view((float *)lowp, n), n, info, s,
-                              Shadow<__half>{(__half *)(w + L.lb), (__half *)(w + L.ut), L.ldsh, scale}, 1, dst, inv};
-  return f.rlu(0, n);
+  return dense_factor_mixed(n, prec, (const double *)a, d->ld, (float *)lowp, info, w, L, nullptr, 0, true, s);
+}
+
+// Scan words (largest off-diagonal, smallest diagonal magnitude) of the mixed
+// factorisation inside its workspace, initialised on s, for copies that
+// fill the working copy themselves (see ebv_gesv_host).
+unsigned int *dense_factor_scan_init(int64_t n, ebv_prec_t prec, void *ws, cudaStream_t s) {
+  unsigned int *scan = (unsigned int *)((char *)ws + factor_layout(n, prec).scan);
+  if (cudaMemsetAsync(scan, 0, 4, s) != cudaSuccess || cudaMemsetAsync(scan + 1, 0x7F, 4, s) != cudaSuccess)
+    return nullptr;
+  return scan;
+}
+
+// Mixed-precision factorisation whose A is still arriving: block b of cbw
+// columns is on the device once ev[b] has completed (see ebv_gesv_host).
+// convert: the factorisation converts each block to FP32 itself; otherwise
+// the copies already wrote the working copy and the scan words.
+ebv_status_t dense_factor_staged(int64_t n, ebv_prec_t prec, const double *a_dev, float *lowp, int32_t *info,
+                                 void *ws, size_t ws_bytes, const cudaEvent_t *ev, int64_t cbw, bool convert,
+                                 cudaStream_t s) {
+  EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  if (n == 0) return EBV_OK;
+  const DenseFactorLayout L = factor_layout(n, prec);
+  if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
+  if (prec != EBV_MIXED_BF16 && prec != EBV_MIXED_FP16) return EBV_ERR_UNSUPPORTED;
+  return dense_factor_mixed(n, prec, a_dev, n, lowp, info, (char *)ws, L, ev, cbw, convert, s);
 }
 
 // R = B - A X for the dense refinement: on the tensor cores (exact digit

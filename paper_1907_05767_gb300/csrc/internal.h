@@ -21,6 +21,10 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
 ebv_status_t dense_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
                          int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
                          size_t ws_bytes, cudaStream_t s);
+unsigned int *dense_factor_scan_init(int64_t n, ebv_prec_t prec, void *ws, cudaStream_t s);
+ebv_status_t dense_factor_staged(int64_t n, ebv_prec_t prec, const double *a_dev, float *lowp, int32_t *info,
+                                 void *ws, size_t ws_bytes, const cudaEvent_t *ev, int64_t cbw, bool convert,
+                                 cudaStream_t s);
 ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t ws_bytes,
                          cudaStream_t s);
 ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
