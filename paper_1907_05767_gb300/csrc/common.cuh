@@ -27,6 +27,8 @@ struct DevStatus {
   int32_t where;  // kernel-specific detail (e.g. the block that timed out)
   int32_t done;   // refinement: set once the stop test has passed
   int32_t pad;
+  int32_t arrive;  // arrival counter of last-CTA hand-offs; back at 0 when each such launch ends
+  int32_t pad2;
 };
 constexpr size_t kStatusBytes = 256;  // keeps what follows 256-byte aligned
 

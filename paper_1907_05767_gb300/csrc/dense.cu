@@ -257,7 +257,7 @@ struct Factorizer {
         const int64_t rows = n - c0 - w1;
         prof::Scope ps(s, prof::kTrsm, 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
         k_leaf_update<T, SH, kNB><<<ceil_div(rows, kNB), 256, leaf_update_smem_bytes<T, kNB>(), s>>>(
-            A, c0, (int)w1, (int)(w - w1), n, leaf_inv(c0), sh);
+            A, c0, (int)w1, (int)(w - w1), n, leaf_inv(c0), sh, st);
         EBV_TRY(launch_ok());
       }
       return leaf(c0 + w1, (int)(w - w1));

@@ -566,7 +566,10 @@ __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h
 // <= 128): U12 = L11^{-1} A12 for the w2 columns right of the left leaf, and
 // the trailing update A22 -= L21 U12 of every row below, in the working
 // precision.  CTA b owns the 64-row block b of A22; every CTA forms U12 (one
-// tile product) and CTA 0 also stores it (and its low-precision shadow).
+// tile product) from A12.  U12 overwrites A12 in place, so it is stored (with
+// its low-precision shadow) by the CTA that arrives last on st->arrive, once
+// every CTA has read A12: with more CTAs than fit on the GPU at once, a CTA
+// of a later wave would otherwise read U12 where it expects A12.
 // Dynamic shared memory: leaf_update_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
@@ -574,10 +577,11 @@ constexpr size_t leaf_update_smem_bytes() { return 4 * sizeof(T) * (size_t)NB * 
 
 template <typename T, typename SH, int NB>
 __global__ void __launch_bounds__(256) k_leaf_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
-                                                     const T *inv, Shadow<SH> sh) {
+                                                     const T *inv, Shadow<SH> sh, DevStatus *st) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int last;
   T *Li = reinterpret_cast<T *>(dsm);
   T *U12 = Li + NB * TS;
   T *L21 = U12 + NB * TS;
@@ -590,8 +594,13 @@ __global__ void __launch_bounds__(256) k_leaf_update(MatView<T> A, int64_t c0, i
   stage_tile<NB, 256, TS>(L21, [&](int i, int k) { return (i < h && k < w1) ? A.get(r0 + i, c0 + k) : T(0); });
   stage_tile<NB, 256, TS>(C, [&](int i, int j) { return (i < h && j < w2) ? A.get(r0 + i, cb + j) : T(0); });
   __syncthreads();
-  tile_product<T, NB, TS>(Li, U12);  // U12 = L11^{-1} A12 (Eq. 6b)
-  if (blockIdx.x == 0) {
+  if (threadIdx.x == 0) {  // A12 is in shared memory: count this CTA as done reading it
+    __threadfence();
+    last = atomicAdd(&st->arrive, 1) == (int)gridDim.x - 1;
+    if (last) st->arrive = 0;  // every CTA has arrived: ready for the next launch
+  }
+  tile_product<T, NB, TS>(Li, U12);  // U12 = L11^{-1} A12 (Eq. 6b); ends with a barrier
+  if (last) {
     for (int e = threadIdx.x; e < NB * NB; e += 256) {
       const int k = e / NB, j = e % NB;
       if (k < w1 && j < w2) A.put(c0 + k, cb + j, U12[k * TS + j]);

@@ -45,6 +45,30 @@ def test_fp64_factor_solve_matches_oracle(n):
     assert backward_error(a, x, b) <= 1e-14
 
 
+def test_fp64_factor_large_rows_sampled():
+    # n = 10000: the two-leaf panel update launches 156 row blocks, more CTAs
+    # than FP64 tiles fit on the GPU at once, so later CTAs run after the first
+    # ones have finished.  |A - LU| on sampled rows (the last ones included,
+    # which the last CTAs own) stays at the level of FP64 rounding.
+    n = 10_000
+    a = synthetic.dense_dd(n, 0.9, 10_000 + n)
+    x_true = synthetic.planted_x(n, 2, 10_000 + n)
+    b = synthetic.rhs_for(a, x_true)
+    f = ebv.factor(torch.from_numpy(a).to(DEV), "fp64")
+    x = ebv.solve(f, torch.from_numpy(b).to(DEV)).cpu().numpy()
+    assert int(f.info.item()) == 0
+    lu = f.lu.cpu().numpy()
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 16), np.arange(n - 260, n, 13), [0, 63, 64, 127, 128]]))
+    lrows = np.where(np.arange(n)[None, :] < rows[:, None], lu[rows], 0.0)  # strict lower part of L's rows
+    lrows[np.arange(len(rows)), rows] = 1.0
+    lu_rows = lrows @ np.triu(lu)
+    assert np.abs(a[rows] - lu_rows).max() <= 1e-13
+    r = b[rows] - a[rows] @ x
+    assert np.abs(r).max() / (np.abs(a[rows]).sum(axis=1).max() * np.abs(x).max()) <= 1e-14
+    assert np.abs(x - x_true).max() <= 1e-11
+
+
 @pytest.mark.parametrize("n", [5, 64, 130, 333])
 def test_fp32_factor_solve_matches_oracle(n):
     a = synthetic.dense_dd(n, 0.9, 20_000 + n)
