@@ -423,6 +423,214 @@ def run_update_only(args):
 
 
 # ----------------------------------------------------------------------------
+# --configs: the other workloads (parity cases of the test suite), one JSON
+# line each, for the results table; not the bench line
+# ----------------------------------------------------------------------------
+
+def _dev_ms(fn, steps, warmup, graph=True):
+    """Device ms per call of fn (CUDA events on the launching stream), replayed
+    from a CUDA graph unless graph is False."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    run = fn
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        g.replay()
+        torch.cuda.synchronize()
+        run = g.replay
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_configs(args):
+    import torch
+
+    import oracle
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    dev = torch.device("cuda")
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    out = []
+
+    # n = 256 dense FP64, one RHS (L2-resident: the whole problem is 0.5 MB)
+    a, x_true, b = synthetic.config0()
+    n = a.shape[0]
+    A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    lu, x = torch.empty_like(A), torch.empty_like(B)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ebv.workspace(n, "fp64", 1, dev)
+
+    def c0():
+        lu.copy_(A)
+        x.copy_(B)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=ws)
+        ebv.ebv_solve(lu, x, "fp64", ws=ws)
+
+    ms = _dev_ms(c0, 200, 10)
+    x_ref = oracle.solve(oracle.lu(a)[0], b)
+    xs = x.cpu().numpy()
+    r = oracle.residual(a, xs, b)
+    out.append({"config": "dense FP64 n=256, 1 RHS", "ms": ms, "solves_per_s": 1e3 / ms,
+                "gflops": nominal_flops(n, 1) / (ms / 1e3) / 1e9,
+                "x_relerr_vs_oracle": float(np.abs(xs - x_ref).max() / np.abs(x_ref).max()),
+                "backward_error": float(np.abs(r).max() / (np.abs(a).sum(axis=1).max() * np.abs(xs).max())),
+                "note": "whole problem L2-resident; launch-latency bound (CUDA graph)"})
+    print(json.dumps(out[-1]), flush=True)
+
+    # banded FP64 5-point Laplacian on a 512 x 512 grid, 8 RHS
+    ab, kl, ku, x_true, b = synthetic.config1()
+    n = ab.shape[0]
+    AB, B = torch.from_numpy(ab).to(dev), torch.from_numpy(b).to(dev)
+    lu, x = torch.empty_like(AB), torch.empty_like(B)
+    ws = ebv.workspace(n, "fp64", b.shape[1], dev, kl=kl, ku=ku, storage=ebv.BAND)
+
+    def c1():
+        lu.copy_(AB)
+        x.copy_(B)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
+        ebv.ebv_solve(lu, x, "fp64", ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
+
+    ms = _dev_ms(c1, 3, 2)
+    xs = x.cpu().numpy()
+    rows = synthetic.pick_indices(11, 512, [n])[:, 0]
+    r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
+    flops = 2.0 * n * kl * ku + 2.0 * n * (kl + ku) * b.shape[1]
+    out.append({"config": "band FP64 Laplacian 512x512 (n=262144, kl=ku=512), 8 RHS", "ms": ms,
+                "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
+                "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
+                "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
+                "band_bytes": int(ab.nbytes), "info": int(info.item())})
+    print(json.dumps(out[-1]), flush=True)
+    del AB, B, lu, x, ws
+
+    # dense n = 16384, 32 RHS: FP16 updates + refinement (bf16 is the bench line)
+    a, x_true, b = synthetic.config2(args.n, args.nrhs)
+    n, nrhs = a.shape[0], b.shape[1]
+    A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    lowp = torch.empty((n, n), dtype=torch.float32, device=dev)
+    x = torch.empty_like(B)
+    rep = torch.zeros(3, dtype=torch.float64, device=dev)
+    ws = ebv.workspace(n, "fp16", nrhs, dev)
+
+    def c2():
+        x.copy_(B)
+        ebv.ebv_factor(A, "fp16", lowp=lowp, info=info, ws=ws)
+        ebv.ebv_solve(lowp, x, "fp16", a_orig=A, refine=(TOL, args.max_iter), report=rep, ws=ws, ld=n)
+
+    ms = _dev_ms(c2, 3, 3)
+    rp = ebv.read_report(rep)
+    xs = x.cpu().numpy()
+    out.append({"config": f"dense n={n}, {nrhs} RHS, fp16 tensor-core updates + FP64 refinement", "ms": ms,
+                "solves_per_s": 1e3 / ms, "gflops": nominal_flops(n, nrhs) / (ms / 1e3) / 1e9,
+                "refine_iters": rp["iters"], "resid_first": rp["resid_first"], "resid_final": rp["resid_final"],
+                "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max())})
+    print(json.dumps(out[-1]), flush=True)
+    del A, B, lowp, x, ws
+
+    # batched: 4096 systems, n ~ U{16..512}, 1-4 RHS, FP64 and FP32
+    ns, rs = synthetic.config3_sizes()
+    systems = [synthetic.config3_system(s, int(ns[s]), int(rs[s])) for s in range(len(ns))]
+    flops = float(sum(nominal_flops(int(nn), int(rr)) for nn, rr in zip(ns, rs)))
+    pick = synthetic.pick_indices(99, 16, [len(ns)])[:, 0]
+    for prec in ("fp64", "fp32"):
+        bt = ebv.Batch(ns, rs, prec)
+        for s, (a, _, b) in enumerate(systems):
+            bt.a_view(s).copy_(torch.from_numpy(a))
+            bt.b_view(s).copy_(torch.from_numpy(b))
+        a0, b0 = bt.a_buf.clone(), bt.b_buf.clone()
+
+        def restore():
+            bt.a_buf.copy_(a0)
+            bt.b_buf.copy_(b0)
+
+        def c3():
+            restore()
+            bt.run()
+
+        ms_restore = _dev_ms(restore, 10, 3)
+        ms_all = _dev_ms(c3, 10, 3)  # last: the buffers hold the factors and X
+        err = 0.0
+        for s in pick:
+            _, xt, _ = systems[s]
+            err = max(err, float(np.abs(bt.b_view(int(s)).double().cpu().numpy() - xt).max() / np.abs(xt).max()))
+        ms_run = ms_all - ms_restore
+        line = {"config": f"batched 4096 systems n~U{{16..512}}, 1-4 RHS, {prec}", "ms": ms_run,
+                "ms_incl_restore": ms_all, "solves_per_s": len(ns) * 1e3 / ms_run,
+                "gflops": flops / (ms_run / 1e3) / 1e9, "launches": 1,
+                "err_vs_x_true_sampled": err, "info_max": int(bt.info.abs().max())}
+        if prec == "fp64":
+            # the same systems one at a time through ebv_factor + ebv_solve
+            wsp = ebv.workspace(512, "fp64", 4, dev)
+            views = [(bt.a_view(s), bt.b_view(s)) for s in range(len(ns))]
+            restore()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for av, bv in views:
+                ebv.ebv_factor(av, "fp64", info=info, ws=wsp)
+                ebv.ebv_solve(av, bv, "fp64", ws=wsp)
+            e1.record()
+            torch.cuda.synchronize()
+            line["per_system_launches_ms"] = e0.elapsed_time(e1)
+            line["speedup_vs_per_system"] = line["per_system_launches_ms"] / ms_run
+        out.append(line)
+        print(json.dumps(out[-1]), flush=True)
+        del bt, a0, b0
+    del systems
+
+    # differentiable batch: 256 FP64 systems n = 1024, 4 RHS; forward + adjoint
+    nb, n, nrhs = 256, 1024, 4
+    data = [synthetic.config4_system(i, n, nrhs) for i in range(nb)]
+    A = torch.from_numpy(np.stack([d[0] for d in data])).to(dev)
+    B = torch.from_numpy(np.stack([d[2] for d in data])).to(dev)
+    W = torch.from_numpy(np.stack([d[3] for d in data])).to(dev)
+    lu, x = torch.empty_like(A), torch.empty_like(B)
+    bt = ebv.uniform_batch(lu, x)
+
+    def fwd():
+        lu.copy_(A)
+        x.copy_(B)
+        bt.run()
+
+    ms_copy = _dev_ms(lambda: (lu.copy_(A), x.copy_(B)), 5, 2)
+    ms_f = _dev_ms(fwd, 5, 2)  # last: lu and x hold the factors and X
+    g_b, g_a = ebv.ebv_solve_adjoint(lu, x, W)
+    torch.cuda.synchronize()
+    ms_b = _dev_ms(lambda: ebv.ebv_solve_adjoint(lu, x, W), 5, 2, graph=False)
+    err = 0.0
+    for i in synthetic.pick_indices(5, 3, [nb])[:, 0]:
+        luo = oracle.lu(data[i][0])[0]
+        xo = oracle.solve(luo, data[i][2])
+        gbo, gao = oracle.adjoint(luo, xo, data[i][3])
+        err = max(err, float(np.abs(g_b[i].cpu().numpy() - gbo).max() / np.abs(gbo).max()),
+                  float(np.abs(g_a[i].cpu().numpy() - gao).max() / np.abs(gao).max()))
+    bwd_bytes = nb * (8.0 * n * n * 2)  # read the factors, write grad_A
+    out.append({"config": "adjoint batch 256 x FP64 n=1024, 4 RHS", "ms_forward": ms_f - ms_copy,
+                "ms_backward": ms_b, "forward_gflops": nb * nominal_flops(n, nrhs) / ((ms_f - ms_copy) / 1e3) / 1e9,
+                "backward_gbs": bwd_bytes / (ms_b / 1e3) / 1e9, "backward_hbm_frac": bwd_bytes / (ms_b / 1e3) / 1e9 / hbm,
+                "grad_relerr_vs_oracle_sampled": err, "info_max": int(bt.info.abs().max())})
+    print(json.dumps(out[-1]), flush=True)
+    return out
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the CPU oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------
 
@@ -464,9 +672,13 @@ def main():
     p.add_argument("--ref-kstop", type=int, default=96)
     p.add_argument("--no-graph", dest="graph", action="store_false")
     p.add_argument("--update-only", default=None, help="M,N,K: time the tensor-core update alone and exit")
+    p.add_argument("--configs", action="store_true", help="time the other workloads (one JSON line each) and exit")
     args = p.parse_args()
     if args.update_only:
         print(json.dumps(run_update_only(args)), flush=True)
+        return
+    if args.configs:
+        run_configs(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))
