@@ -43,14 +43,24 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
     }
     const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
     const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
+    // FP64: 16-row / 16-column strips, four times the CTAs of one 64 x 64
+    // tile each (a band has only kl rows / ku columns per step).
     if (re > rb) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * (re - rb) * w * w);
-      k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
+      if constexpr (sizeof(T) == 8)
+        k_trsm_ru_strip<T, float, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
+      else
+        k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
       EBV_TRY(launch_ok());
     }
     if (ce > cb) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * w * w * (ce - cb));
-      k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, kNB), 256, smem, s>>>(A, c0, w, cb, ce, inv, none);
+      if constexpr (sizeof(T) == 8)
+        k_trsm_ll_multi<T, float, kNB, kTrsmMaxBlocks, 16>
+            <<<ceil_div(ce - cb, 16), 256, trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>(), s>>>(A, c0, w, cb, ce,
+                                                                                               inv, none);
+      else
+        k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, kNB), 256, smem, s>>>(A, c0, w, cb, ce, inv, none);
       EBV_TRY(launch_ok());
     }
     if (re > rb && ce > cb) {

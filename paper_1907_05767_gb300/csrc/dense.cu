@@ -190,7 +190,10 @@ struct Factorizer {
     const int64_t rb = c0 + w, re = n;
     if (re > rb) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * (re - rb) * w * w);
-      k_trsm_ru<T, SH, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
+      if (sizeof(T) == 8 && ceil_div(re - rb, kNB) < 152)  // FP64, fewer 64-row tiles than SMs: 16-row strips
+        k_trsm_ru_strip<T, SH, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
+      else
+        k_trsm_ru<T, SH, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
       EBV_TRY(launch_ok());
     }
     return EBV_OK;
@@ -226,17 +229,17 @@ struct Factorizer {
       constexpr size_t smem = trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
       const int64_t N = ch - cl;
       if (N >= 64 * 148) {
-        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64><<<ceil_div(N, 64), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
+        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64><<<ceil_div(N, 64), 256, smem, s>>>(A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
       } else if (sizeof(T) == 4 && A.ld % 4 == 0 && ((uintptr_t)A.base) % 16 == 0) {
         // binary32 with 16-byte rows: everything resident in shared memory
         if constexpr (sizeof(T) == 4)
           k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks>
-              <<<ceil_div(N, kResCW), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks>(), s>>>(A, r0, (int)h, cl, ch, inv,
-                                                                                         sh);
+              <<<ceil_div(N, kResCW), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks>(), s>>>(
+                  A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
       } else if (N >= 32 * 148) {
-        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32><<<ceil_div(N, 32), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
+        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32><<<ceil_div(N, 32), 256, smem, s>>>(A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
       } else {
-        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16><<<ceil_div(N, 16), 256, smem, s>>>(A, r0, (int)h, cl, ch, inv, sh);
+        k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 16><<<ceil_div(N, 16), 256, smem, s>>>(A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
       }
       return launch_ok();
     }

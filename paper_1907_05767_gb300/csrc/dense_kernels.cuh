@@ -528,6 +528,40 @@ __global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w
   }
 }
 
+// The same L21 for RW-row strips (RW = 16 or 32): more CTAs for few rows, for
+// the FP64 paths, where one SM's FP64 rate makes a whole 64 x 64 x 64 tile
+// product per CTA slow.  Computed transposed, (L21)^T = (U11^{-1})^T A21^T,
+// so the strip is the tile product's column strip.
+// Dynamic shared memory: pair_smem_bytes<T, NB>().
+template <typename T, typename SH, int NB, int RW>
+__global__ void __launch_bounds__(256) k_trsm_ru_strip(MatView<T> A, int64_t k0, int w, int64_t r_begin,
+                                                       int64_t r_end, const T *inv, Shadow<SH> sh) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>();
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T *UiT = reinterpret_cast<T *>(dsm);  // (U11^{-1})^T
+  T *AtT = UiT + NB * TS;               // A21 strip transposed: 64 x RW in a 64 x TS buffer
+  const int64_t r0 = r_begin + (int64_t)blockIdx.x * RW;
+  const int h = (int)min64(RW, r_end - r0);
+  const T *uinv = inv + NB * NB;
+  stage_tile<NB, 256, TS>(UiT, [&](int i, int k) { return uinv[k * NB + i]; });
+  for (int e = threadIdx.x; e < NB * RW; e += 256) {
+    const int i = e / NB, k = e % NB;
+    AtT[k * TS + i] = (i < h && k < w) ? A.get(r0 + i, k0 + k) : T(0);
+  }
+  __syncthreads();
+  tile_product<T, NB, TS, RW>(UiT, AtT);  // AtT <- UiT * AtT
+  const float s = sh.lb ? sh.scale[0] : 1.f;
+  for (int e = threadIdx.x; e < NB * RW; e += 256) {
+    const int i = e / NB, k = e % NB;
+    if (i < h && k < w) {
+      const T v = AtT[k * TS + i];
+      A.put(r0 + i, k0 + k, v);
+      if (sh.lb) sh.lb[(r0 + i) * sh.ld + k0 + k] = from_float<SH>((float)v * s);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // U12 = L11^{-1} A12: the U vectors of the block's h rows for the columns
 // c_begin..c_end-1 (Eq. 6b for every column at once), one h x 64 tile per CTA
@@ -634,6 +668,8 @@ __global__ void __launch_bounds__(256) k_leaf_update(MatView<T> A, int64_t c0, i
 // working precision.  Replaces the recursive split of small TRSMs (a leaf
 // launch and a low-precision GEMM per level) by one launch.  Also writes the
 // scaled low-precision shadow of U^T.
+// inv: the leaves' inverse slots from row r0 on (slot j, rows r0 + 64 j ..,
+// at inv + 2 * NB * NB * j; L^{-1} first).
 // Dynamic shared memory: trsm_multi_smem_bytes<T, NB, MAXB>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB, int MAXB>
@@ -664,7 +700,7 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
       const int64_t ri = r0 + (int64_t)(pos - 1) * NB;
       fetch_tile<NB, 256>(pf, [&](int k, int c) { return k < hj ? A.get(rj + k, ri + c) : T(0); });
     } else {
-      const T *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
+      const T *linv = inv + (int64_t)j * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
       fetch_tile<NB, 256>(pf, [&](int k, int c) { return linv[k * NB + c]; });
     }
   };
@@ -766,7 +802,7 @@ __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int6
         cp_async16(Lt + k * TS + c, k < hj ? A.base + (rj + k) * A.ld + ri + c : A.base, k < hj ? 16 : 0);
       }
     }
-    const float *linv = inv + (rj / NB) * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
+    const float *linv = inv + (int64_t)j * 2 * NB * NB;  // the leaf slot of columns rj..rj+63
     float *Li = ltile(j, j);
     for (int e = threadIdx.x; e < NB * (NB / 4); e += 256) {
       const int k = e / (NB / 4), c = 4 * (e % (NB / 4));
@@ -870,6 +906,8 @@ ebv_status_t prepare_leaf_kernels() {
       e = set_smem(k_trsm_ru<T, SH, kNB>, bytes);
     if (e == cudaSuccess)
       e = set_smem(k_trsm_ll<T, SH, kNB>, bytes);
+    if (e == cudaSuccess)
+      e = set_smem(k_trsm_ru_strip<T, SH, kNB, 16>, bytes);
     if (e == cudaSuccess)
       e = set_smem(k_leaf_update<T, SH, kNB>, (int)leaf_update_smem_bytes<T, kNB>());
     const int tb = (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
