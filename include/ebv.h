@@ -277,7 +277,7 @@ EBV_API ebv_status_t ebv_gesv_host(const ebv_desc_t *desc, ebv_prec_t prec, cons
  * to start at zero): calls whose work overlaps on the GPU (other streams,
  * other host threads without ordering) race and give undefined results.
  */
-#define EBV_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+#define EBV_STATIC_SCRATCH_BYTES ((size_t)20 << 20)
 #define EBV_STATIC_MAX_N 4096
 #define EBV_STATIC_MAX_NRHS 32
 EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu,

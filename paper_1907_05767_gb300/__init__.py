@@ -263,7 +263,7 @@ def ebv_gesv_host(a_host: torch.Tensor, b_host: torch.Tensor, x_host: torch.Tens
 
 
 # Limits of ebv_solve_static (its workspace is a fixed device array).
-STATIC_SCRATCH_BYTES = 16 << 20
+STATIC_SCRATCH_BYTES = 20 << 20
 STATIC_MAX_N = 4096
 STATIC_MAX_NRHS = 32
 

@@ -9,29 +9,35 @@
 namespace ebv {
 namespace {
 
-// Right-hand sides per substitution chain: each chunk of RC columns is solved
-// by its own chain of CTAs, so 32 columns make 4 chains whose per-step
-// critical work is a quarter of one.
+// Right-hand sides per substitution chain (RC): each chunk of RC columns is
+// solved by its own chain of CTAs.  One chain of 32 reads the factors once
+// and, up to n = 64 x (resident CTAs), gives every CTA a single row block,
+// so no CTA has a backlog of folds when its block's turn comes.
+// NS: stages of the factor-tile ring; MINB: CTAs per SM the kernel is
+// compiled for (binary32: two 91 KB CTAs per SM).
 template <typename T>
 struct TrsvCfg {
-  static constexpr int RC = 8;
+  static constexpr int RC = 32;
+  static constexpr int NS = sizeof(T) == 4 ? 3 : 2;
+  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
 };
 
 struct DenseSolveLayout {
-  size_t dinv, flags, bsave, r, corr, xhi, xlo, rmax, bmax, tcres, total;
+  size_t dinv, xw, bsave, r, corr, xhi, xlo, rmax, bmax, tcres, total;
 };
 
 // Solve workspace: status block, inverses of the diagonal blocks of both
-// factors, per-step flags of the two substitutions, refinement buffers (and,
+// factors, the substitutions' published blocks, refinement buffers (and,
 // for the dense path, the tensor-core residual's exponents and digit planes).
 DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize, bool tc_residual = false) {
   DenseSolveLayout L{};
   size_t off = kStatusBytes;
   const size_t nn = (size_t)n * (size_t)std::max<int64_t>(nrhs, 1);
   const size_t nblk = (size_t)std::max<int64_t>(1, (n + kNB - 1) / kNB);
-  const size_t nchunk = (size_t)std::max<int64_t>(1, (nrhs + 7) / 8);  // RC >= 8 for every type
+  const size_t rcols = (size_t)std::max<int64_t>(1, (nrhs + 31) / 32) * 32;  // nrhs rounded up to chunks of 32
   L.dinv = off; off = align256(off + nblk * 4 * kNB * kNB * tsize);
-  L.flags = off; off = align256(off + 2 * nchunk * nblk * sizeof(int));
+  // published solution blocks of the substitutions (tagged words; both triangles use it in turn)
+  L.xw = off; off = align256(off + rcols * nblk * kNB * (tsize / 4) * sizeof(unsigned long long));
   L.bsave = off; off = align256(off + nn * 8);
   L.r = off; off = align256(off + nn * 8);
   L.corr = off; off = align256(off + nn * tsize);
@@ -58,13 +64,14 @@ ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
 
 // One triangle of the substitution as a cooperative persistent launch: at
 // most as many CTAs per right-hand-side chunk as can be resident at once
-// (the CTAs wait on one another's flags).
+// (the CTAs wait on one another's published blocks).
 template <typename T, bool UPPER>
-ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
-                      DevStatus *st, cudaStream_t s) {
-  constexpr int RC = TrsvCfg<T>::RC;
-  constexpr size_t smem = trsvl_smem_bytes<T, kNB, RC>();
-  auto kern = k_trsv_left<T, kNB, RC, UPPER>;
+ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+                      unsigned long long *xw, DevStatus *st, cudaStream_t s) {
+  using C = TrsvCfg<T>;
+  constexpr int RC = C::RC;
+  constexpr size_t smem = trsvl_smem_bytes<T, kNB, RC, C::NS>();
+  auto kern = k_trsv_left<T, kNB, RC, UPPER, C::NS, C::MINB>;
   static int resident = [&] {
     int dev = 0, sms = 0, per_sm = 0;
     if (set_smem(kern, (int)smem) != cudaSuccess) return 0;
@@ -76,7 +83,7 @@ ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, cons
   const int nblk = ceil_div(n, kNB), nchunk = ceil_div(nrhs, RC);
   if (resident < nchunk) return EBV_ERR_UNSUPPORTED;
   const int G = std::max(1, std::min(resident / nchunk, nblk));
-  EBV_CU(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)nchunk * nblk, s));
+  EBV_CU(cudaMemsetAsync(xw, 0, sizeof(unsigned long long) * (size_t)nchunk * nblk * kNB * RC * XWords<T>::W, s));
   prof::Scope ps(s, prof::kTrsv, (double)n * n * nrhs);  // nominal n^2 flops per right-hand side
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(G * nchunk));
@@ -88,17 +95,16 @@ ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, cons
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  EBV_CU(cudaLaunchKernelEx(&cfg, kern, F, n, B, ldb, nrhs, dinv, flags, st));
+  EBV_CU(cudaLaunchKernelEx(&cfg, kern, F, n, B, ldb, nrhs, dinv, xw, st));
   return launch_ok();
 }
 
 // Forward then backward block substitution of B (n x nrhs, T) in place.
 template <typename T>
-ebv_status_t trsv_pair(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags,
-                       DevStatus *st, cudaStream_t s) {
-  const int nblk = ceil_div(n, kNB), nchunk = ceil_div(nrhs, TrsvCfg<T>::RC);
-  EBV_TRY((trsv_one<T, false>(F, n, B, ldb, nrhs, dinv, flags, st, s)));
-  return trsv_one<T, true>(F, n, B, ldb, nrhs, dinv, flags + (size_t)nchunk * nblk, st, s);
+ebv_status_t trsv_pair(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+                       unsigned long long *xw, DevStatus *st, cudaStream_t s) {
+  EBV_TRY((trsv_one<T, false>(F, n, B, ldb, nrhs, dinv, xw, st, s)));
+  return trsv_one<T, true>(F, n, B, ldb, nrhs, dinv, xw, st, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -115,15 +121,15 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
   static const bool carveout = (set_smem(k_narrow<T>, 0), set_smem(k_update_x<T>, 0), set_smem(k_colmax, 0),
                                 set_smem(k_ir_check, 0), set_smem(k_split_x, 0), true);
   (void)carveout;
-  int *flags = (int *)(w + L.flags);
+  unsigned long long *xw = (unsigned long long *)(w + L.xw);
   EBV_TRY(diag_inverses<T>(F, n, dinv, s));
   if (!refine) {
-    if (b_is_double == (sizeof(T) == 8)) return trsv_pair<T>(F, n, (T *)b, ldb, nr, dinv, flags, st, s);
+    if (b_is_double == (sizeof(T) == 8)) return trsv_pair<T>(F, n, (T *)b, ldb, nr, dinv, xw, st, s);
     // FP32 factors applied to FP64 right-hand sides (mixed precisions, no refinement).
     T *c = (T *)(w + L.corr);
     k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>((const double *)b, ldb, c, nrhs, n, nr, st);
     EBV_TRY(launch_ok());
-    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, flags, st, s));
+    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, xw, st, s));
     k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>((double *)b, ldb, c, nrhs, n, nr, 0, st);
     return launch_ok();
   }
@@ -141,7 +147,7 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
   // x0 from the factors.
   k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>(bsave, nrhs, c, nrhs, n, nr, st);
   EBV_TRY(launch_ok());
-  EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, flags, st, s));
+  EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, xw, st, s));
   k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, c, nrhs, n, nr, 0, st);
   EBV_TRY(launch_ok());
   const int max_iter = std::max(0, refine->max_iter);
@@ -153,7 +159,7 @@ ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64
     if (it == max_iter) break;
     k_narrow<T><<<grid_for(n * nrhs), 256, 0, s>>>(r, nrhs, c, nrhs, n, nr, st);
     EBV_TRY(launch_ok());
-    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, flags, st, s));
+    EBV_TRY(trsv_pair<T>(F, n, c, nrhs, nr, dinv, xw, st, s));
     k_update_x<T><<<grid_for(n * nrhs), 256, 0, s>>>(x, ldb, c, nrhs, n, nr, 1, st);
     EBV_TRY(launch_ok());
   }

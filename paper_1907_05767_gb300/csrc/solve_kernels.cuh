@@ -61,44 +61,155 @@ __global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Published solution blocks: every entry of a finished block X_s goes out as
+// 8-byte words {32 value bits, tag s + 1} (one word per binary32 value, two
+// per binary64), written with single stores that are atomic as a whole.  A
+// reader that sees the tag has the value: no fence on the writer's side and
+// no separate flag to read first, so a block reaches the next step one L2
+// round trip after it is stored.  The buffer is zeroed before each launch,
+// so no tag survives from an earlier solve.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct XWords {
+  static constexpr int W = sizeof(T) / 4;
+};
+__device__ __forceinline__ void xw_store(unsigned long long *p, uint32_t bits, uint32_t tag) {
+  const unsigned long long v = ((unsigned long long)tag << 32) | bits;
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long xw_load(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void xw_put(unsigned long long *p, float v, uint32_t tag) {
+  xw_store(p, __float_as_uint(v), tag);
+}
+__device__ __forceinline__ void xw_put(unsigned long long *p, double v, uint32_t tag) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  xw_store(p, (uint32_t)u, tag);
+  xw_store(p + 1, (uint32_t)(u >> 32), tag);
+}
+// The value of an entry's words if every word carries tag.
+__device__ __forceinline__ bool xw_decode(const unsigned long long (&w)[1], uint32_t tag, float &v) {
+  v = __uint_as_float((uint32_t)w[0]);
+  return (uint32_t)(w[0] >> 32) == tag;
+}
+__device__ __forceinline__ bool xw_decode(const unsigned long long (&w)[2], uint32_t tag, double &v) {
+  v = __longlong_as_double((long long)(((w[1] & 0xFFFFFFFFull) << 32) | (w[0] & 0xFFFFFFFFull)));
+  return (uint32_t)(w[0] >> 32) == tag && (uint32_t)(w[1] >> 32) == tag;
+}
+// One attempt: true (and the value) once every word of the entry carries tag.
+__device__ __forceinline__ bool xw_try(const unsigned long long *p, uint32_t tag, float &v) {
+  const unsigned long long w = xw_load(p);
+  if ((uint32_t)(w >> 32) != tag) return false;
+  v = __uint_as_float((uint32_t)w);
+  return true;
+}
+__device__ __forceinline__ bool xw_try(const unsigned long long *p, uint32_t tag, double &v) {
+  const unsigned long long w0 = xw_load(p), w1 = xw_load(p + 1);
+  if ((uint32_t)(w0 >> 32) != tag || (uint32_t)(w1 >> 32) != tag) return false;
+  v = __longlong_as_double((long long)(((w1 & 0xFFFFFFFFull) << 32) | (w0 & 0xFFFFFFFFull)));
+  return true;
+}
+// Bounded wait for one entry, with the same limits and early exit as
+// bounded_wait_geq.  On expiry records EBV_ERR_TIMEOUT with `where`.
+template <typename T>
+__device__ __forceinline__ bool xw_wait(const unsigned long long *p, uint32_t tag, T &v, DevStatus *st,
+                                        int where) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (xw_try(p, tag, v)) return true;
+    if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) return false;
+    if (it >= 32) __nanosleep(64);
+  }
+  set_status(st, EBV_ERR_TIMEOUT, where);
+  return false;
+}
+
+// ---------------------------------------------------------------------------
 // Block substitution in one cooperative launch per triangle (Eq. 1: LY = B,
 // then UX = Y), left-looking.  Steps t = 0..nblk-1 visit the row blocks in
 // solve order (increasing for L, decreasing for U); each chunk of RC
 // right-hand sides is an independent chain of CTAs.  CTA h of a chain owns
 // the steps t = h (mod G) and takes them in order: for its block t it folds
-// the published blocks s < t into a register accumulator, acc -= F(t,s) X_s,
-// in the order they were published, then X_t = D_t^{-1} acc (a tile product
-// with the diagonal-block inverse) and releases flag t.  Only the owner ever
-// touches block t of B, nothing is written back between folds, and a CTA
-// never works on a later block while its current one could advance, so the
-// critical path per step is: flag t-1 seen -> X_{t-1} read from L2 -> one
-// 64 x 64 x RC fold -> one 64 x 64 x RC solve -> store + release.  The next
-// factor tile is fetched into registers while the current fold runs (and
-// while the CTA waits).  Every wait is bounded and gives up once the
-// workspace status reports an error.  All CTAs must be co-resident: the driver
-// launches at most the occupancy limit, cooperatively.
-// Dynamic shared memory: trsvl_smem_bytes<T, NB, RC>().
+// the published blocks s < t-1 into a register accumulator, acc -= F(t,s)
+// X_s, in the order they were published, applies the diagonal-block inverse
+// (y = D_t^{-1} acc, a tile product) before block t-1 exists, and once X_{t-1}
+// is there only does X_t = y - (D_t^{-1} F(t,t-1)) X_{t-1}, then publishes
+// X_t (tagged words, above) and writes it to B.  Only the owner ever touches
+// block t of B, and a CTA never works on a later block while its current one
+// could advance, so the critical path per step is: X_{t-1}'s words seen ->
+// one 64 x 64 x RC product -> X_t stored.
+// The factor tiles F(t, s) and the coupling tile stream through an NS-stage
+// shared-memory ring filled by 16-byte cp.async (16-byte chunks XOR-swizzled
+// by row, so the fold's column reads hit distinct banks); band views and
+// unaligned rows fill the ring with plain loads instead.  Published entries
+// of an earlier block are taken with one attempt each; only if one is
+// missing does thread 0 poll for the block (one poller per CTA at the front
+// of the chain) before every thread waits for its own.  At the last step
+// every thread waits for its entries of X_{t-1} directly.  Every wait is
+// bounded and gives up once the workspace status reports an error.  All
+// CTAs must be co-resident: the driver launches at most the occupancy limit,
+// cooperatively.
+// xw: nchunk * nblk * NB * RC entries of XWords<T>::W words, zeroed.
+// Dynamic shared memory: trsvl_smem_bytes<T, NB, RC, NS>().
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
 __host__ __device__ constexpr int trsvl_stride() { return NB + 16 / (int)sizeof(T); }  // 16-byte rows
 
-template <typename T, int NB, int RC>
+template <typename T, int NB, int RC, int NS>
 constexpr size_t trsvl_smem_bytes() {
-  return sizeof(T) * (2 * (size_t)NB * trsvl_stride<T, NB>() + 2 * (size_t)NB * (RC + 1));
+  return sizeof(T) * ((size_t)NS * NB * NB + (size_t)NB * trsvl_stride<T, NB>() + 3 * (size_t)NB * (RC + 1));
 }
 
-template <typename T, int NB, int RC, bool UPPER>
-__global__ void __launch_bounds__(256)
-    k_trsv_left(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv, int *flags, DevStatus *st) {
-  constexpr int NT = 256, FS = trsvl_stride<T, NB>();
-  constexpr int PASS = NT / RC, OPT = NB / PASS, LPT = NB * NB / NT;
-  static_assert(NT % RC == 0 && NB % PASS == 0 && (NB * NB) % NT == 0, "shape");
+// Element (r, k) of a swizzled NB x NB ring tile.
+template <typename T, int NB>
+__device__ __forceinline__ int ring_idx(int r, int k) {
+  constexpr int E = 16 / (int)sizeof(T), CPR = NB / E;  // elements per chunk, chunks per row
+  return r * NB + (((k / E) ^ (r % CPR)) * E) + (k % E);
+}
+
+// Elements k .. k+3 (k a multiple of 4) of row r of a ring tile, as 16-byte loads.
+template <int NB>
+__device__ __forceinline__ void ring_ld4(const float *tile, int r, int k, float (&f)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(tile + ring_idx<float, NB>(r, k));
+  f[0] = v.x, f[1] = v.y, f[2] = v.z, f[3] = v.w;
+}
+template <int NB>
+__device__ __forceinline__ void ring_ld4(const double *tile, int r, int k, double (&f)[4]) {
+  const double2 v0 = *reinterpret_cast<const double2 *>(tile + ring_idx<double, NB>(r, k));
+  const double2 v1 = *reinterpret_cast<const double2 *>(tile + ring_idx<double, NB>(r, k + 2));
+  f[0] = v0.x, f[1] = v0.y, f[2] = v1.x, f[3] = v1.y;
+}
+// acc[q] -= sum_k P(r_q, k) xs[k][tc] over a ring tile P, r_q = tr + PASS q.
+template <typename T, int NB, int RC, int PASS, int OPT>
+__device__ __forceinline__ void ring_fold(const T *P, const T (*xs)[RC + 1], int tr, int tc, T (&acc)[OPT]) {
+#pragma unroll 4
+  for (int k = 0; k < NB; k += 4) {
+    T x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = xs[k + u][tc];
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      T f[4];
+      ring_ld4<NB>(P, tr + PASS * q, k, f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[q] -= f[u] * x[u];
+    }
+  }
+}
+
+template <typename T, int NB, int RC, bool UPPER, int NS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs,
+                                                         const T *dinv, unsigned long long *xw, DevStatus *st) {
+  constexpr int NT = 256, DS = trsvl_stride<T, NB>(), E = 16 / (int)sizeof(T), CPR = NB / E;
+  constexpr int PASS = NT / RC, OPT = NB / PASS;
+  static_assert(NT % RC == 0 && NB % PASS == 0 && NS >= 2, "shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*Fb)[FS] = reinterpret_cast<T(*)[FS]>(smem_raw);                               // F(t, s)
-  T(*Di)[FS] = reinterpret_cast<T(*)[FS]>(smem_raw + sizeof(T) * NB * FS);         // D_t^{-1}
-  T(*Xs)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + 2 * sizeof(T) * NB * FS);  // X_s
-  T(*Ac)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * (2 * NB * FS + NB * (RC + 1)));
-  __shared__ int s_ok;
+  T *Fr = reinterpret_cast<T *>(smem_raw);                                           // NS ring tiles
+  T(*Di)[DS] = reinterpret_cast<T(*)[DS]>(Fr + NS * NB * NB);                          // D_t^{-1}
+  T(*Xs)[NB][RC + 1] = reinterpret_cast<T(*)[NB][RC + 1]>(Fr + NS * NB * NB + NB * DS);  // 2 x X_s
+  T(*Ac)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(Fr + NS * NB * NB + NB * DS + 2 * NB * (RC + 1));
   if (st && st->done) return;  // refinement already converged
   const int nblk = ceil_div(n, NB);
   const int nchunk = ceil_div(nrhs, RC);
@@ -106,118 +217,166 @@ __global__ void __launch_bounds__(256)
   const int G = gridDim.x / nchunk;
   if (h >= G) return;
   const int c0 = chunk * RC, wc = min(RC, nrhs - c0);
-  int *fl = flags + (int64_t)chunk * nblk;
+  unsigned long long *xc = xw + (size_t)chunk * nblk * NB * RC * XWords<T>::W;
+  auto xent = [&](int s, int k, int c) { return xc + (((size_t)s * NB + k) * RC + c) * XWords<T>::W; };
   auto blk = [&](int s) { return UPPER ? nblk - 1 - s : s; };
+  auto rows_of = [&](int s) { return (int)min64(NB, n - (int64_t)blk(s) * NB); };
   // Blocks s >= t - reach couple into block t (a band limits reach).
   const int reach = (int)max64(1, min64((UPPER ? F.ku + NB - 1 : F.kl + NB - 1) / NB, (int64_t)nblk));
   const int tc = threadIdx.x % RC, tr = threadIdx.x / RC;
+  const bool direct = F.kl >= kDenseBand && F.ku >= kDenseBand && F.ld % E == 0 &&
+                      ((uintptr_t)F.base % 16) == 0;
 
-  T fr[LPT];  // factor tile in flight
-  auto fetch_f = [&](int t, int s) {
-    const int64_t i0 = (int64_t)blk(t) * NB, j0 = (int64_t)blk(s) * NB;
-    const int hi = (int)min64(NB, n - i0), hj = (int)min64(NB, n - j0);
-#pragma unroll
-    for (int q = 0; q < LPT; ++q) {
-      const int e = threadIdx.x + NT * q, r = e / NB, k = e % NB;
-      fr[q] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
+  // Ring tile j of block t: F(t, sb + j) for j < m, then the coupling tile.
+  auto load_tile = [&](T *dst, int t, int s, const T *g) {
+    if (g) {
+      for (int e = threadIdx.x; e < NB * CPR; e += NT) {
+        const int r = e / CPR, c = e % CPR;
+        cp_async16(dst + ring_idx<T, NB>(r, c * E), g + r * NB + c * E, 16);
+      }
+      return;
     }
+    const int64_t i0 = (int64_t)blk(t) * NB, j0 = (int64_t)blk(s) * NB;
+    const int hi = rows_of(t), hj = rows_of(s);
+    if (direct) {
+      for (int e = threadIdx.x; e < NB * CPR; e += NT) {
+        const int r = e / CPR, c = e % CPR;
+        const int valid = r < hi ? max(0, min(E, hj - c * E)) : 0;
+        cp_async16(dst + ring_idx<T, NB>(r, c * E), valid ? F.base + (i0 + r) * F.ld + j0 + c * E : F.base,
+                   valid * (int)sizeof(T));
+      }
+    } else {
+      for (int e = threadIdx.x; e < NB * NB; e += NT) {
+        const int r = e / NB, k = e % NB;
+        dst[ring_idx<T, NB>(r, k)] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
+      }
+    }
+  };
+  auto commit = [] { asm volatile("cp.async.commit_group;" ::: "memory"); };
+  // every copy of this thread landed (also before giving up: none stays in flight)
+  auto drain = [] { asm volatile("cp.async.wait_group 0;" ::: "memory"); };
+  // X_s into xs: one attempt at every entry of this thread (zero outside the
+  // block / chunk).  All loads are issued before any tag is checked, so an
+  // attempt costs one memory round trip however many entries a thread has.
+  auto try_x = [&](int s, T (*xs)[RC + 1]) -> bool {
+    const uint32_t tag = (uint32_t)s + 1;
+    const int hj = rows_of(s);
+    unsigned long long wv[OPT][XWords<T>::W];
+#pragma unroll
+    for (int j = 0; j < OPT; ++j) {
+      const int k = tr + PASS * j;
+#pragma unroll
+      for (int u = 0; u < XWords<T>::W; ++u)
+        wv[j][u] = (k < hj && tc < wc) ? xw_load(xent(s, k, tc) + u) : ((unsigned long long)tag << 32);
+    }
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < OPT; ++j) {
+      const int k = tr + PASS * j;
+      T v;
+      if (!xw_decode(wv[j], tag, v)) ok = false;
+      xs[k][tc] = (k < hj && tc < wc) ? v : T(0);
+    }
+    return ok;
+  };
+  // Bounded wait for all of this thread's entries of X_s (limits and early
+  // exit as bounded_wait_geq; on expiry records EBV_ERR_TIMEOUT with s).
+  auto wait_x = [&](int s, T (*xs)[RC + 1]) -> bool {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+      if (try_x(s, xs)) return true;
+      if ((it & 255) == 255 && st && ld_acquire(&st->code) != 0) return false;
+      if (it >= 32) __nanosleep(64);
+    }
+    set_status(st, EBV_ERR_TIMEOUT, s);
+    return false;
   };
 
   for (int t = h; t < nblk; t += G) {
     const int64_t i0 = (int64_t)blk(t) * NB;
-    const int hi = (int)min64(NB, n - i0);
+    const int hi = rows_of(t);
     const int sb = max(0, t - reach);
+    const int m = max(0, t - 1 - sb);           // folded blocks s = sb .. t-2
+    const int ntiles = m + (t >= 1 ? 1 : 0);    // + the coupling tile
+    const T *slot = dinv + (int64_t)blk(t) * 4 * NB * NB;
+    const T *gmat = slot + (UPPER ? 3 : 2) * NB * NB;  // D_t^{-1} F(t, t-1)
+    auto tile = [&](int j) {
+      if (j < ntiles) load_tile(Fr + (j % NS) * NB * NB, t, sb + j, j < m ? nullptr : gmat);
+      commit();
+    };
+    // (the ring, Di, Xs and Ac are free: the previous block ended with a
+    // barrier after its last use of them)
+    for (int j = 0; j < NS - 1; ++j) tile(j);
+    stage_tile<NB, NT, DS>(&Di[0][0], [&](int r, int k) { return slot[(UPPER ? NB * NB : 0) + r * NB + k]; });
     T acc[OPT];
 #pragma unroll
     for (int q = 0; q < OPT; ++q) {
       const int r = tr + PASS * q;
       acc[q] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
     }
-    const T *slot = dinv + (int64_t)blk(t) * 4 * NB * NB;
-    const T *gmat = slot + (UPPER ? 3 : 2) * NB * NB;  // D_t^{-1} F(t, t-1)
-    auto fetch_g = [&]() {
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) fr[q] = gmat[threadIdx.x + NT * q];
-    };
-    stage_tile<NB, NT, FS>(&Di[0][0], [&](int r, int k) { return slot[(UPPER ? NB * NB : 0) + r * NB + k]; });
-    // Blocks s < t-1 are folded here; block t-1 goes through D_t^{-1} F(t, t-1).
-    if (sb < t - 1) fetch_f(t, sb);
-    else if (t >= 1) fetch_g();
-    for (int s = sb; s < t - 1; ++s) {
-      if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[s], 1, st, kSpinLimit, s);
-      __syncthreads();  // flag seen; the previous fold is done with Fb and Xs
-      if (!s_ok) return;
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        const int e = threadIdx.x + NT * q;
-        Fb[e / NB][e % NB] = fr[q];
+    for (int j = 0; j < m; ++j) {
+      const int s = sb + j;
+      T(*xs)[RC + 1] = Xs[j & 1];
+      const bool got = try_x(s, xs);
+      asm volatile("cp.async.wait_group %0;" ::"n"(NS - 2) : "memory");
+      if (__syncthreads_or(!got)) {  // X_s not (fully) there yet
+        bool ok = true;
+        if (threadIdx.x == 0) {
+          T v;
+          ok = xw_wait(xent(s, 0, 0), (uint32_t)s + 1, v, st, s);
+        }
+        if (__syncthreads_or(!ok)) return drain();
+        ok = wait_x(s, xs);
+        if (__syncthreads_or(!ok)) return drain();
       }
-      {
-        const int64_t j0 = (int64_t)blk(s) * NB;
-        const int hj = (int)min64(NB, n - j0);
-        for (int k = tr; k < NB; k += PASS)
-          Xs[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
-      }
-      if (s + 1 < t - 1) fetch_f(t, s + 1);
-      else fetch_g();
-      __syncthreads();
-#pragma unroll 16
-      for (int k = 0; k < NB; ++k) {
-        const T xk = Xs[k][tc];
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) acc[q] -= Fb[tr + PASS * q][k] * xk;
-      }
+      tile(j + NS - 1);  // into the stage every thread finished with before the barrier
+      ring_fold<T, NB, RC, PASS, OPT>(Fr + (j % NS) * NB * NB, xs, tr, tc, acc);
     }
-    // y = D_t^{-1} acc, before block t-1 is needed.  (Di and Ac are free: the
-    // previous block ended with a barrier after its last use of them.)
+    // y = D_t^{-1} acc, before block t-1 is needed.
 #pragma unroll
     for (int q = 0; q < OPT; ++q) Ac[tr + PASS * q][tc] = acc[q];
     __syncthreads();
     T y[OPT];
 #pragma unroll
-    for (int q = 0; q < OPT; ++q) {
-      const int r = tr + PASS * q;
-      T x = T(0);
-#pragma unroll 16
-      for (int k = 0; k < NB; ++k) x += Di[r][k] * Ac[k][tc];
-      y[q] = x;
+    for (int q = 0; q < OPT; ++q) y[q] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < NB; k += 4) {
+      T x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = Ac[k + u][tc];
+#pragma unroll
+      for (int q = 0; q < OPT; ++q) {
+        const T *d = &Di[tr + PASS * q][k];
+        T f[4];
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(d);
+          f[0] = v.x, f[1] = v.y, f[2] = v.z, f[3] = v.w;
+        } else {
+          const double2 v0 = *reinterpret_cast<const double2 *>(d), v1 = *reinterpret_cast<const double2 *>(d + 2);
+          f[0] = v0.x, f[1] = v0.y, f[2] = v1.x, f[3] = v1.y;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[q] += f[u] * x[u];
+      }
     }
     if (t >= 1) {  // x_t = y - (D_t^{-1} F(t, t-1)) x_{t-1}
-      if (threadIdx.x == 0) s_ok = bounded_wait_geq(&fl[t - 1], 1, st, kSpinLimit, t - 1);
-      __syncthreads();
-      if (!s_ok) return;
-#pragma unroll
-      for (int q = 0; q < LPT; ++q) {
-        const int e = threadIdx.x + NT * q;
-        Fb[e / NB][e % NB] = fr[q];
-      }
-      {
-        const int64_t j0 = (int64_t)blk(t - 1) * NB;
-        const int hj = (int)min64(NB, n - j0);
-        for (int k = tr; k < NB; k += PASS)
-          Xs[k][tc] = (k < hj && tc < wc) ? __ldcg(&B[(j0 + k) * ldb + c0 + tc]) : T(0);
-      }
-      __syncthreads();
-#pragma unroll 16
-      for (int k = 0; k < NB; ++k) {
-        const T xk = Xs[k][tc];
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) y[q] -= Fb[tr + PASS * q][k] * xk;
-      }
+      T(*xs)[RC + 1] = Xs[m & 1];
+      const bool ok = wait_x(t - 1, xs);
+      drain();
+      if (__syncthreads_or(!ok)) return;
+      ring_fold<T, NB, RC, PASS, OPT>(Fr + (m % NS) * NB * NB, xs, tr, tc, y);
     }
+    const uint32_t tag = (uint32_t)t + 1;
 #pragma unroll
     for (int q = 0; q < OPT; ++q) {
       const int r = tr + PASS * q;
-      if (r < hi && tc < wc) B[(i0 + r) * ldb + c0 + tc] = y[q];
+      if (r < hi && tc < wc) {
+        xw_put(xent(t, r, tc), y[q], tag);
+        B[(i0 + r) * ldb + c0 + tc] = y[q];
+      }
     }
-    // The barrier orders every thread's stores of x_t before thread 0's
-    // gpu-scope fence, which makes them visible before the flag (cumulativity).
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release(&fl[t], 1);
-    }
+    __syncthreads();  // the ring, Di, Xs and Ac are free for the next block
   }
+  drain();
 }
 
 // ---------------------------------------------------------------------------

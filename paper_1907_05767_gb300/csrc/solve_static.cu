@@ -24,7 +24,7 @@ namespace {
 
 // Bytes of the static workspace; with n <= EBV_STATIC_MAX_N and
 // nrhs <= EBV_STATIC_MAX_NRHS every precision and storage fits (FP64 with
-// refinement at the limits needs about 14.6 MiB).
+// refinement at the limits needs about 16.5 MiB).
 constexpr size_t kStaticBytes = EBV_STATIC_SCRATCH_BYTES;
 
 // Device-side workspace.  In host code this name is only a stand-in for the
