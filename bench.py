@@ -621,9 +621,14 @@ def run_configs(args):
         gbo, gao = oracle.adjoint(luo, xo, data[i][3])
         err = max(err, float(np.abs(g_b[i].cpu().numpy() - gbo).max() / np.abs(gbo).max()),
                   float(np.abs(g_a[i].cpu().numpy() - gao).max() / np.abs(gao).max()))
-    bwd_bytes = nb * (8.0 * n * n * 2)  # read the factors, write grad_A
+    # backward: two transposed substitutions (n^2 nrhs / 2 multiply-adds each)
+    # and grad_A = -grad_B X^T (n^2 nrhs) -- FP64-pipe bound on this GPU;
+    # bytes: each triangle of the factors read once, grad_A written
+    bwd_flops = nb * 4.0 * n * n * nrhs
+    bwd_bytes = nb * 8.0 * n * n * 2
     out.append({"config": "adjoint batch 256 x FP64 n=1024, 4 RHS", "ms_forward": ms_f - ms_copy,
                 "ms_backward": ms_b, "forward_gflops": nb * nominal_flops(n, nrhs) / ((ms_f - ms_copy) / 1e3) / 1e9,
+                "backward_gflops_fp64": bwd_flops / (ms_b / 1e3) / 1e9,
                 "backward_gbs": bwd_bytes / (ms_b / 1e3) / 1e9, "backward_hbm_frac": bwd_bytes / (ms_b / 1e3) / 1e9 / hbm,
                 "grad_relerr_vs_oracle_sampled": err, "info_max": int(bt.info.abs().max())})
     print(json.dumps(out[-1]), flush=True)

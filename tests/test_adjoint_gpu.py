@@ -39,6 +39,26 @@ def test_adjoint_matches_oracle(batch, n, nrhs):
         assert np.abs(ga[s] - ga_ref).max() <= 1e-10 * np.abs(ga_ref).max()
 
 
+@pytest.mark.parametrize("batch,n,nrhs", [(2, 300, 6), (2, 200, 12), (1, 1700, 9), (1, 97, 16)])
+def test_adjoint_kernel_variants(batch, n, nrhs):
+    # ebv_solve_adjoint from the oracle's factors: right-hand sides in shared
+    # memory with 8 and 16 columns, and (n * 16 doubles above the on-chip
+    # budget) the global-memory kernel.
+    a, b, w = make(batch, n, nrhs, 42_000 + n)
+    lus, xs = [], []
+    for s in range(batch):
+        lu, _ = oracle.lu(a[s])
+        lus.append(lu)
+        xs.append(oracle.solve(lu, b[s]))
+    gb, ga = ebv.ebv_solve_adjoint(torch.from_numpy(np.stack(lus)).cuda(), torch.from_numpy(np.stack(xs)).cuda(),
+                                   torch.from_numpy(w).cuda())
+    gb, ga = gb.cpu().numpy(), ga.cpu().numpy()
+    for s in range(batch):
+        gb_ref, ga_ref = oracle.adjoint(lus[s], xs[s], w[s])
+        assert np.abs(gb[s] - gb_ref).max() <= 1e-10 * np.abs(gb_ref).max()
+        assert np.abs(ga[s] - ga_ref).max() <= 1e-10 * np.abs(ga_ref).max()
+
+
 def test_adjoint_finite_differences():
     batch, n, nrhs = 2, 64, 4
     a, b, w = make(batch, n, nrhs, 41_000)
