@@ -336,11 +336,12 @@ EBV_API ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda,
  * ebv_debug_profile(1) brackets every later launch with CUDA events on its
  * stream, per kernel class: 0 mixed-precision trailing update, 1 working-
  * precision trailing update, 2 diagonal blocks, 3 block substitutions,
- * 4 refinement residual, 5 batched kernel, 6 adjoint, 7 other, 8 L21 / U12
- * tile products and blocked TRSMs.
- * ebv_debug_profile_read fills, for the 9 classes, the summed device time in
+ * 4 refinement residual, 5 batched kernel, 6 adjoint, 7 other, 8 U12
+ * tile products and blocked TRSMs, 9 L21 tile products, 10 two-leaf middle
+ * step (U12 and the trailing update of a 128-column node in one launch).
+ * ebv_debug_profile_read fills, for the 11 classes, the summed device time in
  * ms, the summed algorithmic work (flops) and the launch count of the launches
- * recorded since the previous read (host arrays of 9; synchronises on the
+ * recorded since the previous read (host arrays of 11; synchronises on the
  * recorded events).  Profiling adds an event pair per launch; switch it off
  * for timed runs.
  */

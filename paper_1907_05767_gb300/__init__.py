@@ -92,7 +92,8 @@ _SIGNATURES = [
     ("ebv_debug_profile", None, [_I32]),
     ("ebv_debug_profile_read", _I32, [_VP, _VP, _VP]),
 ]
-PROFILE_CLASSES = ["lowp_gemm", "simt_gemm", "panel", "trsv", "residual", "batched", "adjoint", "other", "trsm"]
+PROFILE_CLASSES = ["lowp_gemm", "simt_gemm", "panel", "trsv", "residual", "batched", "adjoint", "other", "trsm",
+                   "l21", "leaf_update"]
 
 
 def launch_count() -> int:

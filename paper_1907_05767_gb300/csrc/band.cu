@@ -46,7 +46,7 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
     // FP64: 16-row / 16-column strips, four times the CTAs of one 64 x 64
     // tile each (a band has only kl rows / ku columns per step).
     if (re > rb) {
-      prof::Scope ps(s, prof::kTrsm, 2.0 * (re - rb) * w * w);
+      prof::Scope ps(s, prof::kL21, 2.0 * (re - rb) * w * w);
       if constexpr (sizeof(T) == 8)
         k_trsm_ru_strip<T, float, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
       else

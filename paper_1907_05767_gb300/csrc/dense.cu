@@ -189,7 +189,7 @@ struct Factorizer {
     }
     const int64_t rb = c0 + w, re = n;
     if (re > rb) {
-      prof::Scope ps(s, prof::kTrsm, 2.0 * (re - rb) * w * w);
+      prof::Scope ps(s, prof::kL21, 2.0 * (re - rb) * w * w);
       if (sizeof(T) == 8 && ceil_div(re - rb, kNB) < 152)  // FP64, fewer 64-row tiles than SMs: 16-row strips
         k_trsm_ru_strip<T, SH, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
       else
@@ -258,7 +258,7 @@ struct Factorizer {
       EBV_TRY(need(c0 + w));
       {
         const int64_t rows = n - c0 - w1;
-        prof::Scope ps(s, prof::kTrsm, 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
+        prof::Scope ps(s, prof::kLeafUpdate, 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
         k_leaf_update<T, SH, kNB><<<ceil_div(rows, kNB), 256, leaf_update_smem_bytes<T, kNB>(), s>>>(
             A, c0, (int)w1, (int)(w - w1), n, leaf_inv(c0), sh, st);
         EBV_TRY(launch_ok());

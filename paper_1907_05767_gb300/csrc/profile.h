@@ -24,8 +24,10 @@ enum Class : int {
   kBatched = 5,    // batched persistent kernel
   kAdjoint = 6,    // adjoint kernels
   kOther = 7,
-  kTrsm = 8,       // L21 / U12 tile products and blocked TRSMs (kPanel: the diagonal blocks)
-  kNumClasses = 9
+  kTrsm = 8,       // U12 = L11^{-1} A12: tile products and blocked TRSMs
+  kL21 = 9,        // L21 = A21 U11^{-1} tile products
+  kLeafUpdate = 10,  // two-leaf middle step (U12 and the A22 update in one launch)
+  kNumClasses = 11
 };
 
 bool enabled();
