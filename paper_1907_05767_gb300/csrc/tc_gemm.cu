@@ -13,7 +13,8 @@
 //               (M=128, N=BN, K=16) into the TMEM accumulator and commits
 //               each slab back to its empty barrier;
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//               lanes 32*(w%4)...), C -= scale * D in FP32.
+//               lanes 32*(w%4)...), C -= scale * D in FP32, with the loads of
+//               C issued ahead (the first ones while the MMAs still run).
 // Every mbarrier wait is bounded; on expiry the CTA records EBV_ERR_TIMEOUT,
 // drains its own TMA copies and MMAs (bounded), frees TMEM and returns.
 #include <cuda.h>
@@ -133,37 +134,57 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (!mbar_wait(tfull, 0, nullptr)) set_status(st, EBV_ERR_TIMEOUT, 4);  // MMAs retired before TMEM is freed
   } else if (warp >= 2) {
     // ---- epilogue ----
+    // C does not depend on the accumulator: the first PF 16-column chunks of
+    // this thread's row of C are loaded before the MMAs finish, and every
+    // chunk's store is followed by the load of the chunk PF ahead, so PF
+    // loads are always in flight instead of one round trip per chunk.
+    constexpr int NCH = BN / 16, PF = NCH < 4 ? NCH : 4;
     const int q = warp & 3;
     const int row = q * 32 + lane;
     const int64_t gi = m0 + (int64_t)tile_m * BM + row;
     const bool row_ok = gi < m0 + M;
+    float *crow = C + gi * ldc;
+    const int64_t jbase = n0 + (int64_t)tile_n * BN;
+    auto fast = [&](int ci) { return row_ok && vec_ok && jbase + ci * 16 + 16 <= n0 + N; };
+    float4 cb[PF][4];
+    auto fetch = [&](int ci, float4 (&d)[4]) {
+      if (fast(ci)) {
+        const float4 *p = reinterpret_cast<const float4 *>(crow + jbase + ci * 16);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) d[v] = p[v];
+      }
+    };
+#pragma unroll
+    for (int p = 0; p < PF; ++p) fetch(p, cb[p]);
     if (mbar_wait(tfull, 0, abort_flag)) {
       tc_fence_after();
       const float inv = scale[2];
-      float *crow = C + gi * ldc;
-      const int64_t jbase = n0 + (int64_t)tile_n * BN;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t r[16];
-        __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the divergent stores
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-        const int64_t gj0 = jbase + c0;
-        if (!row_ok || gj0 >= n0 + N) continue;
-        if (vec_ok && gj0 + 16 <= n0 + N) {
-          float4 *p = reinterpret_cast<float4 *>(crow + gj0);
+      for (int c = 0; c < NCH; c += PF) {
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            float4 c = p[v];
-            c.x -= __uint_as_float(r[4 * v + 0]) * inv;
-            c.y -= __uint_as_float(r[4 * v + 1]) * inv;
-            c.z -= __uint_as_float(r[4 * v + 2]) * inv;
-            c.w -= __uint_as_float(r[4 * v + 3]) * inv;
-            p[v] = c;
+        for (int p = 0; p < PF; ++p) {
+          const int ci = c + p;
+          uint32_t r[16];
+          __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the divergent stores
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ci * 16), r);
+          const int64_t gj0 = jbase + ci * 16;
+          if (fast(ci)) {
+            float4 *dst = reinterpret_cast<float4 *>(crow + gj0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              float4 x = cb[p][v];
+              x.x -= __uint_as_float(r[4 * v + 0]) * inv;
+              x.y -= __uint_as_float(r[4 * v + 1]) * inv;
+              x.z -= __uint_as_float(r[4 * v + 2]) * inv;
+              x.w -= __uint_as_float(r[4 * v + 3]) * inv;
+              dst[v] = x;
+            }
+          } else if (row_ok && gj0 < n0 + N) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (gj0 + j < n0 + N) crow[gj0 + j] -= __uint_as_float(r[j]) * inv;
           }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (gj0 + j < n0 + N) crow[gj0 + j] -= __uint_as_float(r[j]) * inv;
+          if (ci + PF < NCH) fetch(ci + PF, cb[p]);
         }
       }
     } else {
