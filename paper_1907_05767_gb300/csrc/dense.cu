@@ -179,7 +179,8 @@ struct Factorizer {
   }
   T *leaf_inv(int64_t c0) const { return inv + (c0 / kNB) * 2 * kNB * kNB; }
 
-  ebv_status_t leaf(int64_t c0, int w) {
+  // The diagonal block of the leaf at c0, then (with_l21) its L21 for every row below.
+  ebv_status_t leaf(int64_t c0, int w, bool with_l21 = true) {
     constexpr size_t smem = pair_smem_bytes<T, kNB>();
     EBV_TRY(need(c0 + w));
     {
@@ -188,7 +189,7 @@ struct Factorizer {
       EBV_TRY(launch_ok());
     }
     const int64_t rb = c0 + w, re = n;
-    if (re > rb) {
+    if (with_l21 && re > rb) {
       prof::Scope ps(s, prof::kL21, 2.0 * (re - rb) * w * w);
       if (sizeof(T) == 8 && ceil_div(re - rb, kNB) < 152)  // FP64, fewer 64-row tiles than SMs: 16-row strips
         k_trsm_ru_strip<T, SH, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, leaf_inv(c0), sh);
@@ -254,10 +255,18 @@ struct Factorizer {
     if (w <= kNB) return leaf(c0, (int)w);
     const int64_t w1 = split(w);
     if (w <= 2 * kNB) {  // two leaves: U12 and the trailing update in one launch
-      EBV_TRY(leaf(c0, (int)w1));
+      // binary32: the left leaf's L21 joins that launch as well
+      constexpr bool fuse_l21 = sizeof(T) == 4;
+      EBV_TRY(leaf(c0, (int)w1, !fuse_l21));
       EBV_TRY(need(c0 + w));
-      {
-        const int64_t rows = n - c0 - w1;
+      const int64_t rows = n - c0 - w1;
+      if (fuse_l21) {
+        prof::Scope ps(s, prof::kLeafUpdate,
+                       2.0 * rows * w1 * w1 + 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
+        k_leaf_ru_update<T, SH, kNB><<<ceil_div(rows, kNB), 256, leaf_ru_update_smem_bytes<T, kNB>(), s>>>(
+            A, c0, (int)w1, (int)(w - w1), n, leaf_inv(c0), sh, st);
+        EBV_TRY(launch_ok());
+      } else {
         prof::Scope ps(s, prof::kLeafUpdate, 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
         k_leaf_update<T, SH, kNB><<<ceil_div(rows, kNB), 256, leaf_update_smem_bytes<T, kNB>(), s>>>(
             A, c0, (int)w1, (int)(w - w1), n, leaf_inv(c0), sh, st);

@@ -660,6 +660,93 @@ __global__ void __launch_bounds__(256) k_leaf_update(MatView<T> A, int64_t c0, i
 }
 
 // ---------------------------------------------------------------------------
+// The left leaf's L21 and the two-leaf middle step in one launch (binary32
+// recursion nodes of width <= 128): CTA b owns the 64-row block b below the
+// left leaf and forms its L21 block = A21 U11^{-1} (Eq. 6a), writes it (and
+// its low-precision shadow), forms U12 = L11^{-1} A12 (Eq. 6b; stored by the
+// last CTA to arrive, as in k_leaf_update) and applies A22 -= L21 U12
+// (Eq. 6c) from shared memory.  Replaces k_trsm_ru + k_leaf_update: one
+// launch and no round trip of L21 through memory on the recursion's
+// critical path.  All five input tiles are fetched before any is stored.
+// Dynamic shared memory: leaf_ru_update_smem_bytes<T, NB>().
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+constexpr size_t leaf_ru_update_smem_bytes() { return 5 * sizeof(T) * (size_t)NB * diag_tstride<T, NB>(); }
+
+template <typename T, typename SH, int NB>
+__global__ void __launch_bounds__(256) k_leaf_ru_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
+                                                        const T *inv, Shadow<SH> sh, DevStatus *st) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>(), Q = NB * NB / 256;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int last;
+  T *Li = reinterpret_cast<T *>(dsm);
+  T *U12 = Li + NB * TS;   // A12, then U12
+  T *L21 = U12 + NB * TS;  // U11^{-1}, then L21
+  T *At = L21 + NB * TS;   // A21
+  T *C = At + NB * TS;
+  const int64_t cb = c0 + w1;                        // first column (and row) of the right half
+  const int64_t r0 = cb + (int64_t)blockIdx.x * NB;  // this CTA's rows
+  const int h = (int)min64(NB, n - r0);
+  const T *linv = inv, *uinv = inv + NB * NB;
+  {
+    T f0[Q], f1[Q], f2[Q], f3[Q], f4[Q];
+    fetch_tile<NB, 256>(f0, [&](int i, int k) { return linv[i * NB + k]; });
+    fetch_tile<NB, 256>(f1, [&](int k, int j) { return (k < w1 && j < w2) ? A.get(c0 + k, cb + j) : T(0); });
+    fetch_tile<NB, 256>(f2, [&](int i, int k) { return uinv[i * NB + k]; });
+    fetch_tile<NB, 256>(f3, [&](int i, int k) { return (i < h && k < w1) ? A.get(r0 + i, c0 + k) : T(0); });
+    fetch_tile<NB, 256>(f4, [&](int i, int j) { return (i < h && j < w2) ? A.get(r0 + i, cb + j) : T(0); });
+    put_tile<NB, 256, TS>(Li, f0);
+    put_tile<NB, 256, TS>(U12, f1);
+    put_tile<NB, 256, TS>(L21, f2);
+    put_tile<NB, 256, TS>(At, f3);
+    put_tile<NB, 256, TS>(C, f4);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // A12 is in shared memory: count this CTA as done reading it
+    __threadfence();
+    last = atomicAdd(&st->arrive, 1) == (int)gridDim.x - 1;
+    if (last) st->arrive = 0;  // every CTA has arrived: ready for the next launch
+  }
+  tile_product<T, NB, TS>(At, L21);  // L21 <- A21 U11^{-1}; ends with a barrier
+  tile_product<T, NB, TS>(Li, U12);  // U12 = L11^{-1} A12
+  {
+    const float s = sh.lb ? sh.scale[0] : 1.f;
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int i = e / NB, k = e % NB;
+      if (i < h && k < w1) {
+        const T v = L21[i * TS + k];
+        A.put(r0 + i, c0 + k, v);
+        if (sh.lb) sh.lb[(r0 + i) * sh.ld + c0 + k] = from_float<SH>((float)v * s);
+      }
+    }
+  }
+  if (last) {
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int k = e / NB, j = e % NB;
+      if (k < w1 && j < w2) A.put(c0 + k, cb + j, U12[k * TS + j]);
+    }
+    if (sh.ut) {
+      const float s = sh.scale[1];
+      for (int e = threadIdx.x; e < NB * NB; e += 256) {
+        const int j = e / NB, k = e % NB;
+        if (k < w1 && j < w2) sh.ut[(cb + j) * sh.ld + c0 + k] = from_float<SH>((float)U12[k * TS + j] * s);
+      }
+    }
+  }
+  T acc[4][4];
+  tile_regs<T, TS>(C, acc);
+  tile_fma<T, NB, TS, true>(L21, U12, acc);  // A22 -= L21 U12 (Eq. 6c, 64 steps aggregated)
+  __syncthreads();
+  tile_put<T, TS>(C, acc);
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int i = e / NB, j = e % NB;
+    if (i < h && j < w2) A.put(r0 + i, cb + j, C[i * TS + j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // U12 = L11^{-1} A12 for h <= MAXB * NB rows in one launch (Eq. 6b for the
 // U vectors of several leaf blocks at once): a left-looking blocked forward
 // substitution over the 64-row blocks of L11, one 64-column strip per CTA.
@@ -910,6 +997,8 @@ ebv_status_t prepare_leaf_kernels() {
       e = set_smem(k_trsm_ru_strip<T, SH, kNB, 16>, bytes);
     if (e == cudaSuccess)
       e = set_smem(k_leaf_update<T, SH, kNB>, (int)leaf_update_smem_bytes<T, kNB>());
+    if (e == cudaSuccess)
+      e = set_smem(k_leaf_ru_update<T, SH, kNB>, (int)leaf_ru_update_smem_bytes<T, kNB>());
     const int tb = (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
     if (e == cudaSuccess)
       e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64>, tb);
