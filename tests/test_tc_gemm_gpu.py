@@ -12,12 +12,12 @@ import paper_1907_05767_gb300 as ebv
 pytestmark = pytest.mark.gpu
 
 
-def run_case(m0, n0, k0, M, N, K, ld, dtype, engine, seed=0, scale=(1.0, 1.0)):
+def run_case(m0, n0, k0, M, N, K, ld, dtype, engine, seed=0, scale=(1.0, 1.0), cpad=5):
     g = torch.Generator().manual_seed(seed)
     rows = max(m0 + M, n0 + N) + 3
     lb = (torch.rand((rows, ld), generator=g, dtype=torch.float64) - 0.5).to(dtype)
     ut = (torch.rand((rows, ld), generator=g, dtype=torch.float64) - 0.5).to(dtype)
-    c0 = torch.rand((rows, n0 + N + 5), generator=g, dtype=torch.float32)
+    c0 = torch.rand((rows, n0 + N + cpad), generator=g, dtype=torch.float32)
     s = torch.tensor([scale[0], scale[1], 1.0 / (scale[0] * scale[1]), 0.0], dtype=torch.float32)
     c = c0.clone().cuda()
     ebv.debug_lowp_update(c, lb.cuda(), ut.cuda(), s.cuda(), m0, n0, k0, M, N, K, engine)
@@ -50,6 +50,24 @@ def test_lowp_update_exact_reference(engine, dtype, shape):
     m0, n0, k0, M, N, K = shape
     ld = ((k0 + K + 63) // 64) * 64 + 64
     run_case(m0, n0, k0, M, N, K, ld, dtype, engine)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("shape", [
+    (0, 0, 0, 256, 256, 256),      # whole tiles, four slabs (one ring)
+    (64, 128, 64, 300, 200, 448),  # ragged M and N, seven slabs (ring reuse)
+    (5, 64, 128, 129, 100, 192),   # ragged, three slabs (fewer than the ring)
+    (128, 64, 0, 77, 72, 128),     # one partial tile
+    (0, 0, 0, 640, 384, 512),      # the largest K of the small-K kernel
+])
+def test_tc_small_k_c_in_shared_memory(dtype, shape):
+    # 16-byte rows of C (width a multiple of 4): K <= 512 and N > 64 take the
+    # kernel that stages C in shared memory and stores it back by TMA; the
+    # block edges must clip (nothing outside the block changes).
+    m0, n0, k0, M, N, K = shape
+    ld = ((k0 + K + 63) // 64) * 64 + 64
+    cpad = 4 + (-(n0 + N)) % 4
+    run_case(m0, n0, k0, M, N, K, ld, dtype, "tc", cpad=cpad)
 
 
 def test_tc_scaled_half():
