@@ -332,6 +332,9 @@ def run_gpu(args, rank, world, dist):
                        "err_vs_x_true": err_true, "info": info_v},
         "fp64_plain": fp64,
         "roofline": roofline,
+        "rooflines_by_class": {k: roofline_for(k, v[0], v[1], v[2], peaks, args,
+                                               active=int(rep_np["iters"]) + 1 if k == "residual" else None)
+                               for k, v in prof.items() if v[2] > 0},
         "kernel_classes_ms": {k: round(v[0], 4) for k, v in prof.items() if v[2] > 0},
         "kernel_classes_launches": {k: v[2] for k, v in prof.items() if v[2] > 0},
         "cpu_baseline": cpu,
