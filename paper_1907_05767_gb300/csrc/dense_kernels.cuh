@@ -439,27 +439,38 @@ struct StripMap {
   static constexpr int RPT = CW / 16, RS = 1024 / CW, CG = CW / 4;
   static_assert(CW == 64 || CW == 32 || CW == 16, "strip width");
 };
+// Four consecutive elements (16-byte aligned) of a shared-memory row.
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+  } else {
+    const double2 x0 = *reinterpret_cast<const double2 *>(p);
+    const double2 x1 = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = x0.x, v[1] = x0.y, v[2] = x1.x, v[3] = x1.y;
+  }
+}
+// (Four k at a time: the P row is read with one vector load per four
+// multiply-adds of each output; the order of the additions is k = 0, 1, ...)
 template <typename T, int NB, int TS, bool SUB, int CW = 64, int QS = TS>  // P rows: stride TS; Q rows: QS
 __device__ __forceinline__ void tile_fma(const T *P, const T *Q, T (&c)[StripMap<CW>::RPT][4]) {
   static_assert(NB == 64, "tile mapping assumes 64-row tiles and 256 threads");
   using M = StripMap<CW>;
   const int ti = threadIdx.x / M::CG, tj = threadIdx.x % M::CG;
-#pragma unroll 8
-  for (int k = 0; k < NB; ++k) {
-    T q[4];
-    if constexpr (sizeof(T) == 4) {
-      const float4 v = *reinterpret_cast<const float4 *>(Q + k * QS + 4 * tj);
-      q[0] = v.x, q[1] = v.y, q[2] = v.z, q[3] = v.w;
-    } else {
-      const double2 v0 = *reinterpret_cast<const double2 *>(Q + k * QS + 4 * tj);
-      const double2 v1 = *reinterpret_cast<const double2 *>(Q + k * QS + 4 * tj + 2);
-      q[0] = v0.x, q[1] = v0.y, q[2] = v1.x, q[3] = v1.y;
-    }
+#pragma unroll 2
+  for (int k0 = 0; k0 < NB; k0 += 4) {
+    T q[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ld4(Q + (k0 + u) * QS + 4 * tj, q[u]);
 #pragma unroll
     for (int a = 0; a < M::RPT; ++a) {
-      const T p = P[(ti + M::RS * a) * TS + k];
+      T p[4];
+      ld4(P + (ti + M::RS * a) * TS + k0, p);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) c[a][b] = SUB ? c[a][b] - p * q[b] : c[a][b] + p * q[b];
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) c[a][b] = SUB ? c[a][b] - p[u] * q[u][b] : c[a][b] + p[u] * q[u][b];
     }
   }
 }
@@ -917,15 +928,21 @@ __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int6
       const float *Q = Q_of(kk >> 6);
       const int k0 = kk & 63;
 #pragma unroll
-      for (int k = k0; k < k0 + 16; ++k) {
-        const float4 v = *reinterpret_cast<const float4 *>(Q + k * US + pc);
+      for (int k = k0; k < k0 + 16; k += 4) {  // four k per vector load of each P row
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4 *>(Q + (k + u) * US + pc);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const float p = P[(pr + 16 * a) * TS + k];
-          c[a][0] += p * v.x;
-          c[a][1] += p * v.y;
-          c[a][2] += p * v.z;
-          c[a][3] += p * v.w;
+          const float4 p4 = *reinterpret_cast<const float4 *>(P + (pr + 16 * a) * TS + k);
+          const float p[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            c[a][0] += p[u] * v[u].x;
+            c[a][1] += p[u] * v[u].y;
+            c[a][2] += p[u] * v[u].z;
+            c[a][3] += p[u] * v[u].w;
+          }
         }
       }
     }
