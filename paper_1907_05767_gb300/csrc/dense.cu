@@ -170,8 +170,49 @@ struct Factorizer {
   DevStatus *st = nullptr;
   T *inv = nullptr;  // per leaf: L11^{-1} then U11^{-1} (2 * 64 * 64 entries)
   ColumnStager *stg = nullptr;  // mixed precisions: makes columns available on first use
+  int *flags = nullptr;         // binary32: one zeroed flag per leaf for the fused diagonal-block launches
 
   ebv_status_t need(int64_t c_hi) { return stg ? stg->ensure(c_hi) : EBV_OK; }
+
+  // CTAs of a fused launch that can be co-resident (0 if unknown).
+  template <typename K>
+  static int coop_capacity(K kernel, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    return sms * per;
+  }
+  template <typename K, typename... Args>
+  ebv_status_t launch_coop(K kernel, int grid, size_t smem, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    EBV_CU(cudaLaunchKernelEx(&cfg, kernel, args...));
+    return launch_ok();
+  }
+  // Grid of a fused launch over `rows` rows below a leaf, if it fits co-resident (else 0).
+  int fused_grid(bool update, int64_t rows) const {
+    if constexpr (sizeof(T) != 4) {
+      return 0;
+    } else {
+      if (!flags || rows <= 0) return 0;
+      constexpr size_t smem = diag_fused_smem_bytes<T, kNB>();
+      static const int cap_l21 = coop_capacity(k_diag_l21<T, SH, kNB>, smem);
+      static const int cap_upd = coop_capacity(k_diag_l21_update<T, SH, kNB>, smem);
+      const int64_t grid = 1 + (rows + kNB - 1) / kNB;
+      return grid <= (update ? cap_upd : cap_l21) ? (int)grid : 0;
+    }
+  }
 
   static int64_t split(int64_t w) {  // leaf-aligned first half of a w-wide range
     const int64_t nb = (w + kNB - 1) / kNB;
@@ -183,6 +224,13 @@ struct Factorizer {
   ebv_status_t leaf(int64_t c0, int w, bool with_l21 = true) {
     constexpr size_t smem = pair_smem_bytes<T, kNB>();
     EBV_TRY(need(c0 + w));
+    if (with_l21) {
+      if (const int grid = fused_grid(false, n - c0 - w)) {  // one cooperative launch
+        prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0 + 2.0 * (n - c0 - w) * w * w);
+        return launch_coop(k_diag_l21<T, SH, kNB>, grid, diag_fused_smem_bytes<T, kNB>(), A, c0, w, n, info,
+                           leaf_inv(c0), sh, flags + c0 / kNB, st);
+      }
+    }
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
       k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, leaf_inv(c0));
@@ -257,9 +305,18 @@ struct Factorizer {
     if (w <= 2 * kNB) {  // two leaves: U12 and the trailing update in one launch
       // binary32: the left leaf's L21 joins that launch as well
       constexpr bool fuse_l21 = sizeof(T) == 4;
+      const int64_t rows = n - c0 - w1;
+      if (const int grid = fused_grid(true, rows)) {  // and the left leaf's diagonal block too
+        EBV_TRY(need(c0 + w));
+        prof::Scope ps(s, prof::kPanel,
+                       2.0 * w1 * w1 * w1 / 3.0 + 2.0 * rows * w1 * w1 + 2.0 * w1 * w1 * (w - w1) +
+                           2.0 * rows * w1 * (w - w1));
+        EBV_TRY(launch_coop(k_diag_l21_update<T, SH, kNB>, grid, diag_fused_smem_bytes<T, kNB>(), A, c0, (int)w1,
+                            (int)(w - w1), n, info, leaf_inv(c0), sh, flags + c0 / kNB, st));
+        return leaf(c0 + w1, (int)(w - w1));
+      }
       EBV_TRY(leaf(c0, (int)w1, !fuse_l21));
       EBV_TRY(need(c0 + w));
-      const int64_t rows = n - c0 - w1;
       if (fuse_l21) {
         prof::Scope ps(s, prof::kLeafUpdate,
                        2.0 * rows * w1 * w1 + 2.0 * w1 * w1 * (w - w1) + 2.0 * rows * w1 * (w - w1));
@@ -282,7 +339,7 @@ struct Factorizer {
 };
 
 struct DenseFactorLayout {
-  size_t inv, lb, ut, scale, scan, total;
+  size_t inv, flags, lb, ut, scale, scan, total;
   int64_t ldsh;  // shadow row stride: a multiple of 64 elements (128 B), as TMA wants 16-byte strides
 };
 
@@ -293,6 +350,8 @@ DenseFactorLayout factor_layout(int64_t n, ebv_prec_t prec) {
   const size_t leaves = (size_t)((n + kNB - 1) / kNB);
   L.inv = off;
   off = align256(off + leaves * 2 * kNB * kNB * (prec == EBV_FP64 ? 8 : 4));
+  L.flags = off;
+  off = align256(off + leaves * sizeof(int));
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
     L.lb = off; off = align256(off + (size_t)n * L.ldsh * 2);
     L.ut = off; off = align256(off + (size_t)n * L.ldsh * 2);
@@ -332,19 +391,21 @@ static ebv_status_t dense_factor_mixed(int64_t n, ebv_prec_t prec, const double 
   k_make_scale<<<1, 1, 0, s>>>(op, scan, scan + 1, scale);
   EBV_TRY(launch_ok());
   float *inv = (float *)(w + L.inv);
+  int *flags = (int *)(w + L.flags);
+  EBV_CU(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)((n + kNB - 1) / kNB), s));
   if (op == 0) {
     EBV_TRY((prepare_leaf_kernels<float, __nv_bfloat16>()));
     Factorizer<float, __nv_bfloat16> f{
         dense_view(lowp, n), n, info, s,
         Shadow<__nv_bfloat16>{(__nv_bfloat16 *)(w + L.lb), (__nv_bfloat16 *)(w + L.ut), L.ldsh, scale}, 0, dst, inv,
-        &stg};
+        &stg, flags};
     EBV_TRY(f.rlu(0, n));
     return stg.ensure(n);
   }
   EBV_TRY((prepare_leaf_kernels<float, __half>()));
   Factorizer<float, __half> f{dense_view(lowp, n), n, info, s,
                               Shadow<__half>{(__half *)(w + L.lb), (__half *)(w + L.ut), L.ldsh, scale}, 1, dst, inv,
-                              &stg};
+                              &stg, flags};
   return f.rlu(0, n);
 }
 
@@ -366,7 +427,10 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   }
   if (prec == EBV_FP32) {
     EBV_TRY((prepare_leaf_kernels<float, float>()));
-    Factorizer<float, float> f{dense_view((float *)a, d->ld), n, info, s, none, -1, dst, (float *)(w + L.inv)};
+    int *flags = (int *)(w + L.flags);
+    EBV_CU(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)((n + kNB - 1) / kNB), s));
+    Factorizer<float, float> f{dense_view((float *)a, d->ld), n,    info, s, none, -1, dst, (float *)(w + L.inv),
+                               nullptr,                           flags};
     return f.rlu(0, n);
   }
   return dense_factor_mixed(n, prec, (const double *)a, d->ld, (float *)lowp, info, w, L, nullptr, 0, true, s);

@@ -336,10 +336,10 @@ __device__ __forceinline__ void warp_tri_inv16(const T *D, T *Z, int ld, int o, 
 }
 
 template <typename T, int NB, int NT>
-__global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
+__device__ __forceinline__ void diag_factor_cta(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv,
+                                                unsigned char *dsm) {
   static_assert(NB == 64 && NT == 256, "4 x 4 sub-blocks of 16, 8 warps");
   constexpr int LD = NB + 1, NSB = NB / kSB;
-  extern __shared__ __align__(16) unsigned char dsm[];
   T *D = reinterpret_cast<T *>(dsm);  // the block, then its packed factors
   T *X = D + NB * LD;                 // L11^{-1}
   T *Y = X + NB * LD;                 // U11^{-1}
@@ -422,6 +422,14 @@ __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, in
     inv[e] = X[i * LD + j];
     inv[NB * NB + e] = Y[i * LD + j];
   }
+}
+
+// One launch of the diagonal-block factorisation (dynamic shared memory:
+// diagb_smem_bytes<T, NB>()).
+template <typename T, int NB, int NT>
+__global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  diag_factor_cta<T, NB, NT>(A, k0, w, info, inv, dsm);
 }
 
 // L21 = A21 U11^{-1} and U12 = L11^{-1} A12 are 64 x 64 x 64 tile products
@@ -684,39 +692,19 @@ __global__ void __launch_bounds__(256) k_leaf_update(MatView<T> A, int64_t c0, i
 template <typename T, int NB>
 constexpr size_t leaf_ru_update_smem_bytes() { return 5 * sizeof(T) * (size_t)NB * diag_tstride<T, NB>(); }
 
+// After the five tiles are staged (and a barrier): L21 = A21 U11^{-1}, U12 =
+// L11^{-1} A12 (stored by the last of the nct CTAs that take part to arrive
+// on st->arrive), A22 -= L21 U12; rows r0 .. r0+h of the right half.
 template <typename T, typename SH, int NB>
-__global__ void __launch_bounds__(256) k_leaf_ru_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
-                                                        const T *inv, Shadow<SH> sh, DevStatus *st) {
-  static_assert(NB == 64, "tile mapping assumes 64");
-  constexpr int TS = diag_tstride<T, NB>(), Q = NB * NB / 256;
-  extern __shared__ __align__(16) unsigned char dsm[];
+__device__ __forceinline__ void leaf_ru_update_tail(MatView<T> A, int64_t c0, int w1, int w2, int64_t r0, int h,
+                                                    Shadow<SH> sh, DevStatus *st, int nct, T *Li, T *U12, T *L21,
+                                                    T *At, T *C) {
+  constexpr int TS = diag_tstride<T, NB>();
   __shared__ int last;
-  T *Li = reinterpret_cast<T *>(dsm);
-  T *U12 = Li + NB * TS;   // A12, then U12
-  T *L21 = U12 + NB * TS;  // U11^{-1}, then L21
-  T *At = L21 + NB * TS;   // A21
-  T *C = At + NB * TS;
-  const int64_t cb = c0 + w1;                        // first column (and row) of the right half
-  const int64_t r0 = cb + (int64_t)blockIdx.x * NB;  // this CTA's rows
-  const int h = (int)min64(NB, n - r0);
-  const T *linv = inv, *uinv = inv + NB * NB;
-  {
-    T f0[Q], f1[Q], f2[Q], f3[Q], f4[Q];
-    fetch_tile<NB, 256>(f0, [&](int i, int k) { return linv[i * NB + k]; });
-    fetch_tile<NB, 256>(f1, [&](int k, int j) { return (k < w1 && j < w2) ? A.get(c0 + k, cb + j) : T(0); });
-    fetch_tile<NB, 256>(f2, [&](int i, int k) { return uinv[i * NB + k]; });
-    fetch_tile<NB, 256>(f3, [&](int i, int k) { return (i < h && k < w1) ? A.get(r0 + i, c0 + k) : T(0); });
-    fetch_tile<NB, 256>(f4, [&](int i, int j) { return (i < h && j < w2) ? A.get(r0 + i, cb + j) : T(0); });
-    put_tile<NB, 256, TS>(Li, f0);
-    put_tile<NB, 256, TS>(U12, f1);
-    put_tile<NB, 256, TS>(L21, f2);
-    put_tile<NB, 256, TS>(At, f3);
-    put_tile<NB, 256, TS>(C, f4);
-  }
-  __syncthreads();
+  const int64_t cb = c0 + w1;
   if (threadIdx.x == 0) {  // A12 is in shared memory: count this CTA as done reading it
     __threadfence();
-    last = atomicAdd(&st->arrive, 1) == (int)gridDim.x - 1;
+    last = atomicAdd(&st->arrive, 1) == nct - 1;
     if (last) st->arrive = 0;  // every CTA has arrived: ready for the next launch
   }
   tile_product<T, NB, TS>(At, L21);  // L21 <- A21 U11^{-1}; ends with a barrier
@@ -755,6 +743,148 @@ __global__ void __launch_bounds__(256) k_leaf_ru_update(MatView<T> A, int64_t c0
     const int i = e / NB, j = e % NB;
     if (i < h && j < w2) A.put(r0 + i, cb + j, C[i * TS + j]);
   }
+}
+
+template <typename T, typename SH, int NB>
+__global__ void __launch_bounds__(256) k_leaf_ru_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
+                                                        const T *inv, Shadow<SH> sh, DevStatus *st) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>(), Q = NB * NB / 256;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T *Li = reinterpret_cast<T *>(dsm);
+  T *U12 = Li + NB * TS;   // A12, then U12
+  T *L21 = U12 + NB * TS;  // U11^{-1}, then L21
+  T *At = L21 + NB * TS;   // A21
+  T *C = At + NB * TS;
+  const int64_t cb = c0 + w1;                        // first column (and row) of the right half
+  const int64_t r0 = cb + (int64_t)blockIdx.x * NB;  // this CTA's rows
+  const int h = (int)min64(NB, n - r0);
+  const T *linv = inv, *uinv = inv + NB * NB;
+  {
+    T f0[Q], f1[Q], f2[Q], f3[Q], f4[Q];
+    fetch_tile<NB, 256>(f0, [&](int i, int k) { return linv[i * NB + k]; });
+    fetch_tile<NB, 256>(f1, [&](int k, int j) { return (k < w1 && j < w2) ? A.get(c0 + k, cb + j) : T(0); });
+    fetch_tile<NB, 256>(f2, [&](int i, int k) { return uinv[i * NB + k]; });
+    fetch_tile<NB, 256>(f3, [&](int i, int k) { return (i < h && k < w1) ? A.get(r0 + i, c0 + k) : T(0); });
+    fetch_tile<NB, 256>(f4, [&](int i, int j) { return (i < h && j < w2) ? A.get(r0 + i, cb + j) : T(0); });
+    put_tile<NB, 256, TS>(Li, f0);
+    put_tile<NB, 256, TS>(U12, f1);
+    put_tile<NB, 256, TS>(L21, f2);
+    put_tile<NB, 256, TS>(At, f3);
+    put_tile<NB, 256, TS>(C, f4);
+  }
+  __syncthreads();
+  leaf_ru_update_tail<T, SH, NB>(A, c0, w1, w2, r0, h, sh, st, (int)gridDim.x, Li, U12, L21, At, C);
+}
+
+// ---------------------------------------------------------------------------
+// A leaf's diagonal block together with the launch that consumes it, as one
+// cooperative launch (binary32 recursion).  CTA 0 factors the block (the
+// blocked diagonal-block code above) and releases the leaf's flag; every
+// other CTA stages its tiles that do not depend on the block, waits for the
+// flag (bounded; gives up if the status block reports an error) and then
+// applies the block's inverses, read past L1.  This takes the launch gap and
+// the consumer's load latency off the recursion's critical path.  All CTAs
+// must be co-resident: the driver launches these only when the grid fits.
+//   k_diag_l21:        the leaf's L21 for every row below (CTA b >= 1 owns
+//                      the 64-row block b-1), as k_trsm_ru;
+//   k_diag_l21_update: the left leaf of a two-leaf node with
+//                      k_leaf_ru_update's work for the right half.
+// Dynamic shared memory: diag_fused_smem_bytes<T, NB>().
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+constexpr size_t diag_fused_smem_bytes() {
+  return diagb_smem_bytes<T, NB>() > leaf_ru_update_smem_bytes<T, NB>() ? diagb_smem_bytes<T, NB>()
+                                                                        : leaf_ru_update_smem_bytes<T, NB>();
+}
+
+// Thread 0 waits for *flag >= 1; true for every thread once it has.
+__device__ __forceinline__ bool cta_wait_flag(const int *flag, DevStatus *st, int where) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = bounded_wait_geq(flag, 1, st, kSpinLimit, where);
+  __syncthreads();
+  return ok != 0;
+}
+__device__ __forceinline__ void cta_release_flag(int *flag) {
+  __syncthreads();  // every thread's stores of the block and its inverses are done
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flag, 1);
+  }
+}
+
+template <typename T, typename SH, int NB>
+__global__ void __launch_bounds__(256) k_diag_l21(MatView<T> A, int64_t c0, int w, int64_t n, int32_t *info, T *inv,
+                                                  Shadow<SH> sh, int *flag, DevStatus *st) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>();
+  extern __shared__ __align__(16) unsigned char dsm[];
+  if (blockIdx.x == 0) {
+    diag_factor_cta<T, NB, 256>(A, c0, w, info, inv, dsm);
+    cta_release_flag(flag);
+    return;
+  }
+  T *At = reinterpret_cast<T *>(dsm);
+  T *Ui = At + NB * TS;
+  const int64_t r0 = c0 + w + (int64_t)(blockIdx.x - 1) * NB;
+  const int h = (int)min64(NB, n - r0);
+  stage_tile<NB, 256, TS>(At, [&](int i, int k) { return (i < h && k < w) ? A.get(r0 + i, c0 + k) : T(0); });
+  if (!cta_wait_flag(flag, st, -1)) return;
+  const T *uinv = inv + NB * NB;
+  stage_tile<NB, 256, TS>(Ui, [&](int i, int k) { return __ldcg(uinv + i * NB + k); });
+  __syncthreads();
+  tile_product<T, NB, TS>(At, Ui);  // Ui <- A21 U11^{-1}
+  const float s = sh.lb ? sh.scale[0] : 1.f;
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int ii = e / NB, k = e % NB;
+    if (ii < h && k < w) {
+      const T v = Ui[ii * TS + k];
+      A.put(r0 + ii, c0 + k, v);
+      if (sh.lb) sh.lb[(r0 + ii) * sh.ld + c0 + k] = from_float<SH>((float)v * s);
+    }
+  }
+}
+
+template <typename T, typename SH, int NB>
+__global__ void __launch_bounds__(256) k_diag_l21_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
+                                                         int32_t *info, T *inv, Shadow<SH> sh, int *flag,
+                                                         DevStatus *st) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>(), Q = NB * NB / 256;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  if (blockIdx.x == 0) {
+    diag_factor_cta<T, NB, 256>(A, c0, w1, info, inv, dsm);
+    cta_release_flag(flag);
+    return;
+  }
+  T *Li = reinterpret_cast<T *>(dsm);
+  T *U12 = Li + NB * TS;
+  T *L21 = U12 + NB * TS;
+  T *At = L21 + NB * TS;
+  T *C = At + NB * TS;
+  const int64_t cb = c0 + w1;
+  const int64_t r0 = cb + (int64_t)(blockIdx.x - 1) * NB;
+  const int h = (int)min64(NB, n - r0);
+  {  // the tiles that do not depend on the diagonal block
+    T f1[Q], f3[Q], f4[Q];
+    fetch_tile<NB, 256>(f1, [&](int k, int j) { return (k < w1 && j < w2) ? A.get(c0 + k, cb + j) : T(0); });
+    fetch_tile<NB, 256>(f3, [&](int i, int k) { return (i < h && k < w1) ? A.get(r0 + i, c0 + k) : T(0); });
+    fetch_tile<NB, 256>(f4, [&](int i, int j) { return (i < h && j < w2) ? A.get(r0 + i, cb + j) : T(0); });
+    put_tile<NB, 256, TS>(U12, f1);
+    put_tile<NB, 256, TS>(At, f3);
+    put_tile<NB, 256, TS>(C, f4);
+  }
+  if (!cta_wait_flag(flag, st, -2)) return;
+  {
+    const T *linv = inv, *uinv = inv + NB * NB;
+    T f0[Q], f2[Q];
+    fetch_tile<NB, 256>(f0, [&](int i, int k) { return __ldcg(linv + i * NB + k); });
+    fetch_tile<NB, 256>(f2, [&](int i, int k) { return __ldcg(uinv + i * NB + k); });
+    put_tile<NB, 256, TS>(Li, f0);
+    put_tile<NB, 256, TS>(L21, f2);
+  }
+  __syncthreads();
+  leaf_ru_update_tail<T, SH, NB>(A, c0, w1, w2, r0, h, sh, st, (int)gridDim.x - 1, Li, U12, L21, At, C);
 }
 
 // ---------------------------------------------------------------------------
@@ -1016,6 +1146,10 @@ ebv_status_t prepare_leaf_kernels() {
       e = set_smem(k_leaf_update<T, SH, kNB>, (int)leaf_update_smem_bytes<T, kNB>());
     if (e == cudaSuccess)
       e = set_smem(k_leaf_ru_update<T, SH, kNB>, (int)leaf_ru_update_smem_bytes<T, kNB>());
+    if (e == cudaSuccess)
+      e = set_smem(k_diag_l21<T, SH, kNB>, (int)diag_fused_smem_bytes<T, kNB>());
+    if (e == cudaSuccess)
+      e = set_smem(k_diag_l21_update<T, SH, kNB>, (int)diag_fused_smem_bytes<T, kNB>());
     const int tb = (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
     if (e == cudaSuccess)
       e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64>, tb);
