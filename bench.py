@@ -306,8 +306,7 @@ def run_gpu(args, rank, world, dist):
         pass
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_work, dom_cnt) = dom
-    roofline = roofline_for(dom_name, dom_ms, dom_work, dom_cnt, peaks, args,
-                            active=int(rep_np["iters"]) + 1 if dom_name == "residual" else None)
+    roofline = roofline_for(dom_name, dom_ms, dom_work, dom_cnt, peaks, args, active=active_launches(dom_name, rep_np))
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_kstop > 0:
@@ -332,8 +331,7 @@ def run_gpu(args, rank, world, dist):
                        "err_vs_x_true": err_true, "info": info_v},
         "fp64_plain": fp64,
         "roofline": roofline,
-        "rooflines_by_class": {k: roofline_for(k, v[0], v[1], v[2], peaks, args,
-                                               active=int(rep_np["iters"]) + 1 if k == "residual" else None)
+        "rooflines_by_class": {k: roofline_for(k, v[0], v[1], v[2], peaks, args, active=active_launches(k, rep_np))
                                for k, v in prof.items() if v[2] > 0},
         "kernel_classes_ms": {k: round(v[0], 4) for k, v in prof.items() if v[2] > 0},
         "kernel_classes_launches": {k: v[2] for k, v in prof.items() if v[2] > 0},
@@ -347,6 +345,13 @@ def run_gpu(args, rank, world, dist):
         "input_gen_s": t_gen,
     }
     return line
+
+
+def active_launches(name, rep):
+    """Launches of a refinement-loop class that did work: iters + 1 residuals,
+    2 (iters + 1) triangles."""
+    it = int(rep["iters"]) + 1
+    return {"residual": it, "trsv": 2 * it}.get(name)
 
 
 def roofline_for(name, ms, work, cnt, peaks, args, active=None):
@@ -378,6 +383,10 @@ def roofline_for(name, ms, work, cnt, peaks, args, active=None):
         return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": src,
                 "launches": act, "avg_launch_ms": ms / act}
+    if name == "trsv" and active:
+        # Substitution launches after the stop test has passed exit at once:
+        # only the diagonal inverses and `active` triangles do work.
+        work = work * (active + 1) / cnt
     achieved = work / (ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 75.1, "unit": "TFLOP/s",
             "frac": achieved / 75.1, "traffic": None, "peak_source": "measured FFMA probe", "launches": cnt,
