@@ -530,6 +530,24 @@ def run_configs(args):
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
                 "band_bytes": int(ab.nbytes), "info": int(info.item())})
     print(json.dumps(out[-1]), flush=True)
+
+    # the same Laplacian as a symmetric band (EBV_BAND_SYM: U12 = D11 L21^T,
+    # block-lower trailing updates); same output, same nominal flops
+    def c1s():
+        lu.copy_(AB)
+        x.copy_(B)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=ws, kl=kl, ku=ku, storage=ebv.BAND_SYM)
+        ebv.ebv_solve(lu, x, "fp64", ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
+
+    ms = _dev_ms(c1s, 3, 2)
+    xs = x.cpu().numpy()
+    r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
+    out.append({"config": "band FP64 Laplacian 512x512, symmetric storage mode, 8 RHS", "ms": ms,
+                "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
+                "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
+                "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
+                "info": int(info.item())})
+    print(json.dumps(out[-1]), flush=True)
     del AB, B, lu, x, ws
 
     # dense n = 16384, 32 RHS: FP16 updates + refinement (bf16 is the bench line)

@@ -77,7 +77,17 @@ typedef enum {
                          scaled by a power of two to stay in half's normal range */
 } ebv_prec_t;
 
-typedef enum { EBV_DENSE = 0, EBV_BAND = 1 } ebv_storage_t;
+/*
+ * EBV_BAND_SYM: a symmetric A in the same row-band storage as EBV_BAND with
+ * kl == ku (both halves present).  The factorisation uses the lower half:
+ * for symmetric A the U vectors are the scaled L vectors, U12 = D11 L21^T
+ * with D11 the pivots (eq. 6a-b scale both vectors by the same pivot), and
+ * the trailing update L21 D11 L21^T is symmetric, so only its block-lower
+ * part is formed.  The result is the same packed L\U band as EBV_BAND and
+ * ebv_solve treats both alike.  (Project addition: the LDL^T reading of the
+ * method for symmetric diagonally dominant systems.)
+ */
+typedef enum { EBV_DENSE = 0, EBV_BAND = 1, EBV_BAND_SYM = 2 } ebv_storage_t;
 
 typedef struct ebv_desc {
   int64_t n;       /* order of A, n >= 0 */
@@ -129,7 +139,7 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *             non-finite pivot.  Always written.
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
- * Band storage (EBV_BAND) supports EBV_FP64 and EBV_FP32; fill-in stays inside
+ * Band storage (EBV_BAND, EBV_BAND_SYM) supports EBV_FP64 and EBV_FP32; fill-in stays inside
  * the band because no rows are exchanged.
  */
 EBV_API ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *lowp,

@@ -32,7 +32,7 @@ OK, ERR_ARG, ERR_ZERO_PIVOT, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_
 # ebv_prec_t
 FP64, FP32, MIXED_BF16, MIXED_FP16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
-DENSE, BAND = 0, 1
+DENSE, BAND, BAND_SYM = 0, 1, 2
 
 
 class EbvError(RuntimeError):
@@ -343,12 +343,13 @@ def solve(f: Factors, b: torch.Tensor, refine: tuple | None = None, report: torc
     return x.view(b.shape) if b.dim() == 1 else x
 
 
-def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64") -> Factors:
-    """Factor a row-band matrix (n x (kl+ku+1))."""
+def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64", sym: bool = False) -> Factors:
+    """Factor a row-band matrix (n x (kl+ku+1)).  sym: A is symmetric (kl == ku,
+    both halves stored); U is formed from L and the pivots (EBV_BAND_SYM)."""
     p = _prec(prec)
     dt = torch.float64 if p == FP64 else torch.float32
     lu = ab.to(dt).clone().contiguous()
-    info = ebv_factor(lu, p, kl=kl, ku=ku, storage=BAND)
+    info = ebv_factor(lu, p, kl=kl, ku=ku, storage=BAND_SYM if sym else BAND)
     return Factors(lu, info, p, ab.to(torch.float64).contiguous(), kl, ku, BAND)
 
 

@@ -36,8 +36,9 @@ ebv_status_t check_desc(const ebv_desc_t *d, ebv_prec_t prec) {
   if (d->n < 0 || d->n > kMaxN) return EBV_ERR_ARG;
   if (d->storage == EBV_DENSE) {
     if (d->ld < std::max<int64_t>(1, d->n)) return EBV_ERR_ARG;
-  } else if (d->storage == EBV_BAND) {
+  } else if (d->storage == EBV_BAND || d->storage == EBV_BAND_SYM) {
     if (d->kl < 0 || d->ku < 0) return EBV_ERR_ARG;
+    if (d->storage == EBV_BAND_SYM && d->kl != d->ku) return EBV_ERR_ARG;
     if (d->n > 0 && (d->kl >= d->n || d->ku >= d->n)) return EBV_ERR_ARG;
     if (d->ld < d->kl + d->ku + 1) return EBV_ERR_ARG;
     if (is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
@@ -71,7 +72,7 @@ const char *ebv_status_string(ebv_status_t s) {
 size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64_t nrhs) {
   if (check_desc(desc, prec) != EBV_OK || nrhs < 0) return 0;
   const int64_t n = desc->n;
-  if (desc->storage == EBV_BAND)
+  if (desc->storage != EBV_DENSE)
     return std::max(band_factor_ws(n, desc->kl, desc->ku, prec), band_solve_ws(n, nrhs, prec));
   return std::max(dense_factor_ws(n, prec), dense_solve_ws(n, nrhs, prec));
 }
@@ -84,7 +85,7 @@ ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *
   if (is_mixed(prec) && desc->n > 0 && (!lowp || !aligned(lowp, 16))) return EBV_ERR_ARG;
   if (ws && !aligned(ws, 256)) return EBV_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  if (desc->storage == EBV_BAND) {
+  if (desc->storage != EBV_DENSE) {
     if (!ws || ws_bytes < band_factor_ws(desc->n, desc->kl, desc->ku, prec)) return EBV_ERR_WORKSPACE;
     return band_factor(desc, prec, a, info_dev, ws, ws_bytes, s);
   }
@@ -111,7 +112,7 @@ ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, 
   if (report_dev && !aligned(report_dev, 8)) return EBV_ERR_ARG;
   if (!ws || !aligned(ws, 256)) return EBV_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
-  if (desc->storage == EBV_BAND)
+  if (desc->storage != EBV_DENSE)
     return band_solve(desc, prec, lu, a_orig, b, nrhs, ldb, refine, report_dev, ws, ws_bytes, s);
   return dense_solve(desc, prec, lu, a_orig, b, nrhs, ldb, refine, report_dev, ws, ws_bytes, s);
 }

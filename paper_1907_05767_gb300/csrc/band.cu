@@ -29,7 +29,7 @@ struct BandGemm<float> {
 };
 
 template <typename T>
-ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaStream_t s) {
+ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, bool sym, cudaStream_t s) {
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
   using G = BandGemm<T>;
   EBV_TRY((prepare_leaf_kernels<T, float>()));
@@ -53,7 +53,11 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
         k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
       EBV_TRY(launch_ok());
     }
-    if (ce > cb) {
+    if (ce > cb && sym) {  // U12 = D11 L21^T
+      prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
+      k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
+      EBV_TRY(launch_ok());
+    } else if (ce > cb) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * w * w * (ce - cb));
       if constexpr (sizeof(T) == 8)
         k_trsm_ll_multi<T, float, kNB, kTrsmMaxBlocks, 16>
@@ -66,8 +70,9 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, cudaS
     if (re > rb && ce > cb) {
       prof::Scope ps(s, prof::kSimtGemm, 2.0 * (re - rb) * (ce - cb) * w);
       dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
+      // symmetric: L21 D11 L21^T, only its block-lower part (the diagonal 64-blocks whole)
       k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
-          <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w);
+          <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0);
       EBV_TRY(launch_ok());
     }
   }
@@ -127,10 +132,11 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t 
   if (d->n == 0) return EBV_OK;
   if (!ws || ws_bytes < band_factor_ws(d->n, d->kl, d->ku, prec)) return EBV_ERR_WORKSPACE;
   char *inv = (char *)ws + kStatusBytes;
+  const bool sym = d->storage == EBV_BAND_SYM;
   if (prec == EBV_FP64)
-    return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, (double *)inv, s);
+    return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, (double *)inv, sym, s);
   if (prec == EBV_FP32)
-    return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, s);
+    return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, sym, s);
   return EBV_ERR_UNSUPPORTED;
 }
 

@@ -12,14 +12,16 @@ namespace {
 // Right-hand sides per substitution chain (RC): each chunk of RC columns is
 // solved by its own chain of CTAs.  One chain of 32 reads the factors once
 // and, up to n = 64 x (resident CTAs), gives every CTA a single row block,
-// so no CTA has a backlog of folds when its block's turn comes.
+// so no CTA has a backlog of folds when its block's turn comes.  Up to 8
+// right-hand sides take chunks of 8 instead: the products cover whole
+// chunks, and 32-wide ones would spend 3/4 of the arithmetic on zero columns.
 // NS: stages of the factor-tile ring; MINB: CTAs per SM the kernel is
-// compiled for (binary32: two 91 KB CTAs per SM).
-template <typename T>
+// compiled for.
+template <typename T, int RCW = 32>
 struct TrsvCfg {
-  static constexpr int RC = 32;
+  static constexpr int RC = RCW;
   static constexpr int NS = sizeof(T) == 4 ? 3 : 2;
-  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int MINB = RCW == 32 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 3 : 2);
 };
 
 struct DenseSolveLayout {
@@ -65,10 +67,10 @@ ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
 // One triangle of the substitution as a cooperative persistent launch: at
 // most as many CTAs per right-hand-side chunk as can be resident at once
 // (the CTAs wait on one another's published blocks).
-template <typename T, bool UPPER>
-ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
-                      unsigned long long *xw, DevStatus *st, cudaStream_t s) {
-  using C = TrsvCfg<T>;
+template <typename T, bool UPPER, int RCW>
+ebv_status_t trsv_launch(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+                         unsigned long long *xw, DevStatus *st, cudaStream_t s) {
+  using C = TrsvCfg<T, RCW>;
   constexpr int RC = C::RC;
   constexpr size_t smem = trsvl_smem_bytes<T, kNB, RC, C::NS>();
   auto kern = k_trsv_left<T, kNB, RC, UPPER, C::NS, C::MINB>;
@@ -97,6 +99,13 @@ ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, cons
   cfg.numAttrs = 1;
   EBV_CU(cudaLaunchKernelEx(&cfg, kern, F, n, B, ldb, nrhs, dinv, xw, st));
   return launch_ok();
+}
+
+template <typename T, bool UPPER>
+ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+                      unsigned long long *xw, DevStatus *st, cudaStream_t s) {
+  if (nrhs <= 8) return trsv_launch<T, UPPER, 8>(F, n, B, ldb, nrhs, dinv, xw, st, s);
+  return trsv_launch<T, UPPER, 32>(F, n, B, ldb, nrhs, dinv, xw, st, s);
 }
 
 // Forward then backward block substitution of B (n x nrhs, T) in place.

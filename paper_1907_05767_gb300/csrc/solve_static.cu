@@ -67,7 +67,7 @@ extern "C" ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec
   // Sizes beyond the static array are rejected before any device work.
   if (desc->n > EBV_STATIC_MAX_N || nrhs > EBV_STATIC_MAX_NRHS) return EBV_ERR_WORKSPACE;
   if (desc->n < 0 || nrhs < 0) return EBV_ERR_ARG;
-  const size_t need = desc->storage == EBV_BAND ? band_solve_ws(desc->n, nrhs, prec)
+  const size_t need = desc->storage != EBV_DENSE ? band_solve_ws(desc->n, nrhs, prec)
                                                 : dense_solve_ws(desc->n, nrhs, prec);
   if (need > kStaticBytes) return EBV_ERR_WORKSPACE;
   void *ws = nullptr;

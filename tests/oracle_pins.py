@@ -278,6 +278,34 @@ def pin_band(lib):
     np.testing.assert_allclose(x2, np.linalg.solve(a2, np.ones((n2, 1))), rtol=0, atol=1e-14)
 
 
+def pin_symmetric_ldlt(lib):
+    # Symmetric A (the reading of eq. 6a-b that scales both vectors by the same
+    # pivot): Doolittle's U is D L^T with D the pivots.  For symmetric,
+    # strictly diagonally dominant A with a positive diagonal A is positive
+    # definite, and the Cholesky factor R (A = R R^T, numpy) gives the same
+    # L = R diag(1/r_ii) and D = diag(r_ii^2) independently.
+    n = 40
+    a = synthetic.dense_dd(n, 0.9, 6001)
+    a = 0.5 * (a + a.T)
+    f, info = oracle.lu(a, lib=lib)
+    assert info == 0
+    L = np.tril(f, -1) + np.eye(n)
+    U = np.triu(f)
+    d = np.diag(U)
+    np.testing.assert_allclose(U, np.diag(d) @ L.T, rtol=0, atol=1e-15)
+    r = np.linalg.cholesky(a)
+    np.testing.assert_allclose(L, r / np.diag(r), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(d, np.diag(r) ** 2, rtol=1e-14, atol=0)
+    # the symmetric band: the 2-D Laplacian (symmetric, kl == ku)
+    ab, kl, ku = synthetic.laplacian_band(7)
+    fb, info = oracle.band_lu(ab, kl, ku, lib=lib)
+    assert info == 0
+    fd = synthetic.band_to_dense(fb, kl, ku)
+    Lb = np.tril(fd, -1) + np.eye(fd.shape[0])
+    Ub = np.triu(fd)
+    np.testing.assert_allclose(Ub, np.diag(np.diag(Ub)) @ Lb.T, rtol=0, atol=1e-14)
+
+
 def pin_adjoint(lib):
     n, nrhs = 12, 3
     a = synthetic.dense_dd(n, 0.9, 6001)
@@ -369,6 +397,7 @@ ALL_PINS = [
     pin_lapack_lu_column_dominant,
     pin_planted_solution,
     pin_band,
+    pin_symmetric_ldlt,
     pin_adjoint,
     pin_residual,
     pin_partial_factorisation,

@@ -61,6 +61,7 @@ def test_factor_argument_errors(lib):
         (_d(8, 8, 8, 1, ebv.BAND), ebv.FP64),              # kl >= n
         (_d(8, 3, 1, 2, ebv.BAND), ebv.FP64),              # ld < kl+ku+1
         (_d(8, 8, 0, 0, 7), ebv.FP64),                     # unknown storage
+        (_d(8, 4, 1, 2, ebv.BAND_SYM), ebv.FP64),          # symmetric band with kl != ku
     ]
     for d, p in cases:
         st = lib.ebv_factor(ctypes.byref(d) if d is not None else None, p, FAKE, None, info, None, 0, None)

@@ -20,11 +20,11 @@ def banded_dd(n, kl, ku, seed, w=0.9):
     return synthetic.dense_to_band(a, kl, ku), a
 
 
-def check(ab, kl, ku, nrhs, seed, prec="fp64"):
+def check(ab, kl, ku, nrhs, seed, prec="fp64", sym=False):
     n = ab.shape[0]
     x_true = synthetic.planted_x(n, nrhs, seed)
     b = synthetic.band_rhs(ab, kl, ku, x_true)
-    f = ebv.band_factor(torch.from_numpy(ab).to(DEV), kl, ku, prec)
+    f = ebv.band_factor(torch.from_numpy(ab).to(DEV), kl, ku, prec, sym=sym)
     x = ebv.solve(f, torch.from_numpy(b).to(DEV)).cpu().numpy().astype(np.float64)
     assert int(f.info.item()) == 0
     fb, _ = oracle.band_lu(ab, kl, ku)
@@ -96,3 +96,37 @@ def test_band_refined_solution():
     fb, _ = oracle.band_lu(ab, kl, ku)
     x_ref = oracle.band_solve(fb, kl, ku, b)
     assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-12
+
+
+def symmetric_banded_dd(n, k, seed, w=0.9):
+    a = synthetic.dense_dd(n, w, seed)
+    a = 0.5 * (a + a.T)  # still strictly diagonally dominant
+    d = np.subtract.outer(np.arange(n), np.arange(n))
+    a[np.abs(d) > k] = 0.0
+    return synthetic.dense_to_band(a, k, k)
+
+
+@pytest.mark.parametrize("g", [4, 8, 33, 64])
+def test_symmetric_laplacian_grid(g):
+    # EBV_BAND_SYM: U12 = D11 L21^T and the block-lower trailing update give
+    # the same (unique) factors as the general band path, within rounding.
+    ab, kl, ku = synthetic.laplacian_band(g)
+    check(ab, kl, ku, 8, 300 + g, sym=True)
+
+
+@pytest.mark.parametrize("n,k", [(500, 70), (130, 64), (257, 1), (70, 69), (300, 128), (200, 0)])
+def test_symmetric_bands(n, k):
+    ab = symmetric_banded_dd(n, k, 11 * n + k)
+    f, _ = check(ab, k, k, 3, n + 1, sym=True)
+    # the stored U vectors are the pivots times the L vectors: u_ij = u_ii l_ji
+    lu = f.lu.cpu().numpy()
+    for i in range(0, n, max(1, n // 17)):
+        for j in range(i + 1, min(n, i + k + 1)):
+            u = lu[i, j - i + k]
+            l = lu[j, i - j + k]
+            assert abs(u - lu[i, k] * l) <= 1e-13 * max(1.0, abs(u))
+
+
+def test_symmetric_band_fp32():
+    ab, kl, ku = synthetic.laplacian_band(20)
+    check(ab, kl, ku, 2, 7, prec="fp32", sym=True)
