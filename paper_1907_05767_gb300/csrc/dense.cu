@@ -213,6 +213,15 @@ struct Factorizer {
       return grid <= (update ? cap_upd : cap_l21) ? (int)grid : 0;
     }
   }
+  // Whether a k_diag_l21_u12 grid fits co-resident.
+  bool u12_fits(int64_t grid) const {
+    if constexpr (sizeof(T) != 4) {
+      return false;
+    } else {
+      static const int cap = coop_capacity(k_diag_l21_u12<T, SH, kNB>, diag_fused_smem_bytes<T, kNB>());
+      return flags && grid <= cap;
+    }
+  }
 
   static int64_t split(int64_t w) {  // leaf-aligned first half of a w-wide range
     const int64_t nb = (w + kNB - 1) / kNB;
@@ -330,6 +339,31 @@ struct Factorizer {
         EBV_TRY(launch_ok());
       }
       return leaf(c0 + w1, (int)(w - w1));
+    }
+    if (w1 == 2 * kNB && w <= 4 * kNB) {
+      // The left half is two full leaves: the first as one fused launch, the
+      // second fused with this node's U12 (columns c0+w1 .. c0+w).
+      const int64_t rows1 = n - c0 - kNB, rows2 = n - c0 - w1;
+      const int g1 = fused_grid(true, rows1);
+      const int nl = ceil_div(rows2, kNB), nu = ceil_div(w - w1, 16);
+      if (g1 && u12_fits(1 + nl + nu)) {
+        EBV_TRY(need(c0 + w));
+        {
+          prof::Scope ps(s, prof::kPanel,
+                         2.0 * kNB * kNB * kNB / 3.0 + 2.0 * rows1 * kNB * kNB * 2.0 + 2.0 * rows1 * kNB * kNB);
+          EBV_TRY(launch_coop(k_diag_l21_update<T, SH, kNB>, g1, diag_fused_smem_bytes<T, kNB>(), A, c0, (int)kNB,
+                              (int)kNB, n, info, leaf_inv(c0), sh, flags + c0 / kNB, st));
+        }
+        {
+          prof::Scope ps(s, prof::kPanel,
+                         2.0 * kNB * kNB * kNB / 3.0 + 2.0 * rows2 * kNB * kNB + 1.0 * w1 * w1 * (w - w1));
+          EBV_TRY(launch_coop(k_diag_l21_u12<T, SH, kNB>, 1 + nl + nu, diag_fused_smem_bytes<T, kNB>(), A, c0,
+                              (int)kNB, n, nl, c0 + w1, c0 + w, info, (const T *)leaf_inv(c0), leaf_inv(c0 + kNB),
+                              sh, flags + (c0 + kNB) / kNB, st));
+        }
+        EBV_TRY(gemm(c0 + w1, c0 + w1, c0, n - c0 - w1, w - w1, w1));
+        return rlu(c0 + w1, w - w1);
+      }
     }
     EBV_TRY(rlu(c0, w1));
     EBV_TRY(trsm_ll(c0, w1, c0 + w1, c0 + w));

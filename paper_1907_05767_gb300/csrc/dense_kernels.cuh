@@ -845,6 +845,102 @@ __global__ void __launch_bounds__(256) k_diag_l21(MatView<T> A, int64_t c0, int 
   }
 }
 
+// k_diag_l21 for the second leaf of a two-leaf node (columns c0+w1 ..
+// c0+2*w1, w1 = 64) that also forms the parent node's U12 for the columns
+// [cu, cu_end) when nu > 0: CTAs 1 .. nl are the L21 row blocks, CTAs nl+1 ..
+// take 16-column strips of U12 = L11^{-1} A12 over the node's two leaves:
+// U_0 = L_00^{-1} A_0 and A_1 - L_10 U_0 do not depend on the second
+// diagonal block and are formed while CTA 0 factors it; after its flag only
+// U_1 = L_11^{-1} (A_1 - L_10 U_0) remains.  c0 here is the node's first
+// column; the leaf being factored starts at c0 + 64.
+template <typename T, typename SH, int NB>
+__global__ void __launch_bounds__(256) k_diag_l21_u12(MatView<T> A, int64_t c0, int w, int64_t n, int nl,
+                                                      int64_t cu, int64_t cu_end, int32_t *info, const T *inv0,
+                                                      T *inv1, Shadow<SH> sh, int *flag, DevStatus *st) {
+  static_assert(NB == 64, "tile mapping assumes 64");
+  constexpr int TS = diag_tstride<T, NB>(), CW = 16, Q = NB * NB / 256;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int64_t cl = c0 + NB;  // the leaf factored here
+  if (blockIdx.x == 0) {
+    diag_factor_cta<T, NB, 256>(A, cl, w, info, inv1, dsm);
+    cta_release_flag(flag);
+    return;
+  }
+  if ((int)blockIdx.x <= nl) {  // L21 of the leaf for the 64-row block blockIdx.x - 1 below it
+    T *At = reinterpret_cast<T *>(dsm);
+    T *Ui = At + NB * TS;
+    const int64_t r0 = cl + w + (int64_t)(blockIdx.x - 1) * NB;
+    const int h = (int)min64(NB, n - r0);
+    stage_tile<NB, 256, TS>(At, [&](int i, int k) { return (i < h && k < w) ? A.get(r0 + i, cl + k) : T(0); });
+    if (!cta_wait_flag(flag, st, -5)) return;
+    const T *uinv = inv1 + NB * NB;
+    stage_tile<NB, 256, TS>(Ui, [&](int i, int k) { return __ldcg(uinv + i * NB + k); });
+    __syncthreads();
+    tile_product<T, NB, TS>(At, Ui);  // Ui <- A21 U11^{-1}
+    const float s = sh.lb ? sh.scale[0] : 1.f;
+    for (int e = threadIdx.x; e < NB * NB; e += 256) {
+      const int ii = e / NB, k = e % NB;
+      if (ii < h && k < w) {
+        const T v = Ui[ii * TS + k];
+        A.put(r0 + ii, cl + k, v);
+        if (sh.lb) sh.lb[(r0 + ii) * sh.ld + cl + k] = from_float<SH>((float)v * s);
+      }
+    }
+    return;
+  }
+  // U12 strip: columns j0 .. j0+16 of rows c0 .. c0+64+w of the parent node
+  T *L0 = reinterpret_cast<T *>(dsm);  // L_00^{-1}, later L_11^{-1}
+  T *L10 = L0 + NB * TS;
+  T *U0 = L10 + NB * TS;   // 64 x CW strips (row stride TS)
+  T *U1 = U0 + NB * TS;
+  const int64_t j0 = cu + (int64_t)(blockIdx.x - 1 - nl) * CW;
+  const int wc = (int)min64(CW, cu_end - j0);
+  {
+    T f0[Q], f1[Q];
+    fetch_tile<NB, 256>(f0, [&](int i, int k) { return inv0[i * NB + k]; });
+    fetch_tile<NB, 256>(f1, [&](int i, int k) { return (i < w) ? A.get(cl + i, c0 + k) : T(0); });
+    put_tile<NB, 256, TS>(L0, f0);
+    put_tile<NB, 256, TS>(L10, f1);
+    for (int e = threadIdx.x; e < NB * CW; e += 256) {
+      const int k = e / CW, c = e % CW;
+      U0[k * TS + c] = c < wc ? A.get(c0 + k, j0 + c) : T(0);
+      U1[k * TS + c] = (k < w && c < wc) ? A.get(cl + k, j0 + c) : T(0);
+    }
+  }
+  __syncthreads();
+  tile_product<T, NB, TS, CW>(L0, U0);  // U_0 = L_00^{-1} A_0
+  {
+    T acc[StripMap<CW>::RPT][4];
+    tile_regs<T, TS, CW>(U1, acc);
+    tile_fma<T, NB, TS, true, CW>(L10, U0, acc);  // A_1 - L_10 U_0
+    __syncthreads();
+    tile_put<T, TS, CW>(U1, acc);
+  }
+  if (!cta_wait_flag(flag, st, -6)) return;
+  {
+    T f0[Q];
+    fetch_tile<NB, 256>(f0, [&](int i, int k) { return __ldcg(inv1 + i * NB + k); });
+    put_tile<NB, 256, TS>(L0, f0);  // L_11^{-1}
+  }
+  __syncthreads();
+  tile_product<T, NB, TS, CW>(L0, U1);  // U_1
+  const float s = sh.ut ? sh.scale[1] : 1.f;
+  for (int e = threadIdx.x; e < 2 * NB * CW; e += 256) {
+    const int kk = e / CW, c = e % CW;  // row kk of the node (0 .. 2 NB)
+    const int k = kk % NB;
+    const T *Ub = kk < NB ? U0 : U1;
+    if (c < wc && (kk < NB || k < w)) A.put(c0 + kk, j0 + c, Ub[k * TS + c]);
+  }
+  if (sh.ut) {
+    for (int e = threadIdx.x; e < 2 * NB * CW; e += 256) {
+      const int c = e / (2 * NB), kk = e % (2 * NB);
+      const int k = kk % NB;
+      const T *Ub = kk < NB ? U0 : U1;
+      if (c < wc && (kk < NB || k < w)) sh.ut[(j0 + c) * sh.ld + c0 + kk] = from_float<SH>((float)Ub[k * TS + c] * s);
+    }
+  }
+}
+
 template <typename T, typename SH, int NB>
 __global__ void __launch_bounds__(256) k_diag_l21_update(MatView<T> A, int64_t c0, int w1, int w2, int64_t n,
                                                          int32_t *info, T *inv, Shadow<SH> sh, int *flag,
@@ -1150,6 +1246,8 @@ ebv_status_t prepare_leaf_kernels() {
       e = set_smem(k_diag_l21<T, SH, kNB>, (int)diag_fused_smem_bytes<T, kNB>());
     if (e == cudaSuccess)
       e = set_smem(k_diag_l21_update<T, SH, kNB>, (int)diag_fused_smem_bytes<T, kNB>());
+    if (e == cudaSuccess)
+      e = set_smem(k_diag_l21_u12<T, SH, kNB>, (int)diag_fused_smem_bytes<T, kNB>());
     const int tb = (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>();
     if (e == cudaSuccess)
       e = set_smem(k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64>, tb);
