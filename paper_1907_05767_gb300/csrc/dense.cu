@@ -1,4 +1,4 @@
-// Dense factorisation and solve drivers.
+// Dense factorisation and solve: host-side orchestration of the kernels.
 //
 // Factorisation: recursive column-halving Doolittle (no pivoting).  A panel of
 // w columns is factored by factoring its left half, computing the U vectors of

@@ -1,5 +1,5 @@
 // Leaf kernels of the blocked / recursive Doolittle factorisation and the
-// SIMT trailing-update GEMMs.  Used by the dense and the banded drivers.
+// SIMT trailing-update GEMMs.  Used by the dense and the banded host code.
 //
 // Method (arXiv 1907.05767): Eq. 6a divides the L vector of step r by the
 // pivot; Eq. 6c subtracts the outer product of the L and U vectors from the
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(256) k_leaf_ru_update(MatView<T> A, int64_t c0
 // flag (bounded; gives up if the status block reports an error) and then
 // applies the block's inverses, read past L1.  This takes the launch gap and
 // the consumer's load latency off the recursion's critical path.  All CTAs
-// must be co-resident: the driver launches these only when the grid fits.
+// must be co-resident: the host code launches these only when the grid fits.
 //   k_diag_l21:        the leaf's L21 for every row below (CTA b >= 1 owns
 //                      the 64-row block b-1), as k_trsm_ru;
 //   k_diag_l21_update: the left leaf of a two-leaf node with
@@ -1075,7 +1075,7 @@ constexpr int kTrsmMaxBlocks = 4;  // rows of the one-launch TRSM: up to 4 leave
 // across four groups of 64 threads, each with a 4 x 4 register block over a
 // quarter of K, and reduced through shared memory: a strip this narrow gives
 // one thread too few outputs to keep the FMA pipe busy otherwise.
-// Requires 16-byte aligned rows (ld % 4 == 0, aligned base); the driver
+// Requires 16-byte aligned rows (ld % 4 == 0, aligned base); the host code
 // falls back to the streaming kernel otherwise.
 // Dynamic shared memory: trsm_res_smem_bytes<NB, MAXB>().
 constexpr int kResCW = 16, kResUS = kResCW + 4;  // strip width, its row stride

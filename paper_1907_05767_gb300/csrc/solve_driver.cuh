@@ -1,4 +1,4 @@
-// Solve driver shared by the dense and banded paths: block substitutions
+// Solve orchestration shared by the dense and banded paths: block substitutions
 // (Eq. 1) and iterative refinement with an FP64-accurate residual.
 #pragma once
 

@@ -149,7 +149,7 @@ __device__ __forceinline__ bool xw_wait(const unsigned long long *p, uint32_t ta
 // of the chain) before every thread waits for its own.  At the last step
 // every thread waits for its entries of X_{t-1} directly.  Every wait is
 // bounded and gives up once the workspace status reports an error.  All
-// CTAs must be co-resident: the driver launches at most the occupancy limit,
+// CTAs must be co-resident: the host code launches at most the occupancy limit,
 // cooperatively.
 // xw: nchunk * nblk * NB * RC entries of XWords<T>::W words, zeroed.
 // Dynamic shared memory: trsvl_smem_bytes<T, NB, RC, NS>().
