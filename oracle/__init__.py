@@ -14,6 +14,8 @@ Each function states the passage of the paper it follows:
   sparse experiment, Table 1, read as banded storage).
 * ``adjoint``      -- transposed solves for gradients (no counterpart in the
   paper; project addition).
+* ``inverse``      -- the product-form inverse of Eq. 4c: A^{-1} = U^{-1} L^{-1}
+  as the product of the elementary transformations of the elimination.
 * ``residual``     -- B - A X by the compensated dot product Dot2.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against hand-worked
@@ -74,6 +76,7 @@ def _bind(lib):
     lib.oracle_adjoint.argtypes = [i64, i64, dp, i64, dp, dp, i64, dp, vp, i64]
     lib.oracle_residual.argtypes = [i64, dp, i64, dp, i64, dp, i64, i64, vp, i64, dp, i64]
     lib.oracle_band_residual.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64, i64, dp, i64]
+    lib.oracle_inverse.argtypes = [i64, dp, i64, dp, i64]
     return lib
 
 
@@ -185,6 +188,16 @@ def band_residual(ab, kl: int, ku: int, x, b, lib=None):
     r = np.zeros((n, nrhs))
     lib.oracle_band_residual(n, kl, ku, _p(ab), ab.shape[1], _p(x2), nrhs, _p(b2), nrhs, nrhs, _p(r), nrhs)
     return r
+
+
+def inverse(lu_, lib=None):
+    """A^{-1} from the packed factors in the product form of Eq. 4c."""
+    lib = lib or load()
+    lu_ = _f64(lu_)
+    n = lu_.shape[0]
+    x = np.zeros((n, n))
+    lib.oracle_inverse(n, _p(lu_), n, _p(x), n)
+    return x
 
 
 def unpack(lu_):

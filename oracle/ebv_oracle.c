@@ -243,3 +243,44 @@ void oracle_band_residual(int64_t n, int64_t kl, int64_t ku, const double *ab,
     }
   }
 }
+
+/*
+ * Product-form inverse (Eq. 4a-c) from the packed Doolittle factors A = LU.
+ * Eq. 4c writes A^{-1} as a product of elementary transformations, one per
+ * elimination step; with the Doolittle reading of the factors they are
+ *   L^{-1} = M_{n-1} ... M_2 M_1,     M_k = I - l_k e_k^T
+ *            (l_k: column k of L below the diagonal -- the Gauss transform of
+ *            step k, Eq. 6a),
+ *   U^{-1} = E_1 E_2 ... E_{n-1} D^{-1},  E_k = I - e_k v_k^T, D = diag(u_kk)
+ *            (v_k: row k of U right of the diagonal divided by the pivot u_kk;
+ *            D^{-1} is the diagonal scaling that the printed Eq. 4a-c omit),
+ *   A^{-1} = U^{-1} L^{-1}.
+ * X starts as the identity and takes the factors from the right: M_1 first,
+ * ..., M_{n-1}; then D^{-1}; then E_{n-1}, ..., E_1.  X (n x n, leading
+ * dimension ldx) is overwritten.  The factors must have non-zero pivots.
+ */
+void oracle_inverse(int64_t n, const double *lu, int64_t lda, double *x, int64_t ldx) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) x[IDX(i, j, ldx)] = (i == j) ? 1.0 : 0.0;
+  for (int64_t k = 0; k < n; ++k) { /* M_k: rows i > k take -l_ik * row k */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (n - k > 128)
+#endif
+    for (int64_t i = k + 1; i < n; ++i) {
+      const double lik = lu[IDX(i, k, lda)];
+      for (int64_t j = 0; j < n; ++j) x[IDX(i, j, ldx)] -= lik * x[IDX(k, j, ldx)];
+    }
+  }
+  for (int64_t k = 0; k < n; ++k) /* D^{-1} */
+    for (int64_t j = 0; j < n; ++j) x[IDX(k, j, ldx)] /= lu[IDX(k, k, lda)];
+  for (int64_t k = n - 1; k >= 0; --k) { /* E_k: row k takes -v_kq * row q, q > k */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (n > 128)
+#endif
+    for (int64_t j = 0; j < n; ++j) {
+      double s = x[IDX(k, j, ldx)];
+      for (int64_t q = k + 1; q < n; ++q) s -= (lu[IDX(k, q, lda)] / lu[IDX(k, k, lda)]) * x[IDX(q, j, ldx)];
+      x[IDX(k, j, ldx)] = s;
+    }
+  }
+}

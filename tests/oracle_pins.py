@@ -14,7 +14,10 @@ what the paper or the mathematics fixes:
   matrix, where partial pivoting takes no row exchange and so must return the
   same factors; LAPACK banded solve; numpy's dense solve for A^T;
 * invariants: A = LU to 1e-13, structural zeros/ones, fill confined to the band,
-  central finite differences for the adjoint, exact-rational residuals.
+  central finite differences for the adjoint, exact-rational residuals;
+* the product-form inverse (Eq. 4c): a hand-worked 3 x 3, adjugates of Leibniz
+  cofactors in exact rationals, closed forms (diagonal, bidiagonal with exact
+  dyadic inverses, block diagonal), A X = X A = I and LAPACK's inverse.
 """
 from __future__ import annotations
 
@@ -386,6 +389,84 @@ def pin_info(lib):
     assert info == 2  # 0.5 - (1/2) * 1 = 0
 
 
+def _adjugate_inverse(a):
+    """A^{-1} = adj(A) / det A from Leibniz cofactors, in exact rationals."""
+    m = _frac_matrix(a)
+    n = len(m)
+    det = _leibniz_det(m)
+    out = [[Fraction(0)] * n for _ in range(n)]
+    for i in range(n):
+        for j in range(n):
+            minor = [row[:i] + row[i + 1:] for r, row in enumerate(m) if r != j]
+            c = _leibniz_det(minor) if n > 1 else Fraction(1)
+            out[i][j] = (c if (i + j) % 2 == 0 else -c) / det
+    return out
+
+
+def pin_golden_inverse(lib):
+    g = read_golden("inverse_3x3.txt")
+    f, info = oracle.lu(g["A"], lib=lib)
+    assert info == 0
+    x = oracle.inverse(f, lib=lib)
+    assert np.array_equal(x, g["Ainv"]), x
+    lo, up = oracle.unpack(f)
+    assert np.array_equal(oracle.inverse(lo, lib=lib), g["Linv"])
+    assert np.array_equal(oracle.inverse(up, lib=lib), g["Uinv"])
+
+
+def pin_inverse_leibniz(lib):
+    for n in range(1, 7):
+        for seed in range(2):
+            a = synthetic.dense_dd(n, 0.9, 5000 + 10 * n + seed) + np.triu(np.full((n, n), 0.125), 1)
+            f, info = oracle.lu(a, lib=lib)
+            assert info == 0
+            x = oracle.inverse(f, lib=lib)
+            ex = _adjugate_inverse(a)
+            scale = max(abs(v) for row in ex for v in row)
+            err = max(abs(Fraction(float(x[i, j])) - ex[i][j]) for i in range(n) for j in range(n))
+            assert float(err) <= 1e-14 * float(scale), (n, seed, float(err))
+
+
+def pin_inverse_closed_forms(lib):
+    # diagonal: 1 / a_ii
+    d = np.array([2.0, -4.0, 0.5, 8.0, 1.0, -0.25])
+    f, _ = oracle.lu(np.diag(d), lib=lib)
+    assert np.array_equal(oracle.inverse(f, lib=lib), np.diag(1.0 / d))
+    n = 14
+    i, j = np.indices((n, n))
+    # unit lower bidiagonal, -1/2 below the diagonal: (A^{-1})_ij = 2^{-(i-j)} for i >= j
+    lo = np.eye(n) - 0.5 * np.eye(n, k=-1)
+    f, _ = oracle.lu(lo, lib=lib)
+    assert np.array_equal(oracle.inverse(f, lib=lib), np.where(i >= j, 0.5 ** (i - j), 0.0))
+    # upper bidiagonal 2I + N: A^{-1} = (1/2) sum_k (-N/2)^k, (A^{-1})_ij = (1/2)(-1/2)^{j-i} for j >= i
+    up = 2.0 * np.eye(n) + np.eye(n, k=1)
+    f, _ = oracle.lu(up, lib=lib)
+    assert np.array_equal(oracle.inverse(f, lib=lib), np.where(j >= i, 0.5 * (-0.5) ** (j - i), 0.0))
+    # block diagonal: the inverses of the blocks
+    a1 = synthetic.dense_dd(5, 0.7, 21)
+    a2 = synthetic.dense_dd(4, 0.7, 22)
+    blk = np.zeros((9, 9))
+    blk[:5, :5] = a1
+    blk[5:, 5:] = a2
+    x = oracle.inverse(oracle.lu(blk, lib=lib)[0], lib=lib)
+    assert np.array_equal(x[:5, :5], oracle.inverse(oracle.lu(a1, lib=lib)[0], lib=lib))
+    assert np.array_equal(x[5:, 5:], oracle.inverse(oracle.lu(a2, lib=lib)[0], lib=lib))
+    assert not np.any(x[:5, 5:]) and not np.any(x[5:, :5])
+    # 2 x 2: [[a, b], [c, d]]^{-1} = [[d, -b], [-c, a]] / (ad - bc)
+    a = np.array([[4.0, 3.0], [6.0, 3.0]])
+    x = oracle.inverse(oracle.lu(a, lib=lib)[0], lib=lib)
+    np.testing.assert_allclose(x, np.array([[3.0, -3.0], [-6.0, 4.0]]) / -6.0, rtol=2e-16, atol=0)
+
+
+def pin_inverse_invariants(lib):
+    for n, w in ((33, 0.5), (100, 0.9)):
+        a = synthetic.dense_dd(n, w, 6000 + n)
+        x = oracle.inverse(oracle.lu(a, lib=lib)[0], lib=lib)
+        e = np.eye(n)
+        assert np.abs(a @ x - e).max() <= 1e-14 and np.abs(x @ a - e).max() <= 1e-14
+        np.testing.assert_allclose(x, np.linalg.inv(a), rtol=0, atol=1e-14)
+
+
 ALL_PINS = [
     pin_golden_factor_and_solve,
     pin_golden_adjoint,
@@ -402,4 +483,8 @@ ALL_PINS = [
     pin_residual,
     pin_partial_factorisation,
     pin_info,
+    pin_golden_inverse,
+    pin_inverse_leibniz,
+    pin_inverse_closed_forms,
+    pin_inverse_invariants,
 ]

@@ -41,6 +41,15 @@ MUTANTS = {
                                   "s += grad_b[IDX(j, c, ldx)] * x[IDX(i, c, ldx)];"),
     "residual_drops_product_error": ("comp += pe + se;\n      }\n      r[IDX(t, c, ldr)]",
                                      "comp += se;\n      }\n      r[IDX(t, c, ldr)]"),
+    "inverse_gauss_sign": ("for (int64_t j = 0; j < n; ++j) x[IDX(i, j, ldx)] -= lik * x[IDX(k, j, ldx)];",
+                           "for (int64_t j = 0; j < n; ++j) x[IDX(i, j, ldx)] += lik * x[IDX(k, j, ldx)];"),
+    "inverse_scales_by_pivot": ("x[IDX(k, j, ldx)] /= lu[IDX(k, k, lda)];", "x[IDX(k, j, ldx)] *= lu[IDX(k, k, lda)];"),
+    "inverse_upper_transposed": ("s -= (lu[IDX(k, q, lda)] / lu[IDX(k, k, lda)]) * x[IDX(q, j, ldx)];",
+                                 "s -= (lu[IDX(q, k, lda)] / lu[IDX(k, k, lda)]) * x[IDX(q, j, ldx)];"),
+    "inverse_short_upper_sweep": ("for (int64_t q = k + 1; q < n; ++q) s -=",
+                                  "for (int64_t q = k + 1; q < n - 1; ++q) s -="),
+    "inverse_wrong_gauss_order": ("for (int64_t k = 0; k < n; ++k) { /* M_k",
+                                  "for (int64_t k = n - 1; k >= 0; --k) { /* M_k"),
     "info_off_by_one": ("if (info == 0 && (p == 0.0 || !isfinite(p))) info = k + 1;\n#ifdef _OPENMP\n#pragma omp parallel for schedule(static) if (n - k > 128)",
                         "if (info == 0 && (p == 0.0 || !isfinite(p))) info = k;\n#ifdef _OPENMP\n#pragma omp parallel for schedule(static) if (n - k > 128)"),
 }
