@@ -662,7 +662,51 @@ def run_configs(args):
                 "backward_gbs": bwd_bytes / (ms_b / 1e3) / 1e9, "backward_hbm_frac": bwd_bytes / (ms_b / 1e3) / 1e9 / hbm,
                 "grad_relerr_vs_oracle_sampled": err, "info_max": int(bt.info.abs().max())})
     print(json.dumps(out[-1]), flush=True)
+    out.append(run_inverse_config(args))
     return out
+
+
+# FP64 SIMT peak derived from the unit counts and the clock: 152 SMs x 2 DFMA
+# per clock x 2 flops x 2.07 GHz (an FMA-chain probe reads 1.01 and under-reads:
+# the inverse's products run at 1.21).
+DFMA_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def run_inverse_config(args, n=8192):
+    """Explicit FP64 inverse from FP64 factors (product form, Eq. 4c), n = 8192.
+    Checked through properties that hold at any size: sampled rows of A X - I
+    and X A - I (the oracle inverse itself is O(n^3) on the host)."""
+    import torch
+
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    dev = torch.device("cuda")
+    a = synthetic.dense_dd(n, 0.9, synthetic.seed_for(2))
+    A = torch.from_numpy(a).to(dev)
+    lu = A.clone()
+    info = ebv.ebv_factor(lu, "fp64")
+    x = torch.empty_like(A)
+    ws = torch.empty(ebv.lib().ebv_inverse_workspace_size(n, ebv.FP64), dtype=torch.uint8, device=dev)
+    ms = _dev_ms(lambda: ebv.ebv_inverse(lu, x, "fp64", ws=ws), 3, 1, graph=False)
+    launches0 = ebv.launch_count()
+    ebv.ebv_inverse(lu, x, "fp64", ws=ws)
+    torch.cuda.synchronize()
+    launches = ebv.launch_count() - launches0
+    rows = synthetic.pick_indices(13, 16, [n])[:, 0]
+    xs = x.cpu().numpy()
+    eye = np.eye(n)[rows]
+    r_ax = float(np.abs(a[rows] @ xs - eye).max())
+    r_xa = float(np.abs(xs[rows] @ a - eye).max())
+    flops = 4.0 * n ** 3 / 3.0
+    gf = flops / (ms / 1e3) / 1e9
+    line = {"config": f"explicit inverse FP64 n={n} from FP64 factors (product form)", "ms": ms,
+            "gflops_fp64": gf, "fp64_alu_frac": gf / 1e3 / DFMA_TFLOPS,
+            "fp64_peak_tflops": DFMA_TFLOPS,
+            "fp64_peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz", "launches": launches,
+            "max_abs_AX_minus_I_sampled_rows": r_ax, "max_abs_XA_minus_I_sampled_rows": r_xa,
+            "info": int(info.item())}
+    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------------------------------------
@@ -707,10 +751,14 @@ def main():
     p.add_argument("--ref-kstop", type=int, default=96)
     p.add_argument("--no-graph", dest="graph", action="store_false")
     p.add_argument("--update-only", default=None, help="M,N,K: time the tensor-core update alone and exit")
-    p.add_argument("--configs", action="store_true", help="time the other workloads (one JSON line each) and exit")
+    p.add_argument("--configs", nargs="?", const="all", default=None,
+                   help="time the other workloads (one JSON line each) and exit; --configs inverse: that one alone")
     args = p.parse_args()
     if args.update_only:
         print(json.dumps(run_update_only(args)), flush=True)
+        return
+    if args.configs == "inverse":
+        run_inverse_config(args)
         return
     if args.configs:
         run_configs(args)

@@ -214,6 +214,35 @@ EBV_API ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, in
                                 float *ms_host, ebv_stream_t stream);
 
 /*
+ * ebv_inverse -- the explicit inverse from the packed factors, in the product
+ * form of Eq. 4c: A^{-1} = U^{-1} L^{-1}, where L^{-1} is the product of the
+ * elimination's Gauss transforms and U^{-1} that of the row transforms of U
+ * and the pivot scaling.  For many right-hand sides that arrive one by one
+ * (X B is one matrix product), not for single solves (ebv_solve is cheaper
+ * and more accurate).
+ *   desc  dense storage only (EBV_BAND, EBV_BAND_SYM: EBV_ERR_UNSUPPORTED);
+ *         n and the factors' leading dimension ld.
+ *   prec  EBV_FP64 (lu and x binary64) or EBV_FP32 (binary32: the factors of
+ *         ebv_factor with EBV_FP32, or the binary32 lowp factors of a
+ *         mixed-precision factorisation); others give EBV_ERR_UNSUPPORTED.
+ *   lu    device, the packed factors (L strictly below the diagonal, unit
+ *         diagonal implied; U on and above), row-major; read only.  They must
+ *         come from a factorisation whose info was 0: zero pivots are not
+ *         checked here and give non-finite entries in x.
+ *   x     device output, n x n, row-major, leading dimension ldx >= n; it
+ *         must not overlap lu (EBV_ERR_ARG) and serves as scratch until the
+ *         last launch writes A^{-1}.
+ *   ws    device workspace, 256-byte aligned, of at least
+ *         ebv_inverse_workspace_size(n, prec) bytes (the packed inverses of the
+ *         two triangles: n x n elements); EBV_ERR_WORKSPACE otherwise.
+ * Work: 4n^3/3 flops in 2 + 2*ceil(log2(n/64)) launches on `stream`; no host
+ * synchronisation, capturable.  n <= 2^21.
+ */
+EBV_API size_t ebv_inverse_workspace_size(int64_t n, ebv_prec_t prec);
+EBV_API ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, void *x, int64_t ldx,
+                                 void *ws, size_t ws_bytes, ebv_stream_t stream);
+
+/*
  * ebv_solve_adjoint -- gradients of X = A^{-1} B for a batch of equal-size
  * FP64 systems (project addition; the paper has no gradients).  From the
  * stored factors (A = LU, so A^T = U^T L^T):
@@ -348,10 +377,11 @@ EBV_API ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda,
  * precision trailing update, 2 diagonal blocks, 3 block substitutions,
  * 4 refinement residual, 5 batched kernel, 6 adjoint, 7 other, 8 U12
  * tile products and blocked TRSMs, 9 L21 tile products, 10 two-leaf middle
- * step (U12 and the trailing update of a 128-column node in one launch).
- * ebv_debug_profile_read fills, for the 11 classes, the summed device time in
+ * step (U12 and the trailing update of a 128-column node in one launch),
+ * 11 explicit inverse (ebv_inverse).
+ * ebv_debug_profile_read fills, for the 12 classes, the summed device time in
  * ms, the summed algorithmic work (flops) and the launch count of the launches
- * recorded since the previous read (host arrays of 11; synchronises on the
+ * recorded since the previous read (host arrays of 12; synchronises on the
  * recorded events).  Profiling adds an event pair per launch; switch it off
  * for timed runs.
  */

@@ -81,6 +81,8 @@ _SIGNATURES = [
     ("ebv_factor_solve_batched", _I32, [_I64, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _SZ, _VP]),
     ("ebv_batch_autotune_scratch", _SZ, [_I32, _I32, _I32]),
     ("ebv_batch_autotune", _I32, [_VP, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP]),
+    ("ebv_inverse_workspace_size", _SZ, [_I64, _I32]),
+    ("ebv_inverse", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _I64, _VP, _SZ, _VP]),
     ("ebv_solve_adjoint", _I32, [_I64, _I64, _I64, _VP, _I64, _I64, _VP, _VP, _VP, _VP, _VP]),
     ("ebv_debug_set_lowp_gemm", None, [_I32]),
     ("ebv_debug_residual", _I32, [_I64, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
@@ -93,7 +95,7 @@ _SIGNATURES = [
     ("ebv_debug_profile_read", _I32, [_VP, _VP, _VP]),
 ]
 PROFILE_CLASSES = ["lowp_gemm", "simt_gemm", "panel", "trsv", "residual", "batched", "adjoint", "other", "trsm",
-                   "l21", "leaf_update"]
+                   "l21", "leaf_update", "inverse"]
 
 
 def launch_count() -> int:
@@ -224,6 +226,26 @@ def ebv_solve(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tens
     return b
 
 
+def ebv_inverse(lu: torch.Tensor, x: torch.Tensor | None = None, prec="fp64", ws: torch.Tensor | None = None,
+                ld=None) -> torch.Tensor:
+    """A^{-1} (n x n) from packed dense factors, product form of Eq. 4c.
+    ``prec``: fp64 or fp32 (the binary32 factors of a mixed factorisation too)."""
+    p = _prec(prec)
+    _need_cuda(lu, x, ws)
+    n = lu.shape[0]
+    if ld is None:
+        ld = lu.stride(0)
+    if x is None:
+        x = torch.empty((n, n), dtype=lu.dtype, device=lu.device)
+    if ws is None:
+        nbytes = int(lib().ebv_inverse_workspace_size(n, p))
+        ws = torch.empty(max(256, nbytes), dtype=torch.uint8, device=lu.device)
+    d = _desc(n, ld)
+    _check(lib().ebv_inverse(ctypes.byref(d), p, _ptr(lu), _ptr(x), x.stride(0), _ptr(ws), ws.numel(),
+                             _stream(lu.device)), "ebv_inverse")
+    return x
+
+
 def gesv_host_workspace(n, nrhs, prec="bf16", device="cuda") -> torch.Tensor:
     d = _desc(n, n)
     size = lib().ebv_gesv_host_workspace_size(ctypes.byref(d), _prec(prec), nrhs)
@@ -341,6 +363,13 @@ def solve(f: Factors, b: torch.Tensor, refine: tuple | None = None, report: torc
         x = x.view(-1, 1)
     ebv_solve(f.lu, x, f.prec, a_orig=f.a, refine=refine, report=report, kl=f.kl, ku=f.ku, storage=f.storage)
     return x.view(b.shape) if b.dim() == 1 else x
+
+
+def inverse(f: Factors) -> torch.Tensor:
+    """Explicit A^{-1} from dense factors (FP64 factors: FP64; FP32 or mixed: FP32)."""
+    if f.storage != DENSE:
+        raise ValueError("the explicit inverse takes dense factors")
+    return ebv_inverse(f.lu, prec=FP64 if f.prec == FP64 else FP32)
 
 
 def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64", sym: bool = False) -> Factors:

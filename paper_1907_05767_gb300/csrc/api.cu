@@ -11,6 +11,9 @@ using namespace ebv;
 namespace {
 
 constexpr int64_t kMaxN = int64_t(1) << 30;
+// Largest order of the explicit inverse (its level launches put two nodes per
+// grid.z slot, its product one CTA per tile in grid.x).
+constexpr int64_t kMaxInverseN = int64_t(1) << 21;
 
 // Runs the library's bounded wait on flag (which the caller leaves at 0, so
 // nothing ever sets it): every thread of the CTA returns after `polls` polls
@@ -115,6 +118,28 @@ ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, 
   if (desc->storage != EBV_DENSE)
     return band_solve(desc, prec, lu, a_orig, b, nrhs, ldb, refine, report_dev, ws, ws_bytes, s);
   return dense_solve(desc, prec, lu, a_orig, b, nrhs, ldb, refine, report_dev, ws, ws_bytes, s);
+}
+
+size_t ebv_inverse_workspace_size(int64_t n, ebv_prec_t prec) {
+  if (n < 0 || n > kMaxInverseN || (prec != EBV_FP64 && prec != EBV_FP32)) return 0;
+  return inverse_ws(n, prec);
+}
+
+ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, void *x, int64_t ldx, void *ws,
+                         size_t ws_bytes, ebv_stream_t stream) {
+  EBV_TRY(check_desc(desc, prec));
+  if (desc->storage != EBV_DENSE || (prec != EBV_FP64 && prec != EBV_FP32)) return EBV_ERR_UNSUPPORTED;
+  const int64_t n = desc->n;
+  if (n > kMaxInverseN) return EBV_ERR_UNSUPPORTED;
+  if (ldx < std::max<int64_t>(1, n)) return EBV_ERR_ARG;
+  if (n == 0) return EBV_OK;
+  const size_t es = elem_size(prec);
+  if (!lu || !x || !aligned(lu, es) || !aligned(x, es)) return EBV_ERR_ARG;
+  const uintptr_t l0 = (uintptr_t)lu, l1 = l0 + ((n - 1) * desc->ld + n) * es;
+  const uintptr_t x0 = (uintptr_t)x, x1 = x0 + ((n - 1) * ldx + n) * es;
+  if (l0 < x1 && x0 < l1) return EBV_ERR_ARG;  // X is written while the factors are still read
+  if (!ws || !aligned(ws, 256) || ws_bytes < inverse_ws(n, prec)) return EBV_ERR_WORKSPACE;
+  return inverse(n, prec, lu, desc->ld, x, ldx, ws, (cudaStream_t)stream);
 }
 
 // Testing hook: 0 = automatic, 1 = SIMT only, 2 = tensor cores where possible.

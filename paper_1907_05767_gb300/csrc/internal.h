@@ -31,6 +31,11 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
                         int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
                         size_t ws_bytes, cudaStream_t s);
 
+// Product-form inverse (Eq. 4c) from packed dense factors (inverse.cu).
+size_t inverse_ws(int64_t n, ebv_prec_t prec);
+ebv_status_t inverse(int64_t n, ebv_prec_t prec, const void *lu, int64_t ldl, void *x, int64_t ldx, void *ws,
+                     cudaStream_t s);
+
 struct DevStatus;
 
 // Mixed-precision trailing update C(m0.., n0..) -= scale[2] * lb(m0.., k0..) * ut(n0.., k0..)^T

@@ -27,7 +27,8 @@ enum Class : int {
   kTrsm = 8,       // U12 = L11^{-1} A12: tile products and blocked TRSMs
   kL21 = 9,        // L21 = A21 U11^{-1} tile products
   kLeafUpdate = 10,  // two-leaf middle step (U12 and the A22 update in one launch)
-  kNumClasses = 11
+  kInverse = 11,   // product-form inverse (leaf inverses, level products, W Z)
+  kNumClasses = 12
 };
 
 bool enabled();

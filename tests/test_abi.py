@@ -104,3 +104,27 @@ def test_workspace_sizes(lib):
     assert sz(1024, ebv.FP64, 32) > sz(1024, ebv.FP64, 1)
     d = _d(-3, 1)
     assert lib.ebv_workspace_size(ctypes.byref(d), ebv.FP64, 0) == 0
+
+
+def test_inverse_argument_errors(lib):
+    n = 100
+    need = lib.ebv_inverse_workspace_size(n, ebv.FP64)
+    assert need >= n * n * 8 and need % 256 == 0
+    assert lib.ebv_inverse_workspace_size(n, ebv.FP32) >= n * n * 4
+    assert lib.ebv_inverse_workspace_size(n, ebv.MIXED_BF16) == 0
+    assert lib.ebv_inverse_workspace_size(-1, ebv.FP64) == 0
+    lu, x, ws = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x10000000), ctypes.c_void_p(0x40000000)
+    d = _d(n, n)
+    call = lambda desc, prec, l, xx, ldx, w, wb: lib.ebv_inverse(  # noqa: E731
+        ctypes.byref(desc) if desc is not None else None, prec, l, xx, ldx, w, wb, None)
+    assert call(None, ebv.FP64, lu, x, n, ws, need) == 1                      # null descriptor
+    assert call(_d(n, n, 2, 2, ebv.BAND), ebv.FP64, lu, x, n, ws, need) == 7  # band storage
+    assert call(d, ebv.MIXED_BF16, lu, x, n, ws, need) == 7                   # mixed: pass the FP32 factors
+    assert call(d, ebv.FP64, lu, x, n - 1, ws, need) == 1                     # ldx < n
+    assert call(d, ebv.FP64, None, x, n, ws, need) == 1                       # null factors
+    assert call(d, ebv.FP64, lu, ctypes.c_void_p(0x100004), n, ws, need) == 1  # misaligned x
+    assert call(d, ebv.FP64, lu, ctypes.c_void_p(0x100000 + 8 * n * 50), n, ws, need) == 1  # x overlaps lu
+    assert call(d, ebv.FP64, lu, x, n, None, need) == 8                       # no workspace
+    assert call(d, ebv.FP64, lu, x, n, ws, need - 256) == 8                   # workspace too small
+    assert call(d, ebv.FP64, lu, x, n, ctypes.c_void_p(0x40000010), need) == 8  # misaligned workspace
+    assert call(_d(0, 1), ebv.FP64, None, None, 1, None, 0) == 0              # n = 0: nothing to do
