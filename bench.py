@@ -672,8 +672,9 @@ def run_configs(args):
 DFMA_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def run_inverse_config(args, n=8192):
-    """Explicit FP64 inverse from FP64 factors (product form, Eq. 4c), n = 8192.
+def run_inverse_config(args):
+    """Explicit FP64 inverse from FP64 factors (product form, Eq. 4c), n = 8192
+    (--inverse-n).
     Checked through properties that hold at any size: sampled rows of A X - I
     and X A - I (the oracle inverse itself is O(n^3) on the host)."""
     import torch
@@ -681,6 +682,7 @@ def run_inverse_config(args, n=8192):
     import paper_1907_05767_gb300 as ebv
     import synthetic
     dev = torch.device("cuda")
+    n = args.inverse_n
     a = synthetic.dense_dd(n, 0.9, synthetic.seed_for(2))
     A = torch.from_numpy(a).to(dev)
     lu = A.clone()
@@ -753,6 +755,7 @@ def main():
     p.add_argument("--update-only", default=None, help="M,N,K: time the tensor-core update alone and exit")
     p.add_argument("--configs", nargs="?", const="all", default=None,
                    help="time the other workloads (one JSON line each) and exit; --configs inverse: that one alone")
+    p.add_argument("--inverse-n", type=int, default=8192, help="order of the explicit-inverse workload")
     args = p.parse_args()
     if args.update_only:
         print(json.dumps(run_update_only(args)), flush=True)
