@@ -663,7 +663,76 @@ def run_configs(args):
                 "grad_relerr_vs_oracle_sampled": err, "info_max": int(bt.info.abs().max())})
     print(json.dumps(out[-1]), flush=True)
     out.append(run_inverse_config(args))
+    out.append(run_profile_config(args))
     return out
+
+
+def profile_work(ab, kl, ku):
+    """Flops of a no-pivot LU confined to the profile: sum over steps k of
+    2 r_k c_k, r_k (c_k) = the rows below (columns right of) k whose first
+    non-zero left of (above) the diagonal is at or before k."""
+    n = ab.shape[0]
+    i = np.arange(n)
+    low = ab[:, :kl] != 0.0
+    f = np.where(low.any(axis=1), i - kl + np.argmax(low, axis=1), i)
+    g = i.copy()
+    for d in range(ku, 0, -1):  # column j, row j - d: slot kl + d of row j - d
+        j = np.arange(d, n)
+        hit = ab[j - d, kl + d] != 0.0
+        g[j[hit]] = np.minimum(g[j[hit]], j[hit] - d)
+    r = np.zeros(n + 1)
+    c = np.zeros(n + 1)
+    np.add.at(r, f, 1.0)
+    np.add.at(r, i, -1.0)
+    np.add.at(c, g, 1.0)
+    np.add.at(c, i, -1.0)
+    r, c = np.cumsum(r)[:n], np.cumsum(c)[:n]
+    return float(2.0 * (r * c).sum()), float(r.sum()), float(c.sum())
+
+
+def run_profile_config(args):
+    """Variable band: the 5-point Laplacian on a disc of radius 289 (n = 262341,
+    stored in its widest band kl = ku = 578), FP64, 8 RHS; factorisation with
+    and without the block-envelope skipping."""
+    import torch
+
+    import oracle
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    dev = torch.device("cuda")
+    ab, kl, ku = synthetic.laplacian_disc_band(289)
+    n, nrhs = ab.shape[0], 8
+    x_true = synthetic.planted_x(n, nrhs, synthetic.seed_for(1, 7))
+    b = synthetic.band_rhs(ab, kl, ku, x_true)
+    AB, B = torch.from_numpy(ab).to(dev), torch.from_numpy(b).to(dev)
+    lu, x = torch.empty_like(AB), torch.empty_like(B)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ebv.workspace(n, "fp64", nrhs, dev, kl=kl, ku=ku, storage=ebv.BAND)
+
+    def step():
+        lu.copy_(AB)
+        x.copy_(B)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
+        ebv.ebv_solve(lu, x, "fp64", ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
+
+    ebv.lib().ebv_debug_set_band_envelope(0)
+    ms_full = _dev_ms(step, 3, 1)
+    ebv.lib().ebv_debug_set_band_envelope(1)
+    ms = _dev_ms(step, 3, 1)
+    xs = x.cpu().numpy()
+    rows = synthetic.pick_indices(12, 512, [n])[:, 0]
+    r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
+    work, rsum, csum = profile_work(ab, kl, ku)
+    flops = work + 2.0 * (rsum + csum) * nrhs
+    line = {"config": f"variable band FP64: Laplacian on a disc of radius 289 (n={n}, widest band kl=ku={kl}), "
+                      f"{nrhs} RHS", "ms": ms, "ms_without_envelope": ms_full, "speedup_envelope": ms_full / ms,
+            "profile_gflop": flops / 1e9, "band_gflop": (2.0 * n * kl * ku + 2.0 * n * (kl + ku) * nrhs) / 1e9,
+            "gflops_profile": flops / (ms / 1e3) / 1e9,
+            "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
+            "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
+            "info": int(info.item())}
+    print(json.dumps(line), flush=True)
+    return line
 
 
 # FP64 SIMT peak derived from the unit counts and the clock: 152 SMs x 2 DFMA
@@ -754,7 +823,7 @@ def main():
     p.add_argument("--no-graph", dest="graph", action="store_false")
     p.add_argument("--update-only", default=None, help="M,N,K: time the tensor-core update alone and exit")
     p.add_argument("--configs", nargs="?", const="all", default=None,
-                   help="time the other workloads (one JSON line each) and exit; --configs inverse: that one alone")
+                   help="time the other workloads (one JSON line each) and exit; --configs inverse / profile: one alone")
     p.add_argument("--inverse-n", type=int, default=8192, help="order of the explicit-inverse workload")
     args = p.parse_args()
     if args.update_only:
@@ -762,6 +831,9 @@ def main():
         return
     if args.configs == "inverse":
         run_inverse_config(args)
+        return
+    if args.configs == "profile":
+        run_profile_config(args)
         return
     if args.configs:
         run_configs(args)

@@ -140,7 +140,10 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
  * Band storage (EBV_BAND, EBV_BAND_SYM) supports EBV_FP64 and EBV_FP32; fill-in stays inside
- * the band because no rows are exchanged.
+ * the band because no rows are exchanged.  A band whose width varies row by row
+ * (a profile, or skyline, matrix stored in its widest band) costs the work of
+ * its profile: the factorisation first finds each 64-block's envelope and
+ * skips the tiles outside it (see ebv_debug_set_band_envelope).
  */
 EBV_API ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *lowp,
                         int32_t *info_dev, void *ws, size_t ws_bytes, ebv_stream_t stream);
@@ -331,6 +334,17 @@ EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, c
  * only.  Process-wide; not for concurrent use with running factorisations.
  */
 EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
+
+/*
+ * Testing hook: the banded factorisation (EBV_BAND, EBV_BAND_SYM) first finds
+ * the block envelope of A -- per 64-block, the first non-zero left of the
+ * diagonal over the block's rows and above it over its columns -- and skips
+ * the L21, U12 and trailing-update tiles that lie outside it (no row exchanges,
+ * so the factors never leave the envelope; a band whose width varies row by
+ * row costs the work of its profile).  enable = 0 switches the skipping off;
+ * the factors are the same bit for bit.  Process-wide, default on.
+ */
+EBV_API void ebv_debug_set_band_envelope(int32_t enable);
 
 /*
  * Testing hook (project addition; the residual of the refinement loop):

@@ -85,6 +85,7 @@ _SIGNATURES = [
     ("ebv_inverse", _I32, [ctypes.POINTER(Desc), _I32, _VP, _VP, _I64, _VP, _SZ, _VP]),
     ("ebv_solve_adjoint", _I32, [_I64, _I64, _I64, _VP, _I64, _I64, _VP, _VP, _VP, _VP, _VP]),
     ("ebv_debug_set_lowp_gemm", None, [_I32]),
+    ("ebv_debug_set_band_envelope", None, [_I32]),
     ("ebv_debug_residual", _I32, [_I64, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     ("ebv_debug_lowp_update", _I32, [_I32, _I32, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _I64, _I64, _I64, _I64, _I64,
                                      _VP, _VP]),

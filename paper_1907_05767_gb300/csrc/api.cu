@@ -142,6 +142,9 @@ ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu
   return inverse(n, prec, lu, desc->ld, x, ldx, ws, (cudaStream_t)stream);
 }
 
+// Testing hook: 0 = the banded factorisation ignores the block envelope.
+void ebv_debug_set_band_envelope(int32_t enable) { set_band_envelope(enable != 0); }
+
 // Testing hook: 0 = automatic, 1 = SIMT only, 2 = tensor cores where possible.
 void ebv_debug_set_lowp_gemm(int32_t mode) { set_lowp_gemm_mode(mode); }
 

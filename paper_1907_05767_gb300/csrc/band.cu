@@ -8,6 +8,12 @@
 // <= ku columns to the right, and one dense (kl x ku x 64) window update.  All
 // kernels read through a band view (out-of-band entries read as 0, never
 // written).
+//
+// Variable band (the profile, or skyline, of the matrix): a first kernel finds
+// each 64-block's envelope -- the first non-zero left of the diagonal over the
+// block's rows, above it over its columns -- and the L21, U12 and update CTAs
+// whose block lies outside it for the current panel return at once, so a band
+// whose width varies costs the work of its envelope, not of its widest row.
 #include <algorithm>
 
 #include "internal.h"
@@ -28,12 +34,59 @@ struct BandGemm<float> {
   static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
 };
 
+// Block envelope (see Envelope): one warp per index i scans row i left of the
+// diagonal from its band edge for the first non-zero and column i above the
+// diagonal from its band edge likewise, and lowers lo[i/64] / up[i/64] to
+// what it found (i itself when the part is empty).  lo and up start above any
+// index.  The column scan reads one element per row (stride ld) but stops at
+// the first non-zero, which for a band matrix is near the band edge.
 template <typename T>
-ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, bool sym, cudaStream_t s) {
+__global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, int32_t *lo, int32_t *up) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
+  if (i >= n) return;
+  int64_t first = i;
+  for (int64_t j0 = max64(0, i - A.kl); j0 < i; j0 += 32) {  // row i, columns j0 .. i-1
+    const int64_t j = j0 + lane;
+    const unsigned nz = __ballot_sync(0xffffffffu, j < i && A.get(i, j) != T(0));
+    if (nz) {
+      first = j0 + __ffs(nz) - 1;
+      break;
+    }
+  }
+  if (lane == 0) atomicMin(&lo[i / 64], (int32_t)first);
+  first = i;
+  for (int64_t r0 = max64(0, i - A.ku); r0 < i; r0 += 32) {  // column i, rows r0 .. i-1
+    const int64_t r = r0 + lane;
+    const unsigned nz = __ballot_sync(0xffffffffu, r < i && A.get(r, i) != T(0));
+    if (nz) {
+      first = r0 + __ffs(nz) - 1;
+      break;
+    }
+  }
+  if (lane == 0) atomicMin(&up[i / 64], (int32_t)first);
+}
+
+bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
+
+template <typename T>
+ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym,
+                           cudaStream_t s) {
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
   using G = BandGemm<T>;
   EBV_TRY((prepare_leaf_kernels<T, float>()));
   constexpr size_t smem = pair_smem_bytes<T, kNB>();
+  Envelope env;
+  if (g_band_envelope) {
+    const int64_t nblk = ceil_div(n, kNB);
+    int32_t *env_up = env_lo + nblk;
+    EBV_CU(cudaMemsetAsync(env_lo, 0x7f, 2 * nblk * sizeof(int32_t), s));  // 0x7f7f7f7f > any index
+    prof::Scope ps(s, prof::kOther, 0.0);
+    k_band_envelope<T><<<ceil_div(n, 8), 256, 0, s>>>(A, n, env_lo, env_up);
+    EBV_TRY(launch_ok());
+    env.lo = env_lo;
+    env.up = env_up;
+  }
   for (int64_t c0 = 0; c0 < n; c0 += kNB) {
     const int w = (int)std::min<int64_t>(kNB, n - c0);
     {
@@ -48,9 +101,10 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, bool 
     if (re > rb) {
       prof::Scope ps(s, prof::kL21, 2.0 * (re - rb) * w * w);
       if constexpr (sizeof(T) == 8)
-        k_trsm_ru_strip<T, float, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
+        k_trsm_ru_strip<T, float, kNB, 16><<<ceil_div(re - rb, 16), 256, smem, s>>>(A, c0, w, rb, re, inv, none,
+                                                                                      env);
       else
-        k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none);
+        k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none, env);
       EBV_TRY(launch_ok());
     }
     if (ce > cb && sym) {  // U12 = D11 L21^T
@@ -62,9 +116,9 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, bool 
       if constexpr (sizeof(T) == 8)
         k_trsm_ll_multi<T, float, kNB, kTrsmMaxBlocks, 16>
             <<<ceil_div(ce - cb, 16), 256, trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>(), s>>>(A, c0, w, cb, ce,
-                                                                                               inv, none);
+                                                                                               inv, none, env);
       else
-        k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, kNB), 256, smem, s>>>(A, c0, w, cb, ce, inv, none);
+        k_trsm_ll<T, float, kNB><<<ceil_div(ce - cb, kNB), 256, smem, s>>>(A, c0, w, cb, ce, inv, none, env);
       EBV_TRY(launch_ok());
     }
     if (re > rb && ce > cb) {
@@ -72,7 +126,7 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, bool 
       dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
       // symmetric: L21 D11 L21^T, only its block-lower part (the diagonal 64-blocks whole)
       k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
-          <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0);
+          <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0, env);
       EBV_TRY(launch_ok());
     }
   }
@@ -116,11 +170,14 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-// Workspace of the banded factorisation: the status block and the inverses
-// of the current leaf's two triangular factors (used right after they are made).
-size_t band_factor_ws(int64_t, int64_t, int64_t, ebv_prec_t prec) {
-  return kStatusBytes + align256((size_t)2 * kNB * kNB * (prec == EBV_FP64 ? 8 : 4));
+// Workspace of the banded factorisation: the status block, the inverses of
+// the current leaf's two triangular factors (used right after they are made)
+// and the block envelope (two int32 per 64-block).
+static size_t band_inv_bytes(ebv_prec_t prec) { return align256((size_t)2 * kNB * kNB * (prec == EBV_FP64 ? 8 : 4)); }
+size_t band_factor_ws(int64_t n, int64_t, int64_t, ebv_prec_t prec) {
+  return kStatusBytes + band_inv_bytes(prec) + align256((size_t)2 * ceil_div(n, kNB) * sizeof(int32_t));
 }
+void set_band_envelope(bool on) { g_band_envelope = on; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
 }
@@ -132,11 +189,13 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t 
   if (d->n == 0) return EBV_OK;
   if (!ws || ws_bytes < band_factor_ws(d->n, d->kl, d->ku, prec)) return EBV_ERR_WORKSPACE;
   char *inv = (char *)ws + kStatusBytes;
+  int32_t *env = (int32_t *)(inv + band_inv_bytes(prec));
   const bool sym = d->storage == EBV_BAND_SYM;
   if (prec == EBV_FP64)
-    return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, (double *)inv, sym, s);
+    return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, (double *)inv, env, sym,
+                                 s);
   if (prec == EBV_FP32)
-    return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, sym, s);
+    return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, env, sym, s);
   return EBV_ERR_UNSUPPORTED;
 }
 

@@ -33,6 +33,23 @@ struct MatView {
 
 constexpr int64_t kDenseBand = int64_t(1) << 60;
 
+// Block envelope of a banded matrix, per 64-block of rows / columns (absolute
+// indices): lo[b] = the first column holding a non-zero left of the diagonal
+// in any row of row block b (none: a value >= the block's first row), up[b] =
+// the first row holding a non-zero above the diagonal in any column of column
+// block b.  Without row exchanges the factors stay inside the envelope (an L
+// entry left of a row's first non-zero, or a U entry above a column's, never
+// becomes non-zero), so for a panel ending at column kend the rows of block b
+// carry no L entries when lo[b] >= kend, and the columns of block b no U
+// entries when up[b] >= kend: their L21 / U12 tiles are zero and stay zero,
+// and their trailing-update tiles receive nothing.  Null: no envelope.
+struct Envelope {
+  const int32_t *lo = nullptr;
+  const int32_t *up = nullptr;
+  __device__ __forceinline__ bool rows_empty(int64_t r, int64_t kend) const { return lo && lo[r / 64] >= kend; }
+  __device__ __forceinline__ bool cols_empty(int64_t c, int64_t kend) const { return up && up[c / 64] >= kend; }
+};
+
 template <typename T>
 inline MatView<T> dense_view(T *a, int64_t ld) { return MatView<T>{a, ld, kDenseBand, kDenseBand}; }
 template <typename T>
@@ -523,13 +540,14 @@ __device__ __forceinline__ void tile_product(const T *P, T *Q) {
 // ---------------------------------------------------------------------------
 template <typename T, typename SH, int NB>
 __global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w, int64_t r_begin, int64_t r_end,
-                                                 const T *inv, Shadow<SH> sh) {
+                                                 const T *inv, Shadow<SH> sh, Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
   T *At = reinterpret_cast<T *>(dsm);
   T *Ui = At + NB * TS;
   const int64_t r0 = r_begin + (int64_t)blockIdx.x * NB;
+  if (env.rows_empty(r0, k0 + w)) return;  // A21 rows zero: L21 rows zero
   const int h = (int)min64(NB, r_end - r0);
   const T *uinv = inv + NB * NB;
   stage_tile<NB, 256, TS>(Ui, [&](int i, int k) { return uinv[i * NB + k]; });
@@ -554,13 +572,15 @@ __global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w
 // Dynamic shared memory: pair_smem_bytes<T, NB>().
 template <typename T, typename SH, int NB, int RW>
 __global__ void __launch_bounds__(256) k_trsm_ru_strip(MatView<T> A, int64_t k0, int w, int64_t r_begin,
-                                                       int64_t r_end, const T *inv, Shadow<SH> sh) {
+                                                       int64_t r_end, const T *inv, Shadow<SH> sh,
+                                                       Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
   T *UiT = reinterpret_cast<T *>(dsm);  // (U11^{-1})^T
   T *AtT = UiT + NB * TS;               // A21 strip transposed: 64 x RW in a 64 x TS buffer
   const int64_t r0 = r_begin + (int64_t)blockIdx.x * RW;
+  if (env.rows_empty(r0, k0 + w)) return;  // A21 rows zero: L21 rows zero (RW divides 64)
   const int h = (int)min64(RW, r_end - r0);
   const T *uinv = inv + NB * NB;
   stage_tile<NB, 256, TS>(UiT, [&](int i, int k) { return uinv[k * NB + i]; });
@@ -589,13 +609,14 @@ __global__ void __launch_bounds__(256) k_trsm_ru_strip(MatView<T> A, int64_t k0,
 // ---------------------------------------------------------------------------
 template <typename T, typename SH, int NB>
 __global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h, int64_t c_begin, int64_t c_end,
-                                                 const T *inv, Shadow<SH> sh) {
+                                                 const T *inv, Shadow<SH> sh, Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
   T *At = reinterpret_cast<T *>(dsm);
   T *Li = At + NB * TS;
   const int64_t c0 = c_begin + (int64_t)blockIdx.x * NB;
+  if (env.cols_empty(c0, r0 + h)) return;  // A12 columns zero: U12 columns zero
   const int wc = (int)min64(NB, c_end - c0);
   stage_tile<NB, 256, TS>(Li, [&](int k, int j) { return inv[k * NB + j]; });
   stage_tile<NB, 256, TS>(At, [&](int k, int j) { return (k < h && j < wc) ? A.get(r0 + k, c0 + j) : T(0); });
@@ -1001,7 +1022,8 @@ constexpr size_t trsm_multi_smem_bytes() { return sizeof(T) * (MAXB + 2) * (size
 
 template <typename T, typename SH, int NB, int MAXB, int CW>
 __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0, int h, int64_t c_begin,
-                                                       int64_t c_end, const T *inv, Shadow<SH> sh) {
+                                                       int64_t c_end, const T *inv, Shadow<SH> sh,
+                                                       Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -1009,6 +1031,7 @@ __global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0,
   T *Lt = U + MAXB * NB * TS;         // L_ji
   T *Li = Lt + NB * TS;               // L_jj^{-1}
   const int64_t c0 = c_begin + (int64_t)blockIdx.x * CW;
+  if (env.cols_empty(c0, r0 + h)) return;  // A12 columns zero: U12 columns zero (CW divides 64)
   const int wc = (int)min64(CW, c_end - c0);
   const int nbk = ceil_div(h, NB);
   // Tile stream, in the order it is consumed: per block j, A_j (this CTA's
@@ -1295,7 +1318,8 @@ __global__ void __launch_bounds__(256) k_sym_u12(MatView<T> A, int64_t c0, int w
 // ---------------------------------------------------------------------------
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    k_gemm_nn(MatView<T> A, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, int lower64 = 0) {
+    k_gemm_nn(MatView<T> A, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, int lower64 = 0,
+              Envelope env = {}) {
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
@@ -1305,6 +1329,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   // lower64 (symmetric update, m0 == n0): only the tiles of 64-blocks on or
   // below the diagonal (BM, BN divide 64).
   if (lower64 && (bn - n0) / 64 > (bm - m0) / 64) return;
+  // outside the envelope (BM, BN divide 64 and m0, n0 start 64-blocks): nothing to subtract
+  if (env.rows_empty(bm, k0 + K) || env.cols_empty(bn, k0 + K)) return;
   T acc[TM][TN];
 #pragma unroll
   for (int a = 0; a < TM; ++a)

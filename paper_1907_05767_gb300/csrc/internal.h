@@ -27,6 +27,9 @@ ebv_status_t dense_factor_staged(int64_t n, ebv_prec_t prec, const double *a_dev
                                  cudaStream_t s);
 ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t ws_bytes,
                          cudaStream_t s);
+// Testing hook of the banded factorisation: false = no block envelope (every
+// CTA of the band window works; the results are the same).
+void set_band_envelope(bool on);
 ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
                         int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
                         size_t ws_bytes, cudaStream_t s);

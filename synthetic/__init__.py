@@ -19,6 +19,11 @@ row-diagonally-dominant coefficient matrix (Eq. 2).  Recipes:
 * ``laplacian_band(g)``: 2D 5-point Laplacian on a g x g grid, natural ordering,
   Dirichlet boundary (edge nodes lack their outside neighbours), diagonal 4.1,
   neighbours -1, stored as a row band with kl = ku = g.
+* ``laplacian_disc_band(r)``: the same operator on the grid points of a disc of
+  radius r (an irregular domain), ordered row by row; the distance to a node's
+  neighbour in the next grid row follows the chord length, so the band's width
+  varies from row to row (a profile, or skyline, matrix stored in its widest
+  band, kl = ku = the largest distance).
 * planted solutions ``x_true ~ U[-1, 1]`` with ``b = A @ x_true``.
 """
 from __future__ import annotations
@@ -140,6 +145,31 @@ def laplacian_band(g: int, diag: float = 4.1) -> tuple[np.ndarray, int, int]:
     ab[gy > 0, kl - g] = -1.0
     ab[gy < g - 1, kl + g] = -1.0
     return ab, kl, ku
+
+
+def laplacian_disc_band(r: int, diag: float = 4.1) -> tuple[np.ndarray, int, int]:
+    """2D 5-point Laplacian on the grid points (x, y) with x^2 + y^2 <= r^2.
+
+    Nodes are numbered row by row (y, then x); a node's neighbours are the grid
+    points next to it that lie in the disc (Dirichlet boundary: the others are
+    left out).  Diagonal 4.1, neighbours -1.  Returns ``(ab, kl, ku)``, the row
+    band with kl = ku = the largest index distance between neighbours.
+    """
+    ys, xs = np.mgrid[-r:r + 1, -r:r + 1]
+    inside = xs * xs + ys * ys <= r * r
+    idx = np.full(inside.shape, -1, dtype=np.int64)
+    n = int(inside.sum())
+    idx[inside] = np.arange(n)
+    east = inside[:, :-1] & inside[:, 1:]
+    south = inside[:-1, :] & inside[1:, :]
+    i = np.concatenate([idx[:, :-1][east], idx[:-1, :][south]])
+    j = np.concatenate([idx[:, 1:][east], idx[1:, :][south]])
+    d = int((j - i).max()) if i.size else 0
+    ab = np.zeros((n, 2 * d + 1), dtype=np.float64)
+    ab[:, d] = diag
+    ab[i, d + (j - i)] = -1.0
+    ab[j, d - (j - i)] = -1.0
+    return ab, d, d
 
 
 def band_to_dense(ab: np.ndarray, kl: int, ku: int) -> np.ndarray:

@@ -281,6 +281,57 @@ def pin_band(lib):
     np.testing.assert_allclose(x2, np.linalg.solve(a2, np.ones((n2, 1))), rtol=0, atol=1e-14)
 
 
+def profile_of(a):
+    """First non-zero column left of the diagonal per row (i when none) and
+    first non-zero row above the diagonal per column (j when none)."""
+    n = a.shape[0]
+    lo = np.array([next((j for j in range(i) if a[i, j] != 0.0), i) for i in range(n)])
+    up = np.array([next((i for i in range(j) if a[i, j] != 0.0), j) for j in range(n)])
+    return lo, up
+
+
+def variable_profile_dd(n: int, kl: int, ku: int, seed: int):
+    """Strictly row-dominant matrix whose row / column profile is drawn at random
+    inside a kl / ku band (test input for the profile pins and tests)."""
+    rng = np.random.default_rng(seed)
+    a = np.zeros((n, n))
+    for i in range(n):
+        f = i - int(rng.integers(0, min(i, kl) + 1))
+        a[i, f:i] = rng.uniform(-1.0, 1.0, i - f)
+        if f < i:
+            a[i, f] = 0.5
+    for j in range(n):
+        g = j - int(rng.integers(0, min(j, ku) + 1))
+        a[g:j, j] = rng.uniform(-1.0, 1.0, j - g)
+        if g < j:
+            a[g, j] = -0.5
+    a += np.diag(np.abs(a).sum(axis=1) + 1.0)
+    return a
+
+
+def pin_band_profile(lib):
+    # Without row exchanges the factors stay inside the profile: L_ij = 0 left of
+    # row i's first non-zero and U_ij = 0 above column j's first non-zero, and the
+    # band factors equal the dense ones (irregular-domain Laplacian and a random
+    # variable profile).
+    ab, kl, ku = synthetic.laplacian_disc_band(7)
+    cases = [(synthetic.band_to_dense(ab, kl, ku), kl, ku), (variable_profile_dd(70, 9, 13, 8), 9, 13)]
+    for c, (a, kl, ku) in enumerate(cases):
+        n = a.shape[0]
+        lo, up = profile_of(a)
+        assert (lo < np.arange(n)).any() and (lo > np.arange(n) - kl).any()  # the profile is uneven
+        fb, info = oracle.band_lu(synthetic.dense_to_band(a, kl, ku), kl, ku, lib=lib)
+        assert info == 0
+        f = synthetic.band_to_dense(fb, kl, ku)
+        assert np.array_equal(f, oracle.lu(a, lib=lib)[0])
+        i, j = np.indices((n, n))
+        assert not np.any(f[(j < i) & (j < lo[:, None])])
+        assert not np.any(f[(i < j) & (i < up[None, :])])
+        if c == 0:  # the Laplacian is sparse inside its profile, and the factors fill it
+            inner = (j < i) & (j >= lo[:, None])
+            assert np.count_nonzero(f[inner]) > np.count_nonzero(a[inner])
+
+
 def pin_symmetric_ldlt(lib):
     # Symmetric A (the reading of eq. 6a-b that scales both vectors by the same
     # pivot): Doolittle's U is D L^T with D the pivots.  For symmetric,
@@ -478,6 +529,7 @@ ALL_PINS = [
     pin_lapack_lu_column_dominant,
     pin_planted_solution,
     pin_band,
+    pin_band_profile,
     pin_symmetric_ldlt,
     pin_adjoint,
     pin_residual,

@@ -130,3 +130,35 @@ def test_symmetric_bands(n, k):
 def test_symmetric_band_fp32():
     ab, kl, ku = synthetic.laplacian_band(20)
     check(ab, kl, ku, 2, 7, prec="fp32", sym=True)
+
+
+def factors_without_envelope(ab, kl, ku, prec, sym):
+    ebv.lib().ebv_debug_set_band_envelope(0)
+    try:
+        f = ebv.band_factor(torch.from_numpy(ab).to(DEV), kl, ku, prec, sym=sym)
+        return f.lu.cpu().numpy()
+    finally:
+        ebv.lib().ebv_debug_set_band_envelope(1)
+
+
+@pytest.mark.parametrize("sym", [False, True])
+@pytest.mark.parametrize("r", [20, 45])
+def test_profile_disc_laplacian(r, sym):
+    # An irregular domain: the distance to the next grid row's neighbour follows
+    # the chord, so the band's width varies and the factorisation skips the
+    # tiles outside the profile.  Skipped tiles are exactly zero, so the factors
+    # equal those of the full band window bit for bit.
+    ab, kl, ku = synthetic.laplacian_disc_band(r)
+    f, _ = check(ab, kl, ku, 4, 400 + r, sym=sym)
+    assert np.array_equal(f.lu.cpu().numpy(), factors_without_envelope(ab, kl, ku, "fp64", sym))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_profile_random(prec):
+    from oracle_pins import variable_profile_dd
+    kl, ku = 90, 130
+    a = variable_profile_dd(700, kl, ku, 3)
+    a = (a + np.diag(np.abs(a).sum(axis=1))) / 128.0  # well conditioned, O(1) pivots: the FP32 tolerances
+    ab = synthetic.dense_to_band(a, kl, ku)
+    f, _ = check(ab, kl, ku, 3, 701, prec=prec)
+    assert np.array_equal(f.lu.cpu().numpy(), factors_without_envelope(ab, kl, ku, prec, False))
