@@ -139,6 +139,22 @@ def cpu_model() -> str:
 # GPU arm
 # ----------------------------------------------------------------------------
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it); the time itself at N = 1."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(world, flops_per_replica, ms):
+    """Replicas only (no data-path collective): every rank solves its own
+    system per step, so the job's rate is world systems per slowest step."""
+    return world * flops_per_replica / (ms / 1e3) / 1e9
+
+
 def run_gpu(args, rank, world, dist):
     import torch
 
@@ -208,10 +224,7 @@ def run_gpu(args, rank, world, dist):
     launches = launches_per_step * args.steps
     ms_total = e0.elapsed_time(e1)
     ms = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     rep_np = ebv.read_report(rep)
     info_v = int(info.item())
 
@@ -224,7 +237,7 @@ def run_gpu(args, rank, world, dist):
     err_true = float(np.abs(xs - x_true).max() / np.abs(x_true).max())
 
     flops = nominal_flops(n, nrhs)
-    value = world * flops / (ms / 1e3) / 1e9
+    value = whole_job_gflops(world, flops, ms)
 
     # per-kernel-class device times of one more (profiled) step
     ebv.profile(True)
