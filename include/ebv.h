@@ -130,17 +130,21 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *   desc      matrix shape and storage.
  *   prec      EBV_FP64 or EBV_FP32: `a` (device, double* or float*) is
  *             overwritten by the packed factors; `lowp` must be NULL.
- *             EBV_MIXED_BF16 / EBV_MIXED_FP16 (dense only): `a` is a device
- *             double* holding A and is NOT modified; `lowp` (device float*,
- *             n x n, leading dimension n) receives the packed FP32 factors,
- *             whose trailing (Schur) updates were computed from bfloat16 /
- *             half operands on the tensor cores with FP32 accumulation.
+ *             EBV_MIXED_BF16 / EBV_MIXED_FP16: `a` is a device double*
+ *             holding A and is NOT modified; `lowp` (device float*) receives
+ *             the packed FP32 factors.  Dense: lowp is n x n, leading
+ *             dimension n, and the trailing (Schur) updates are computed from
+ *             bfloat16 / half operands on the tensor cores with FP32
+ *             accumulation.  Band: lowp has the band layout of `a` (n rows of
+ *             ld floats) and the updates run in FP32 (a band's updates are
+ *             too thin for the tensor cores); ebv_solve with `refine` then
+ *             brings X to FP64 accuracy.
  *   info_dev  device int32: 0, or the 1-based index of the first zero or
  *             non-finite pivot.  Always written.
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
- * Band storage (EBV_BAND, EBV_BAND_SYM) supports EBV_FP64 and EBV_FP32; fill-in stays inside
- * the band because no rows are exchanged.  A band whose width varies row by row
+ * Band storage (EBV_BAND, EBV_BAND_SYM) supports every precision (the mixed ones as above);
+ * fill-in stays inside the band because no rows are exchanged.  A band whose width varies row by row
  * (a profile, or skyline, matrix stored in its widest band) costs the work of
  * its profile: the factorisation first finds each 64-block's envelope and
  * skips the tiles outside it (see ebv_debug_set_band_envelope).

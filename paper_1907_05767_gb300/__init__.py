@@ -375,11 +375,19 @@ def inverse(f: Factors) -> torch.Tensor:
 
 def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64", sym: bool = False) -> Factors:
     """Factor a row-band matrix (n x (kl+ku+1)).  sym: A is symmetric (kl == ku,
-    both halves stored); U is formed from L and the pivots (EBV_BAND_SYM)."""
+    both halves stored); U is formed from L and the pivots (EBV_BAND_SYM).
+    Mixed precisions: FP32 factors of the FP64 band in a new tensor, for
+    refined solves to FP64 accuracy."""
     p = _prec(prec)
+    storage = BAND_SYM if sym else BAND
+    if p in (MIXED_BF16, MIXED_FP16):
+        a64 = ab.to(torch.float64).contiguous()
+        lowp = torch.empty(a64.shape, dtype=torch.float32, device=a64.device)
+        info = ebv_factor(a64, p, lowp=lowp, kl=kl, ku=ku, storage=storage)
+        return Factors(lowp, info, p, a64, kl, ku, BAND)
     dt = torch.float64 if p == FP64 else torch.float32
     lu = ab.to(dt).clone().contiguous()
-    info = ebv_factor(lu, p, kl=kl, ku=ku, storage=BAND_SYM if sym else BAND)
+    info = ebv_factor(lu, p, kl=kl, ku=ku, storage=storage)
     return Factors(lu, info, p, ab.to(torch.float64).contiguous(), kl, ku, BAND)
 
 

@@ -44,7 +44,6 @@ ebv_status_t check_desc(const ebv_desc_t *d, ebv_prec_t prec) {
     if (d->storage == EBV_BAND_SYM && d->kl != d->ku) return EBV_ERR_ARG;
     if (d->n > 0 && (d->kl >= d->n || d->ku >= d->n)) return EBV_ERR_ARG;
     if (d->ld < d->kl + d->ku + 1) return EBV_ERR_ARG;
-    if (is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
   } else {
     return EBV_ERR_ARG;
   }
@@ -90,7 +89,7 @@ ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *
   cudaStream_t s = (cudaStream_t)stream;
   if (desc->storage != EBV_DENSE) {
     if (!ws || ws_bytes < band_factor_ws(desc->n, desc->kl, desc->ku, prec)) return EBV_ERR_WORKSPACE;
-    return band_factor(desc, prec, a, info_dev, ws, ws_bytes, s);
+    return band_factor(desc, prec, a, lowp, info_dev, ws, ws_bytes, s);
   }
   const size_t need = dense_factor_ws(desc->n, prec);
   if (need > 0 && (!ws || ws_bytes < need)) return EBV_ERR_WORKSPACE;

@@ -69,6 +69,14 @@ __global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, 
 
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
 
+// Binary32 working copy of the whole band array (mixed precisions): count
+// elements, grid-stride.  Slots outside the matrix are copied too and, as in
+// the FP64 array, never read.
+__global__ void __launch_bounds__(256) k_band_narrow(const double *ab, float *lo, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < count; e += (int64_t)gridDim.x * 256)
+    lo[e] = (float)ab[e];
+}
+
 template <typename T>
 ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym,
                            cudaStream_t s) {
@@ -182,8 +190,8 @@ size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
 }
 
-ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t ws_bytes,
-                         cudaStream_t s) {
+ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
+                         size_t ws_bytes, cudaStream_t s) {
   EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
   if (d->n == 0) return EBV_OK;
@@ -196,6 +204,16 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t 
                                  s);
   if (prec == EBV_FP32)
     return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, env, sym, s);
+  if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
+    // FP32 factors of the FP64 band in lowp (same layout); a stays untouched
+    // for the refinement's residual.  The band's updates run in FP32 SIMT.
+    const int64_t count = d->n * d->ld;
+    k_band_narrow<<<(unsigned)std::min<int64_t>(4096, (count + 255) / 256), 256, 0, s>>>((const double *)a,
+                                                                                         (float *)lowp, count);
+    EBV_TRY(launch_ok());
+    return band_factor_t<float>(band_view((float *)lowp, d->ld, d->kl, d->ku), d->n, info, (float *)inv, env, sym,
+                                s);
+  }
   return EBV_ERR_UNSUPPORTED;
 }
 
@@ -223,6 +241,9 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
   if (prec == EBV_FP32)
     return solve_refined<float>(band_view((float *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
                                 (char *)ws, L, false, residual, s);
+  if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16)  // FP32 factors, FP64 right-hand sides and solution
+    return solve_refined<float>(band_view((float *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
+                                (char *)ws, L, true, residual, s);
   return EBV_ERR_UNSUPPORTED;
 }
 

@@ -25,8 +25,8 @@ unsigned int *dense_factor_scan_init(int64_t n, ebv_prec_t prec, void *ws, cudaS
 ebv_status_t dense_factor_staged(int64_t n, ebv_prec_t prec, const double *a_dev, float *lowp, int32_t *info,
                                  void *ws, size_t ws_bytes, const cudaEvent_t *ev, int64_t cbw, bool convert,
                                  cudaStream_t s);
-ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, int32_t *info, void *ws, size_t ws_bytes,
-                         cudaStream_t s);
+ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
+                         size_t ws_bytes, cudaStream_t s);
 // Testing hook of the banded factorisation: false = no block envelope (every
 // CTA of the band window works; the results are the same).
 void set_band_envelope(bool on);

@@ -72,9 +72,10 @@ def test_factor_argument_errors(lib):
     # mixed precision needs the FP32 output buffer and the workspace
     assert lib.ebv_factor(ctypes.byref(d), ebv.MIXED_BF16, FAKE, None, info, None, 0, None) == ebv.ERR_ARG
     assert lib.ebv_factor(ctypes.byref(d), ebv.MIXED_BF16, FAKE, FAKE, info, None, 0, None) == ebv.ERR_WORKSPACE
-    # mixed precision is dense only
+    # band storage in mixed precision: FP32 factors into lowp (same band layout), workspace required
     db = _d(8, 3, 1, 1, ebv.BAND)
-    assert lib.ebv_factor(ctypes.byref(db), ebv.MIXED_FP16, FAKE, FAKE, info, None, 0, None) == ebv.ERR_UNSUPPORTED
+    assert lib.ebv_factor(ctypes.byref(db), ebv.MIXED_FP16, FAKE, None, info, None, 0, None) == ebv.ERR_ARG
+    assert lib.ebv_factor(ctypes.byref(db), ebv.MIXED_FP16, FAKE, FAKE, info, None, 0, None) == ebv.ERR_WORKSPACE
 
 
 def test_solve_argument_errors(lib):

@@ -162,3 +162,26 @@ def test_profile_random(prec):
     ab = synthetic.dense_to_band(a, kl, ku)
     f, _ = check(ab, kl, ku, 3, 701, prec=prec)
     assert np.array_equal(f.lu.cpu().numpy(), factors_without_envelope(ab, kl, ku, prec, False))
+
+
+@pytest.mark.parametrize("prec,sym,grid", [("bf16", False, 40), ("fp16", True, 40), ("bf16", True, 0)])
+def test_band_mixed_refined(prec, sym, grid):
+    # Mixed precision on a band: FP32 factors of the FP64 band (FP32 tolerances
+    # against the oracle's factors), then refinement with the FP64-accurate
+    # band residual to a relative residual of 1e-12.
+    ab, kl, ku = synthetic.laplacian_band(grid) if grid else synthetic.laplacian_disc_band(30)
+    n = ab.shape[0]
+    x_true = synthetic.planted_x(n, 8, 800 + n)
+    b = synthetic.band_rhs(ab, kl, ku, x_true)
+    f = ebv.band_factor(torch.from_numpy(ab).to(DEV), kl, ku, prec, sym=sym)
+    assert f.lu.dtype == torch.float32 and int(f.info.item()) == 0
+    fb, _ = oracle.band_lu(ab, kl, ku)
+    assert np.abs(f.lu.cpu().numpy().astype(np.float64) - fb).max() <= 5e-5
+    rep = torch.zeros(3, dtype=torch.float64, device=DEV)
+    x = ebv.solve(f, torch.from_numpy(b).to(DEV), refine=(1e-12, 10), report=rep).cpu().numpy()
+    r = ebv.read_report(rep)
+    assert r["status"] == ebv.OK and r["resid_final"] <= 1e-12 and r["iters"] >= 1, r
+    x_ref = oracle.band_solve(fb, kl, ku, b)
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-11
+    res = oracle.band_residual(ab, kl, ku, x, b)
+    assert (np.abs(res).max(axis=0) / np.abs(b).max(axis=0)).max() <= 1e-12
