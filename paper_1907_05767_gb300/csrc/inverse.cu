@@ -236,14 +236,14 @@ ebv_status_t inverse_t(int64_t n, const T *lu, int64_t ldl, T *x, int64_t ldx, v
   using G = InvTile<T>;
   constexpr int NT = (G::BM / G::TM) * (G::BN / G::TN);
   if (n == 0) return EBV_OK;
-  static bool ready = false;  // one attribute set per process and type
-  if (!ready) {
-    EBV_CU(set_smem(k_inv_leaf<T>, (int)diag_smem_bytes<T, kNB>()));
-    EBV_CU(set_smem(k_inv_level<T, 1>, 0));
-    EBV_CU(set_smem(k_inv_level<T, 2>, 0));
-    EBV_CU(set_smem(k_inv_product<T>, 0));
-    ready = true;
-  }
+  static const cudaError_t attr = [] {  // once per process and type (thread-safe static initialisation)
+    cudaError_t e = set_smem(k_inv_leaf<T>, (int)diag_smem_bytes<T, kNB>());
+    if (e == cudaSuccess) e = set_smem(k_inv_level<T, 1>, 0);
+    if (e == cudaSuccess) e = set_smem(k_inv_level<T, 2>, 0);
+    if (e == cudaSuccess) e = set_smem(k_inv_product<T>, 0);
+    return e;
+  }();
+  if (attr != cudaSuccess) return EBV_ERR_CUDA;
   T *P = static_cast<T *>(ws);
   const int64_t ldp = inv_ldp(n);
   const int64_t nblk = ceil_div(n, kNB);
