@@ -11,9 +11,11 @@ after a Doolittle factorisation without pivoting of a diagonally dominant A
 (Eq. 2, Eq. 6a-c), with long and short vectors paired for equal work (Eq. 7).
 
 Names follow the C ABI in include/ebv.h: ``ebv_factor``, ``ebv_solve``,
-``ebv_factor_solve_batched``, ``ebv_solve_adjoint`` take torch tensors.
-Convenience wrappers: ``factor``, ``solve``, ``band_factor``, ``band_solve``,
-``factor_solve_batched``, and the autograd function ``EbvSolve``.
+``ebv_gesv_host``, ``ebv_solve_static``, ``ebv_inverse``, ``ebv_solve_adjoint``
+take torch tensors.  Convenience wrappers: ``factor``, ``band_factor`` (both
+return ``Factors``), ``solve`` and ``inverse`` (dense or band factors),
+``Batch`` / ``uniform_batch`` (``ebv_factor_solve_batched``), and the autograd
+function ``EbvSolve``.
 """
 from __future__ import annotations
 
