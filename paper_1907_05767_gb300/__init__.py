@@ -13,7 +13,7 @@ after a Doolittle factorisation without pivoting of a diagonally dominant A
 Names follow the C ABI in include/ebv.h: ``ebv_factor``, ``ebv_solve``,
 ``ebv_gesv_host``, ``ebv_solve_static``, ``ebv_inverse``, ``ebv_solve_adjoint``
 take torch tensors.  Convenience wrappers: ``factor``, ``band_factor`` (both
-return ``Factors``), ``solve`` and ``inverse`` (dense or band factors),
+return ``Factors``), ``solve`` (dense or band factors), ``inverse`` (dense),
 ``Batch`` / ``uniform_batch`` (``ebv_factor_solve_batched``), and the autograd
 function ``EbvSolve``.
 """
