@@ -503,6 +503,14 @@ def pin_inverse_closed_forms(lib):
     assert np.array_equal(x[:5, :5], oracle.inverse(oracle.lu(a1, lib=lib)[0], lib=lib))
     assert np.array_equal(x[5:, 5:], oracle.inverse(oracle.lu(a2, lib=lib)[0], lib=lib))
     assert not np.any(x[:5, 5:]) and not np.any(x[5:, :5])
+    # tridiag(-1, 2, -1) of order m (1-based indices): (A^{-1})_ij = min(i, j) (m + 1 - max(i, j)) / (m + 1)
+    # (its pivots (k+1)/k never vanish, so the no-pivot factors exist)
+    m = 24
+    t = 2.0 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)
+    i1, j1 = np.indices((m, m)) + 1
+    closed = np.minimum(i1, j1) * (m + 1 - np.maximum(i1, j1)) / (m + 1.0)
+    x = oracle.inverse(oracle.lu(t, lib=lib)[0], lib=lib)
+    assert np.abs(x - closed).max() <= 1e-13 * np.abs(closed).max()
     # 2 x 2: [[a, b], [c, d]]^{-1} = [[d, -b], [-c, a]] / (ad - bc)
     a = np.array([[4.0, 3.0], [6.0, 3.0]])
     x = oracle.inverse(oracle.lu(a, lib=lib)[0], lib=lib)
