@@ -11,6 +11,8 @@
  *             of the L and U vectors from the trailing matrix.
  *   - Eq. 7a-e: the 2n vectors (n columns of L, n rows of U) are paired long
  *             with short so that every thread gets the same amount of work.
+ *   - Eq. 4c: A^{-1} as the product of the elimination's elementary
+ *             transformations, U^{-1} L^{-1} (ebv_inverse).
  *
  * Conventions shared by every entry point
  *   - Matrices are row-major: element (i, j) of a dense matrix is at
