@@ -155,6 +155,80 @@ def whole_job_gflops(world, flops_per_replica, ms):
     return world * flops_per_replica / (ms / 1e3) / 1e9
 
 
+def shard_of_rank(ns, rs, world, rank):
+    """Indices (ascending) of the systems of a batch that rank `rank` of
+    `world` solves: the library's size-balanced split (long/short pairs of
+    Eq. 7 across systems, then longest-first onto the least-loaded rank).
+    Every rank computes the same split; no data moves between ranks."""
+    import paper_1907_05767_gb300 as ebv
+    rank_of, cost = ebv.ebv_batch_partition(ns, rs, world)
+    return np.flatnonzero(rank_of == rank), rank_of, cost
+
+
+def gather_by_system(values, idx, batch, dist, device):
+    """Every rank's per-system values (int64, in the order of its `idx`) put
+    back into system order on every rank: the batched workload's only
+    exchange, done once after the timed region (per-system info words)."""
+    import torch
+    full = torch.zeros(batch, dtype=torch.int64, device=device)
+    full[torch.as_tensor(idx, dtype=torch.int64, device=device)] = torch.as_tensor(values, dtype=torch.int64,
+                                                                                   device=device)
+    if dist is not None:
+        dist.all_reduce(full, op=dist.ReduceOp.SUM)  # each system is owned by exactly one rank
+    return full.cpu().numpy()
+
+
+def run_batched(args, rank, world, dist):
+    """The batched workload: 4096 dense systems n ~ U{16..512}, 1-4 RHS, in
+    FP64 or FP32, split across the ranks by size (no exchange in the data
+    path); each rank solves its share in one persistent launch replayed from
+    a CUDA graph.  The value is systems (and nominal flops) of the whole job
+    per slowest rank's step."""
+    import torch
+
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ns, rs = synthetic.config3_sizes()
+    idx, _, cost = shard_of_rank(ns, rs, world, rank)
+    vmap, tuned = None, None
+    if args.autotune:
+        vmap, tuned = ebv.batch_autotune_buckets(args.batched_prec, cache_path=args.tune_cache)
+    bt = ebv.Batch(ns[idx], rs[idx], args.batched_prec, device=dev, variant_of_n=vmap)
+    for k, s in enumerate(idx):
+        a, _, b = synthetic.config3_system(int(s), int(ns[s]), int(rs[s]))
+        bt.a_view(k).copy_(torch.from_numpy(a))
+        bt.b_view(k).copy_(torch.from_numpy(b))
+    a0, b0 = bt.a_buf.clone(), bt.b_buf.clone()
+
+    def restore():
+        bt.a_buf.copy_(a0)
+        bt.b_buf.copy_(b0)
+
+    def step():
+        restore()
+        bt.run()
+
+    ms_restore = _dev_ms(restore, args.steps, args.warmup)
+    ms_all = _dev_ms(step, args.steps, max(3, args.warmup))
+    ms = max_over_ranks(ms_all - ms_restore, dist, dev)
+    info = gather_by_system(bt.info.cpu().numpy(), idx, len(ns), dist, dev)
+    flops = float(sum(nominal_flops(int(n), int(r)) for n, r in zip(ns, rs)))
+    line = {"metric": "batched factor+solve solves/s & GFLOP/s (4096 systems n~U{16..512}, 1-4 RHS)",
+            "value": len(ns) * 1e3 / ms, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "gflops": flops / (ms / 1e3) / 1e9, "dtype": args.batched_prec, "data": "synthetic (seeded)",
+            "config": {"workload": "batched 4096 systems n~U{16..512}, 1-4 RHS, offdiag U[-0.5,0.5]/(n-1)",
+                       "parallelism": f"systems split over {world} rank(s) by cost, no exchange",
+                       "cuda_graph": True, "l2": "restore of the inputs (1.5-3 GB) between steps flushes L2",
+                       "rank_cost_spread": float(cost.max() / max(cost.min(), 1.0))},
+            "info_nonzero": int(np.count_nonzero(info)), "gpu_launches": 1,
+            "tuned_variants": tuned}
+    return line
+
+
 def run_gpu(args, rank, world, dist):
     import torch
 
@@ -881,6 +955,11 @@ def main():
                    help="time the other workloads (one JSON line each) and exit; --configs inverse / profile / band_mixed: "
                         "one alone")
     p.add_argument("--inverse-n", type=int, default=8192, help="order of the explicit-inverse workload")
+    p.add_argument("--workload", default="dense", choices=["dense", "batched"],
+                   help="batched: the 4096-system batch split across the ranks (one JSON line)")
+    p.add_argument("--batched-prec", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--autotune", action="store_true", help="batched: tuned variant per size bucket")
+    p.add_argument("--tune-cache", default=None, help="batched: JSON cache of the autotuner")
     args = p.parse_args()
     if args.update_only:
         print(json.dumps(run_update_only(args)), flush=True)
@@ -914,7 +993,7 @@ def main():
         import torch.distributed as tdist
         tdist.init_process_group("nccl")
         dist = tdist
-    line = run_gpu(args, rank, world, dist)
+    line = run_batched(args, rank, world, dist) if args.workload == "batched" else run_gpu(args, rank, world, dist)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -74,7 +74,10 @@ typedef enum {
   EBV_FP32 = 1,       /* binary32 throughout */
   EBV_MIXED_BF16 = 2, /* FP32 factors whose trailing updates take bfloat16
                          operands on the tensor cores (FP32 accumulation);
-                         FP64 residual / update / pivot reciprocals */
+                         FP64 for the refinement's residual r = b - Ax and
+                         update x += d, and for the pivot reciprocals (formed
+                         as 1/(double)a_rr, rounded once to binary32 for the
+                         FP32 factors; EBV_FP32 does the same) */
   EBV_MIXED_FP16 = 3  /* as above with IEEE half operands, each operand panel
                          scaled by a power of two to stay in half's normal range */
 } ebv_prec_t;
@@ -159,8 +162,9 @@ EBV_API ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a
  *
  *   lu        device: packed factors from ebv_factor (double* for EBV_FP64,
  *             float* for EBV_FP32 and the mixed precisions, i.e. `lowp`).
- *   a_orig    device double*, the original A (same desc); required for the mixed
- *             precisions and whenever `refine` is given, else may be NULL.
+ *   a_orig    device double*, the original A (same desc); required whenever
+ *             `refine` is given (it is the A of the FP64 residual) and ignored
+ *             otherwise (may be NULL).
  *   b         device, n x nrhs, leading dimension ldb >= nrhs; overwritten by X.
  *             double* for EBV_FP64 and the mixed precisions, float* for EBV_FP32.
  *   refine    NULL: no refinement.  Otherwise iterative refinement: r = b - A x
@@ -188,8 +192,12 @@ EBV_API ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const vo
  *   right-hand-side counts (host arrays) into `schedule_host`; EBV_ERR_ARG for
  *   an order outside 0..4096 or a count outside 0..64.  `variant_of_n`
  *   (host, nullable, 4096 entries) maps each order 1..4096 to a kernel
- *   variant id (0 = blocks of 16 columns, 1 = blocks of 32), e.g. from
- *   ebv_batch_autotune; NULL uses the built-in default (16 up to order 64).
+ *   variant id v in 0..EBV_BATCH_VARIANTS-1: block width NB = 16 << (v % 3)
+ *   columns and trailing-update output tiles of TM = 64 >> (v / 3) squared
+ *   (0: NB 16, TM 64; 1: NB 32, TM 64; 2: NB 64, TM 64; 3..5: the same with
+ *   TM 32).  NB = 64 is offered for EBV_FP32 only (in FP64 those ids run as
+ *   id 1).  The map usually comes from ebv_batch_autotune; NULL uses the
+ *   built-in default (id 0 up to order 64, id 1 above).
  *   The caller copies the schedule to device memory once and may reuse it for
  *   every call with the same sizes.
  * ebv_factor_solve_batched: system s has order n_dev[s] (1..4096) and
@@ -205,18 +213,38 @@ EBV_API int64_t ebv_batch_schedule_len(int64_t batch);
 EBV_API size_t ebv_batch_workspace_size(int64_t batch);
 EBV_API ebv_status_t ebv_batch_schedule(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host,
                                 const int8_t *variant_of_n, int32_t *schedule_host);
+/*
+ * ebv_batch_partition (host): splits a batch across nranks processes, one GPU
+ * each, with no exchange between them (the systems are independent; the
+ * paper's Abstract and Conclusions name multiple devices as a fit for the
+ * method).  The systems are first grouped into the long/short pairs of
+ * ebv_batch_schedule (Eq. 7's equalisation across systems); the pairs, in
+ * decreasing cost, then go one by one to the rank with the least work so far
+ * (lowest rank on ties), so no rank gets more than one pair's cost above the
+ * average.  Deterministic: every rank computes the same split from the same
+ * sizes.  rank_of_host (host, batch entries) receives each system's rank;
+ * cost_of_rank_host (host, nranks entries, nullable) each rank's summed cost
+ * in flops (2n^3/3 + 2n^2 nrhs + 1 per system).  EBV_ERR_ARG as for
+ * ebv_batch_schedule, or for nranks outside 1..65536.
+ */
+EBV_API ebv_status_t ebv_batch_partition(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host,
+                                         int32_t nranks, int32_t *rank_of_host, double *cost_of_rank_host);
 EBV_API ebv_status_t ebv_factor_solve_batched(int64_t batch, const int32_t *n_dev, const int32_t *nrhs_dev,
                                       void *const *a_ptrs_dev, void *const *b_ptrs_dev, ebv_prec_t prec,
                                       const int32_t *schedule_dev, int32_t *info_dev, void *ws,
                                       size_t ws_bytes, ebv_stream_t stream);
 
 /*
- * Autotuner for the batched kernel: times every variant on `reps` synthetic
- * systems of each order in `orders` (host array of count entries) and writes
- * the fastest variant id per order to best_variant_host.  scratch_dev must
- * hold ebv_batch_autotune_scratch(max order, reps, prec) bytes.  Synchronises
- * the stream (it measures time).
+ * Autotuner for the batched kernel: times every variant offered in `prec` on
+ * `reps` synthetic diagonally dominant systems of each order in `orders`
+ * (host array of count entries; one launch per variant and order, the
+ * second of two runs timed with CUDA events) and writes the fastest variant
+ * id per order to best_variant_host.  ms_host (host, nullable, count *
+ * EBV_BATCH_VARIANTS entries) receives the times, -1 for variants not
+ * offered in `prec`.  scratch_dev must hold ebv_batch_autotune_scratch(max
+ * order, reps, prec) bytes.  Synchronises the stream (it measures time).
  */
+#define EBV_BATCH_VARIANTS 6
 EBV_API size_t ebv_batch_autotune_scratch(int32_t max_n, int32_t reps, ebv_prec_t prec);
 EBV_API ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, int32_t reps, ebv_prec_t prec,
                                 void *scratch_dev, size_t scratch_bytes, int8_t *best_variant_host,
@@ -318,12 +346,16 @@ EBV_API ebv_status_t ebv_gesv_host(const ebv_desc_t *desc, ebv_prec_t prec, cons
  * Limits: n <= EBV_STATIC_MAX_N and nrhs <= EBV_STATIC_MAX_NRHS; larger
  * sizes return EBV_ERR_WORKSPACE before any work is enqueued.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture on that device.  All calls on a device share the
- * one array, which keeps the last call's contents (each call clears what has
- * to start at zero): calls whose work overlaps on the GPU (other streams,
- * other host threads without ordering) race and give undefined results.
+ * The first call in a CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress) with that context current; make that first call
+ * before any stream capture in it.  The address is cached per device with
+ * the context's unique ID and looked up again when another context is
+ * current: after cudaDeviceReset (which makes a new primary context) or when
+ * the caller has made a context of its own current, the next call is such a
+ * first call again.  All calls on a device share the one array, which keeps
+ * the last call's contents (each call clears what has to start at zero):
+ * calls whose work overlaps on the GPU (other streams, other host threads
+ * without ordering) race and give undefined results.
  */
 #define EBV_STATIC_SCRATCH_BYTES ((size_t)20 << 20)
 #define EBV_STATIC_MAX_N 4096
@@ -353,13 +385,6 @@ EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
 EBV_API void ebv_debug_set_band_envelope(int32_t enable);
 
 /*
- * Testing hook (project addition; the residual of the refinement loop):
- * R = B - A X for a dense FP64 A (n x n, lda) and FP64 X, B (n x nrhs,
- * leading dimension nrhs), evaluated exactly as ebv_solve's refinement does
- * it (double-float arithmetic).  R: device, n x nrhs.  ws: a workspace of at
- * least ebv_workspace_size(dense n, EBV_FP64, nrhs) bytes.
- */
-/*
  * Testing hook (project addition; the aggregated rank-1 update of Eq. 6c as
  * the mixed-precision factorisation runs it):
  *   C(m0+i, n0+j) -= scale[2] * sum_{k<K} lb(m0+i, k0+k) * ut(n0+j, k0+k)
@@ -386,6 +411,17 @@ EBV_API int32_t ebv_debug_tc_available(void);
  */
 EBV_API ebv_status_t ebv_debug_wait_probe(int64_t polls, void *ws, ebv_stream_t stream);
 
+/*
+ * Testing hook (project addition; the residual of the refinement loop):
+ * R = B - A X for a dense FP64 A (n x n, lda) and FP64 X, B (n x nrhs,
+ * leading dimension nrhs), evaluated exactly as ebv_solve's dense refinement
+ * does it: on the tensor cores by exact splitting of A and X into integer
+ * digits (products and partial sums exact in the FP32 accumulators, the
+ * digit-pair sums carried in triple-binary32), accurate to FP64 level;
+ * without the tensor-map encoder, the triple-binary32 SIMT kernel.
+ * R: device, n x nrhs.  ws: a workspace of at least
+ * ebv_workspace_size(dense n, EBV_FP64, nrhs) bytes.
+ */
 EBV_API ebv_status_t ebv_debug_residual(int64_t n, const double *a, int64_t lda, const double *x, const double *b,
                                         int64_t nrhs, double *r, void *ws, size_t ws_bytes, ebv_stream_t stream);
 

@@ -80,6 +80,7 @@ _SIGNATURES = [
     ("ebv_batch_schedule_len", _I64, [_I64]),
     ("ebv_batch_workspace_size", _SZ, [_I64]),
     ("ebv_batch_schedule", _I32, [_I64, _VP, _VP, _VP, _VP]),
+    ("ebv_batch_partition", _I32, [_I64, _VP, _VP, _I32, _VP, _VP]),
     ("ebv_factor_solve_batched", _I32, [_I64, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _SZ, _VP]),
     ("ebv_batch_autotune_scratch", _SZ, [_I32, _I32, _I32]),
     ("ebv_batch_autotune", _I32, [_VP, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP]),
@@ -406,7 +407,9 @@ def debug_residual(a: torch.Tensor, x: torch.Tensor, b: torch.Tensor) -> torch.T
     return r
 
 
-BATCH_VARIANTS = {0: "nb16", 1: "nb32"}
+# Batched kernel variants: block width NB x trailing-update tile edge TM.
+BATCH_VARIANTS = {0: "nb16_tm64", 1: "nb32_tm64", 2: "nb64_tm64", 3: "nb16_tm32", 4: "nb32_tm32",
+                  5: "nb64_tm32"}
 MAX_BATCH_ORDER = 4096
 
 
@@ -425,6 +428,19 @@ def ebv_batch_schedule(n_list, nrhs_list, variant_of_n=None):
                                     vmap.ctypes.data if vmap is not None else None, sched.ctypes.data),
            "ebv_batch_schedule")
     return sched
+
+
+def ebv_batch_partition(n_list, nrhs_list, nranks):
+    """Split a batch across ``nranks`` GPUs (host): returns (rank of each
+    system as an int32 numpy array, summed cost of each rank in flops)."""
+    import numpy as np
+    n_arr = np.ascontiguousarray(n_list, dtype=np.int32)
+    r_arr = np.ascontiguousarray(nrhs_list, dtype=np.int32)
+    rank_of = np.zeros(n_arr.size, dtype=np.int32)
+    cost = np.zeros(int(nranks), dtype=np.float64)
+    _check(lib().ebv_batch_partition(n_arr.size, n_arr.ctypes.data, r_arr.ctypes.data, int(nranks),
+                                     rank_of.ctypes.data, cost.ctypes.data), "ebv_batch_partition")
+    return rank_of, cost
 
 
 class Batch:
@@ -486,7 +502,8 @@ def batch_autotune(orders, prec="fp64", reps=16, device="cuda", cache_path=None)
     import json
     import numpy as np
     p = _prec(prec)
-    key = f"{torch.cuda.get_device_name(device)}|{p}|{reps}"
+    cap = torch.cuda.get_device_capability(device)
+    key = f"{torch.cuda.get_device_name(device)}|sm_{cap[0]}{cap[1]}|{p}|{reps}"
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as fh:
@@ -502,8 +519,9 @@ def batch_autotune(orders, prec="fp64", reps=16, device="cuda", cache_path=None)
         _check(lib().ebv_batch_autotune(arr.ctypes.data, arr.size, reps, p, _ptr(scratch), scratch.numel(),
                                         best.ctypes.data, ms.ctypes.data, _stream(scratch.device)),
                "ebv_batch_autotune")
+        nv = len(BATCH_VARIANTS)
         for i, o in enumerate(todo):
-            entry[str(o)] = {"best": int(best[i]), "ms": [float(v) for v in ms[i * 2:(i + 1) * 2]]}
+            entry[str(o)] = {"best": int(best[i]), "ms": [float(v) for v in ms[i * nv:(i + 1) * nv]]}
         cache[key] = entry
         if cache_path:
             with open(cache_path, "w") as fh:
@@ -515,6 +533,23 @@ def batch_autotune(orders, prec="fp64", reps=16, device="cuda", cache_path=None)
     for n in range(1, MAX_BATCH_ORDER + 1):
         vmap[n - 1] = vals[np.abs(keys - n).argmin()]
     return vmap, {k: entry[str(k)]["ms"] for k, _ in tuned}
+
+
+BATCH_BUCKET = 32  # orders per autotuner size bucket
+
+
+def batch_autotune_buckets(prec="fp64", nmin=16, nmax=512, reps=304, device="cuda", cache_path=None):
+    """The autotuner over size buckets: orders nmin..nmax in buckets of
+    BATCH_BUCKET, each tuned at its middle order on `reps` systems (304 = two
+    resident CTAs on each of 152 SMs, so a launch is timed at full occupancy).
+    Returns (variant_of_n for every order 1..4096, {bucket middle order:
+    {"best": variant name, "ms": [ms per variant, -1 where not offered]}}).
+    With cache_path the per-order results are kept in that JSON file, keyed
+    by device name, compute capability, precision and reps."""
+    mids = sorted({min(nmax, lo + BATCH_BUCKET // 2) for lo in range(nmin, nmax + 1, BATCH_BUCKET)})
+    vmap, ms = batch_autotune(mids, prec, reps=reps, device=device, cache_path=cache_path)
+    table = {m: {"best": BATCH_VARIANTS[int(vmap[m - 1])], "ms": [round(v, 4) for v in ms[m]]} for m in mids}
+    return vmap, table
 
 
 def uniform_batch(a: torch.Tensor, b: torch.Tensor, variant_of_n=None) -> "Batch":

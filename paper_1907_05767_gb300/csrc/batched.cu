@@ -13,7 +13,9 @@
 //   U12 = L11^{-1} A12 are 64-wide tile products; A22 -= L21 U12 runs as
 //   register-tiled tiles; then the forward (LY = B) and backward (UX = Y)
 //   block substitutions of Eq. 1.
-// Variants: NB = 16 or 32 (per order, from the autotuner).
+// Variants (per order, from the autotuner): the block width NB (16 or 32;
+// 64 too in FP32) and the edge TM of the trailing update's output tiles (32
+// or 64; small systems waste less of a 32 x 32 tile).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -30,8 +32,18 @@ constexpr int BT = 256;              // threads per CTA
 constexpr int kMaxBatchOrder = 4096;  // largest order a system may have
 constexpr int kMaxBatchRhs = 64;
 constexpr int kSchedHeader = 8;
-constexpr int kNumVariants = 2;  // 0: NB = 16, 1: NB = 32
+// Variant id v: NB = 16 << (v % 3), TM = 64 >> (v / 3), so 0..2 are NB = 16,
+// 32, 64 with 64 x 64 tiles and 3..5 the same with 32 x 32 tiles.  NB = 64
+// (ids 2 and 5) is offered in FP32 only: in FP64 its shared memory would
+// leave one CTA per SM for every variant.
+constexpr int kNumVariants = 6;
 constexpr int kVariantShift = 28;
+__host__ __device__ constexpr int variant_nb(int v) { return 16 << (v % 3); }
+__host__ __device__ constexpr int variant_tm(int v) { return 64 >> (v / 3); }
+template <typename T>
+constexpr int max_nb() { return sizeof(T) == 4 ? 64 : 32; }
+template <typename T>
+bool variant_ok(int v) { return v >= 0 && v < kNumVariants && variant_nb(v) <= max_nb<T>(); }
 
 struct BatchArgs {
   const int32_t *n;
@@ -82,69 +94,93 @@ __device__ void warp_diag_factor(BatchSmem<T, NB> &sm, int w, int k0, int lane) 
     }
     __syncwarp();
   }
-  // Inverses of both factors (identity beyond w): lane c owns column c.
+}
+
+// Inverses of both triangles of the factored block (identity beyond w), one
+// warp each: warp 0 builds L11^{-1}, warp 1 U11^{-1}.  A lane owns columns
+// c = lane, lane + 32 and substitutes down (L) or up (U) its own column, so
+// lanes never wait on one another.
+template <typename T, int NB>
+__device__ void warp_tri_inverses(BatchSmem<T, NB> &sm, int w, int warp, int lane) {
+  if (warp > 1) return;
+  T(*Z)[NB + 1] = warp == 0 ? sm.Li : sm.Ui;
   for (int e = lane; e < NB * NB; e += 32) {
     const int i = e / NB, j = e % NB;
-    sm.Li[i][j] = sm.Ui[i][j] = (i == j) ? T(1) : T(0);
+    Z[i][j] = (i == j) ? T(1) : T(0);
   }
   __syncwarp();
-  for (int i = 1; i < w; ++i) {  // L^{-1}[i][c] = -(l_ic + sum_{c<k<i} l_ik L^{-1}[k][c])
-    if (lane < i && lane < NB) {
-      T s = sm.D[i][lane];
-      for (int k = lane + 1; k < i; ++k) s += sm.D[i][k] * sm.Li[k][lane];
-      sm.Li[i][lane] = -s;
+  for (int c = lane; c < w; c += 32) {
+    if (warp == 0) {  // L^{-1}[i][c] = -(l_ic + sum_{c<k<i} l_ik L^{-1}[k][c]), i = c+1 .. w-1
+      for (int i = c + 1; i < w; ++i) {
+        T s = sm.D[i][c];
+        for (int k = c + 1; k < i; ++k) s += sm.D[i][k] * Z[k][c];
+        Z[i][c] = -s;
+      }
+    } else {  // U^{-1}[i][c] = -(sum_{i<k<=c} u_ik U^{-1}[k][c]) / u_ii, i = c .. 0
+      Z[c][c] = sm.rcp[c];
+      for (int i = c - 1; i >= 0; --i) {
+        T s = T(0);
+        for (int k = i + 1; k <= c; ++k) s += sm.D[i][k] * Z[k][c];
+        Z[i][c] = -s * sm.rcp[i];
+      }
     }
-    __syncwarp();
   }
-  for (int i = w - 1; i >= 0; --i) {  // U^{-1}[i][c] = -(sum_{i<k<=c} u_ik U^{-1}[k][c]) / u_ii
-    const T rc = sm.rcp[i];
-    if (lane >= i && lane < w) {
-      T s = T(0);
-      for (int k = i + 1; k <= lane; ++k) s += sm.D[i][k] * sm.Ui[k][lane];
-      sm.Ui[i][lane] = (lane == i) ? rc : -s * rc;
-    }
-    __syncwarp();
-  }
+  __syncwarp();
 }
 
 // A22 -= L21 U12 for the m x m trailing block (rows/cols k0+w..n-1) of one
-// system, K = w: 64 x 64 output tiles, each thread a 4 x 4 register block.
-template <typename T, int NB>
+// system, K = w: TM x TM output tiles (TM = 64: a 4 x 4 register block per
+// thread; TM = 32: 2 x 2).  The K-slabs of L21 and U12 are read with
+// consecutive threads on consecutive addresses of a row (coalesced) and
+// stored transposed for L21; the tile of C is loaded into registers before
+// the slab products, so its latency overlaps them.
+template <typename T, int NB, int TM>
 __device__ void cta_trailing_update(BatchSmem<T, NB> &sm, T *A, int n, int k0, int w) {
+  constexpr int TT = TM / 16;  // outputs per thread along each dimension
   const int base = k0 + w, m = n - base;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  for (int ti = 0; ti < m; ti += 64) {
-    for (int tj = 0; tj < m; tj += 64) {
-      for (int e = threadIdx.x; e < NB * 64; e += BT) {
-        const int k = e / 64, x = e % 64;
-        const bool ok = k < w;
-        sm.As[k][x] = (ok && ti + x < m) ? A[(int64_t)(base + ti + x) * n + k0 + k] : T(0);
-        sm.Bs[k][x] = (ok && tj + x < m) ? A[(int64_t)(k0 + k) * n + base + tj + x] : T(0);
+  for (int ti = 0; ti < m; ti += TM) {
+    for (int tj = 0; tj < m; tj += TM) {
+      T c[TT][TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) {
+        const int i = ti + ty + 16 * q;
+#pragma unroll
+        for (int u = 0; u < TT; ++u) {
+          const int j = tj + tx + 16 * u;
+          c[q][u] = (i < m && j < m) ? A[(int64_t)(base + i) * n + base + j] : T(0);
+        }
+      }
+      for (int e = threadIdx.x; e < NB * TM; e += BT) {
+        const int x = e / NB, k = e % NB;  // L21: row x of the tile, k along the row
+        sm.As[k][x] = (k < w && ti + x < m) ? A[(int64_t)(base + ti + x) * n + k0 + k] : T(0);
+        const int kb = e / TM, xb = e % TM;  // U12: row kb, xb along the row
+        sm.Bs[kb][xb] = (kb < w && tj + xb < m) ? A[(int64_t)(k0 + kb) * n + base + tj + xb] : T(0);
       }
       __syncthreads();
-      T acc[4][4] = {};
+      T acc[TT][TT] = {};
 #pragma unroll 8
       for (int k = 0; k < NB; ++k) {
-        T ra[4], rb[4];
+        T ra[TT], rb[TT];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < TT; ++q) {
           ra[q] = sm.As[k][ty + 16 * q];
           rb[q] = sm.Bs[k][tx + 16 * q];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < TT; ++q)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[q][u] += ra[q] * rb[u];
+          for (int u = 0; u < TT; ++u) acc[q][u] += ra[q] * rb[u];
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < TT; ++q) {
         const int i = ti + ty + 16 * q;
         if (i >= m) continue;
         T *row = A + (int64_t)(base + i) * n + base;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < TT; ++u) {
           const int j = tj + tx + 16 * u;
-          if (j < m) row[j] -= acc[q][u];
+          if (j < m) row[j] = c[q][u] - acc[q][u];
         }
       }
       __syncthreads();
@@ -153,7 +189,7 @@ __device__ void cta_trailing_update(BatchSmem<T, NB> &sm, T *A, int n, int k0, i
 }
 
 // In-place LU (packed L\U) of one n x n system, then X = U^{-1} L^{-1} B.
-template <typename T, int NB>
+template <typename T, int NB, int TM>
 __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, int32_t *info) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) sm.bad = INT32_MAX;
@@ -166,6 +202,8 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
     }
     __syncthreads();
     if (warp == 0) warp_diag_factor<T, NB>(sm, w, k0, lane);
+    __syncthreads();
+    warp_tri_inverses<T, NB>(sm, w, warp, lane);
     __syncthreads();
     for (int e = threadIdx.x; e < w * w; e += BT) {
       const int i = e / w, j = e % w;
@@ -221,7 +259,7 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
           if (rg + 4 * q < w) A[(int64_t)(k0 + rg + 4 * q) * n + t0 + c] = out[q];
     }
     __syncthreads();
-    if (n - k0 - w > 0) cta_trailing_update<T, NB>(sm, A, n, k0, w);
+    if (n - k0 - w > 0) cta_trailing_update<T, NB, TM>(sm, A, n, k0, w);
     __syncthreads();
   }
   if (threadIdx.x == 0) *info = sm.bad == INT32_MAX ? 0 : sm.bad + 1;
@@ -279,7 +317,7 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
 // through a device counter until none is left.
 template <typename T>
 __global__ void __launch_bounds__(BT, 2) k_batched(BatchArgs args) {
-  extern __shared__ __align__(16) unsigned char smraw[];  // sizeof(BatchSmem<T, 32>)
+  extern __shared__ __align__(16) unsigned char smraw[];  // sizeof(BatchSmem<T, max_nb<T>()>)
   __shared__ int s_item;
   const int P = args.sched[0];
   for (;;) {
@@ -299,10 +337,22 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchArgs args) {
       }
       T *A = (T *)args.a[sys];
       T *B = (T *)args.b[sys];
-      if (variant == 0)
-        cta_lu_solve<T, 16>(*reinterpret_cast<BatchSmem<T, 16> *>(smraw), n, A, B, nrhs, &args.info[sys]);
-      else
-        cta_lu_solve<T, 32>(*reinterpret_cast<BatchSmem<T, 32> *>(smraw), n, A, B, nrhs, &args.info[sys]);
+      switch (variant) {
+        case 0: cta_lu_solve<T, 16, 64>(*reinterpret_cast<BatchSmem<T, 16> *>(smraw), n, A, B, nrhs, &args.info[sys]); break;
+        case 3: cta_lu_solve<T, 16, 32>(*reinterpret_cast<BatchSmem<T, 16> *>(smraw), n, A, B, nrhs, &args.info[sys]); break;
+        case 4: cta_lu_solve<T, 32, 32>(*reinterpret_cast<BatchSmem<T, 32> *>(smraw), n, A, B, nrhs, &args.info[sys]); break;
+        case 2:
+        case 5:
+          if constexpr (max_nb<T>() >= 64) {
+            if (variant == 2)
+              cta_lu_solve<T, 64, 64>(*reinterpret_cast<BatchSmem<T, 64> *>(smraw), n, A, B, nrhs, &args.info[sys]);
+            else
+              cta_lu_solve<T, 64, 32>(*reinterpret_cast<BatchSmem<T, 64> *>(smraw), n, A, B, nrhs, &args.info[sys]);
+            break;
+          }
+          [[fallthrough]];
+        default: cta_lu_solve<T, 32, 64>(*reinterpret_cast<BatchSmem<T, 32> *>(smraw), n, A, B, nrhs, &args.info[sys]); break;
+      }
       __syncthreads();
     }
   }
@@ -314,7 +364,7 @@ int default_variant(int n) { return n <= 64 ? 0 : 1; }
 template <typename T>
 int resident_ctas() {
   static const int r = [] {
-    constexpr int smem = (int)sizeof(BatchSmem<T, 32>);
+    constexpr int smem = (int)sizeof(BatchSmem<T, max_nb<T>()>);
     if (set_smem(k_batched<T>, smem) != cudaSuccess)
       return 0;
     int dev = 0, sms = 0, per_sm = 0;
@@ -333,7 +383,7 @@ ebv_status_t launch_batched(const BatchArgs &args, int items, cudaStream_t s) {
   if (resident <= 0) return EBV_ERR_CUDA;
   const int grid = std::min(items, resident);
   prof::Scope ps(s, prof::kBatched, 0.0);
-  k_batched<T><<<grid, BT, sizeof(BatchSmem<T, 32>), s>>>(args);
+  k_batched<T><<<grid, BT, sizeof(BatchSmem<T, max_nb<T>()>), s>>>(args);
   return launch_ok();
 }
 
@@ -355,6 +405,46 @@ __global__ void k_fill_dd(T *a, T *b, int n, int reps) {
   }
 }
 
+// Work items of a batch: Eq. 7's equalisation applied across systems.  The
+// systems are sorted by cost (2n^3/3 + 2n^2 nrhs flops, + 1 so that empty
+// systems still count); walking from the most expensive system down and from
+// the cheapest up, a short system joins a long one while the pair costs no
+// more than the single most expensive system, the time every CTA's work is
+// equalised towards.  Items come out in decreasing cost (stable: equal costs
+// keep the systems' order).  EBV_ERR_ARG for an order outside 0..4096 or a
+// right-hand-side count outside 0..64.
+struct Item {
+  double cost;
+  int32_t sys[2];  // the long system, and the short one or -1
+};
+
+ebv_status_t pair_systems(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host, std::vector<Item> &items) {
+  if (batch > 0 && (!n_host || !nrhs_host)) return EBV_ERR_ARG;
+  std::vector<double> cost((size_t)batch);
+  for (int64_t s = 0; s < batch; ++s) {
+    const int n = n_host[s], r = nrhs_host[s];
+    if (n < 0 || n > kMaxBatchOrder || r < 0 || r > kMaxBatchRhs) return EBV_ERR_ARG;
+    cost[s] = 2.0 * n * n * n / 3.0 + 2.0 * n * n * r + 1.0;
+  }
+  std::vector<int32_t> order((size_t)batch);
+  for (int64_t s = 0; s < batch; ++s) order[s] = (int32_t)s;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+  items.clear();
+  items.reserve((size_t)batch);
+  const double cap = batch > 0 ? cost[order[0]] : 0.0;
+  for (int64_t i = 0, j = batch - 1; i <= j; ++i) {
+    const int32_t lo = order[i];
+    if (j > i && cost[lo] + cost[order[j]] <= cap) {
+      const int32_t sh = order[j--];
+      items.push_back({cost[lo] + cost[sh], {lo, sh}});
+    } else {
+      items.push_back({cost[lo], {lo, -1}});
+    }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+  return EBV_OK;
+}
+
 }  // namespace
 }  // namespace ebv
 
@@ -369,48 +459,48 @@ size_t ebv_batch_workspace_size(int64_t) { return kStatusBytes; }
 ebv_status_t ebv_batch_schedule(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host,
                                 const int8_t *variant_of_n, int32_t *schedule_host) {
   if (batch < 0 || batch >= (int64_t(1) << kVariantShift) || !schedule_host) return EBV_ERR_ARG;
-  if (batch > 0 && (!n_host || !nrhs_host)) return EBV_ERR_ARG;
-  std::vector<double> cost((size_t)batch);
-  for (int64_t s = 0; s < batch; ++s) {
-    const int n = n_host[s], r = nrhs_host[s];
-    if (n < 0 || n > kMaxBatchOrder || r < 0 || r > kMaxBatchRhs) return EBV_ERR_ARG;
-    cost[s] = 2.0 * n * n * n / 3.0 + 2.0 * n * n * r + 1.0;
-  }
-  std::vector<int32_t> order((size_t)batch);
-  for (int64_t s = 0; s < batch; ++s) order[s] = (int32_t)s;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+  std::vector<Item> items;
+  EBV_TRY(pair_systems(batch, n_host, nrhs_host, items));
   auto code = [&](int32_t s) -> int32_t {
+    if (s < 0) return -1;
     const int n = n_host[s];
     int v = default_variant(n);
     if (variant_of_n && n >= 1 && variant_of_n[n - 1] >= 0 && variant_of_n[n - 1] < kNumVariants)
       v = variant_of_n[n - 1];
     return s | (v << kVariantShift);
   };
-  // Pair long with short (Eq. 7's equalisation, across systems): walking from
-  // the most expensive system down and from the cheapest up, a short system
-  // joins a long one while the pair costs no more than the single most
-  // expensive system, the time every CTA's work is equalised towards.
-  std::vector<std::pair<double, std::pair<int32_t, int32_t>>> items;
-  items.reserve((size_t)batch);
-  const double cap = batch > 0 ? cost[order[0]] : 0.0;
-  for (int64_t i = 0, j = batch - 1; i <= j; ++i) {
-    const int32_t lo = order[i];
-    if (j > i && cost[lo] + cost[order[j]] <= cap) {
-      const int32_t sh = order[j--];
-      items.push_back({cost[lo] + cost[sh], {code(lo), code(sh)}});
-    } else {
-      items.push_back({cost[lo], {code(lo), -1}});
-    }
-  }
   const int64_t P = (int64_t)items.size();
-  std::stable_sort(items.begin(), items.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
   std::memset(schedule_host, 0, sizeof(int32_t) * (size_t)ebv_batch_schedule_len(batch));
   schedule_host[0] = (int32_t)P;
   schedule_host[1] = (int32_t)batch;
   for (int64_t p = 0; p < P; ++p) {
-    schedule_host[kSchedHeader + 2 * p] = items[p].second.first;
-    schedule_host[kSchedHeader + 2 * p + 1] = items[p].second.second;
+    schedule_host[kSchedHeader + 2 * p] = code(items[p].sys[0]);
+    schedule_host[kSchedHeader + 2 * p + 1] = code(items[p].sys[1]);
   }
+  return EBV_OK;
+}
+
+ebv_status_t ebv_batch_partition(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host, int32_t nranks,
+                                 int32_t *rank_of_host, double *cost_of_rank_host) {
+  if (batch < 0 || batch >= (int64_t(1) << kVariantShift) || nranks < 1 || nranks > 65536) return EBV_ERR_ARG;
+  if (batch > 0 && !rank_of_host) return EBV_ERR_ARG;
+  std::vector<Item> items;
+  EBV_TRY(pair_systems(batch, n_host, nrhs_host, items));
+  // Longest processing time first: the items (long/short pairs, already in
+  // decreasing cost) go one by one to the rank with the least work so far,
+  // the lowest rank on ties.  No rank then ends more than one item's cost
+  // above the average.
+  std::vector<double> load((size_t)nranks, 0.0);
+  for (const Item &it : items) {
+    int32_t r = 0;
+    for (int32_t q = 1; q < nranks; ++q)
+      if (load[q] < load[r]) r = q;
+    load[r] += it.cost;
+    for (int h = 0; h < 2; ++h)
+      if (it.sys[h] >= 0) rank_of_host[it.sys[h]] = r;
+  }
+  if (cost_of_rank_host)
+    for (int32_t q = 0; q < nranks; ++q) cost_of_rank_host[q] = load[q];
   return EBV_OK;
 }
 
@@ -492,7 +582,12 @@ ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, int32_t re
     }
     float best = 0.f;
     int bestv = default_variant(n);
+    bool have = false;
     for (int v = 0; v < kNumVariants; ++v) {
+      if (!(prec == EBV_FP64 ? variant_ok<double>(v) : variant_ok<float>(v))) {
+        if (ms_host) ms_host[oi * kNumVariants + v] = -1.f;  // not offered in this precision
+        continue;
+      }
       std::fill(vmap.begin(), vmap.end(), (int8_t)v);
       ebv_batch_schedule(reps, hn.data(), hr.data(), vmap.data(), hs.data());
       cudaMemcpyAsync(sched, hs.data(), hs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
@@ -517,9 +612,10 @@ ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, int32_t re
       }
       if (status != EBV_OK) break;
       if (ms_host) ms_host[oi * kNumVariants + v] = tms;
-      if (v == 0 || tms < best) {
+      if (!have || tms < best) {
         best = tms;
         bestv = v;
+        have = true;
       }
     }
     best_variant_host[oi] = (int8_t)bestv;

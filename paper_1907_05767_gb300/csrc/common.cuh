@@ -80,20 +80,14 @@ __device__ __forceinline__ float to_float(double x) { return (float)x; }
 __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
 
-// Reciprocal of a pivot in the working precision, correctly rounded.  The
-// binary32 version stays on the FP32 pipe: on GB300 one FP64 division costs
-// several hundred cycles, which on the pivot's critical path dominated the
-// 64-step diagonal-block kernels.
+// Reciprocal of a pivot.  It is always formed in FP64 (the pivots'
+// reciprocals are among the few FP64 operations of the mixed-precision
+// paths); the binary32 factorisations round it once to binary32 and scale
+// their L vectors with it (Eq. 6a).  Measured on GB300: a dependent FP64
+// reciprocal of one warp takes about as long as the IEEE binary32 one (~88
+// cycles per pivot step), so the FP64 form costs nothing extra on the chain.
 __device__ __forceinline__ double pivot_rcp(double p) { return 1.0 / p; }
-__device__ __forceinline__ float pivot_rcp(float p) { return __frcp_rn(p); }
-// The same for the short pivot chains of the 16 x 16 warp factorisations:
-// binary32 uses the SFU reciprocal refined by one Newton step (error a few
-// ulp, within the FP32 factors' tolerance), off the IEEE-division slow path.
-__device__ __forceinline__ double pivot_rcp_fast(double p) { return 1.0 / p; }
-__device__ __forceinline__ float pivot_rcp_fast(float p) {
-  const float r = __fdividef(1.f, p);
-  return fmaf(r, fmaf(-p, r, 1.f), r);  // one Newton step: r (2 - p r)
-}
+__device__ __forceinline__ float pivot_rcp(float p) { return (float)(1.0 / (double)p); }
 // A zero or non-finite pivot (tested in the working precision).
 template <typename T>
 __device__ __forceinline__ bool pivot_bad(T p) { return !(p != T(0)) || !isfinite(p); }

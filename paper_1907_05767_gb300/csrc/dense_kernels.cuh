@@ -281,7 +281,7 @@ __device__ __forceinline__ void warp_lu16(T *D, int ld, int o, T *rcp, int w, in
     const int tr = r >> 2, gr = r & 3;
     const int ps = r < 8 ? r : kSB - 1 - r;  // pair holding column r
     const T pv = __shfl_sync(FULL, r < 8 ? v0[tr] : v1[tr], gr * 8 + ps);
-    const T rc = pivot_rcp_fast(pv);
+    const T rc = pivot_rcp(pv);
     if (c0 == r) rc0 = rc;
     if (c1 == r) rc1 = rc;
     if (first_bad == kSB && o + r < w && pivot_bad(pv)) first_bad = r;

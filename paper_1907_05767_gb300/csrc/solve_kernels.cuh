@@ -136,7 +136,14 @@ __device__ __forceinline__ bool xw_wait(const unsigned long long *p, uint32_t ta
 // X_s, in the order they were published, applies the diagonal-block inverse
 // (y = D_t^{-1} acc, a tile product) before block t-1 exists, and once X_{t-1}
 // is there only does X_t = y - (D_t^{-1} F(t,t-1)) X_{t-1}, then publishes
-// X_t (tagged words, above) and writes it to B.  Only the owner ever touches
+// X_t (tagged words, above) and writes it to B.
+// Rounding: the folds accumulate from zero and meet B_t once; the inverse's
+// off-diagonal part and the coupling product accumulate from zero too, and
+// the diagonal term D_t^{-1}(r, r) acc_r (of the size of the solution) joins
+// last.  Every small term is then rounded against small partial sums, and an
+// entry of X_t takes O(1) roundings at its own magnitude instead of one per
+// folded product (for n = 16384 that is 16k roundings against a value of
+// order 1, about 1e-14 of backward error).  Only the owner ever touches
 // block t of B, and a CTA never works on a later block while its current one
 // could advance, so the critical path per step is: X_{t-1}'s words seen ->
 // one 64 x 64 x RC product -> X_t stored.
@@ -210,6 +217,7 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n
   T(*Di)[DS] = reinterpret_cast<T(*)[DS]>(Fr + NS * NB * NB);                          // D_t^{-1}
   T(*Xs)[NB][RC + 1] = reinterpret_cast<T(*)[NB][RC + 1]>(Fr + NS * NB * NB + NB * DS);  // 2 x X_s
   T(*Ac)[RC + 1] = reinterpret_cast<T(*)[RC + 1]>(Fr + NS * NB * NB + NB * DS + 2 * NB * (RC + 1));
+  __shared__ T dg[NB];  // diagonal of D_t^{-1} (Di holds the rest, zero diagonal)
   if (st && st->done) return;  // refinement already converged
   const int nblk = ceil_div(n, NB);
   const int nchunk = ceil_div(nrhs, RC);
@@ -306,12 +314,16 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n
     // (the ring, Di, Xs and Ac are free: the previous block ended with a
     // barrier after its last use of them)
     for (int j = 0; j < NS - 1; ++j) tile(j);
-    stage_tile<NB, NT, DS>(&Di[0][0], [&](int r, int k) { return slot[(UPPER ? NB * NB : 0) + r * NB + k]; });
+    stage_tile<NB, NT, DS>(&Di[0][0], [&](int r, int k) {
+      return r == k ? T(0) : slot[(UPPER ? NB * NB : 0) + r * NB + k];
+    });
+    for (int r = threadIdx.x; r < NB; r += NT) dg[r] = slot[(UPPER ? NB * NB : 0) + r * NB + r];
     T acc[OPT];
 #pragma unroll
     for (int q = 0; q < OPT; ++q) {
       const int r = tr + PASS * q;
-      acc[q] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);
+      Ac[r][tc] = (r < hi && tc < wc) ? B[(i0 + r) * ldb + c0 + tc] : T(0);  // B_t, joined after the folds
+      acc[q] = T(0);
     }
     for (int j = 0; j < m; ++j) {
       const int s = sb + j;
@@ -331,9 +343,10 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n
       tile(j + NS - 1);  // into the stage every thread finished with before the barrier
       ring_fold<T, NB, RC, PASS, OPT>(Fr + (j % NS) * NB * NB, xs, tr, tc, acc);
     }
-    // y = D_t^{-1} acc, before block t-1 is needed.
+    // y = D_t^{-1} (B_t + acc), before block t-1 is needed: the off-diagonal
+    // part now, the diagonal term after the coupling product.
 #pragma unroll
-    for (int q = 0; q < OPT; ++q) Ac[tr + PASS * q][tc] = acc[q];
+    for (int q = 0; q < OPT; ++q) Ac[tr + PASS * q][tc] += acc[q];  // this thread's own entries
     __syncthreads();
     T y[OPT];
 #pragma unroll
@@ -364,6 +377,11 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n
       drain();
       if (__syncthreads_or(!ok)) return;
       ring_fold<T, NB, RC, PASS, OPT>(Fr + (m % NS) * NB * NB, xs, tr, tc, y);
+    }
+#pragma unroll
+    for (int q = 0; q < OPT; ++q) {
+      const int r = tr + PASS * q;
+      y[q] += dg[r] * Ac[r][tc];
     }
     const uint32_t tag = (uint32_t)t + 1;
 #pragma unroll

@@ -14,7 +14,6 @@
 // word, substitution flags, the refinement's column maxima) on every call.
 // Two calls whose work overlaps on the GPU (different streams, or different
 // host threads without ordering) race on the array.
-#include <atomic>
 #include <mutex>
 
 #include "internal.h"
@@ -32,25 +31,66 @@ constexpr size_t kStaticBytes = EBV_STATIC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
-std::atomic<void *> g_ws_ptr[kMaxDevices];
-std::mutex g_setup_mutex;
 
-// Device address of g_static_ws on the current device, looked up once per
-// device (the first call on a device does this).
+// The array's address belongs to the CUDA context that loaded this library's
+// module on the device: after cudaDeviceReset the primary context, and the
+// module in it, are made anew, and a caller may make a context of its own
+// current on the same device.  So the address is cached per device together
+// with the driver's unique ID of the context it was looked up in, and looked
+// up again whenever the current context's ID differs.
+struct Slot {
+  unsigned long long ctx_id = 0;  // 0: nothing cached
+  void *ptr = nullptr;
+};
+Slot g_slot[kMaxDevices];
+std::mutex g_mutex;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique ID of the current context (0 if there is none or it cannot be read).
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of g_static_ws in the current context of the current
+// device.  The first call in a context looks it up (cudaGetSymbolAddress,
+// which also makes the device's primary context current if none is); later
+// calls in the same context reuse it.
 ebv_status_t static_ws(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return EBV_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return EBV_ERR_UNSUPPORTED;
-  void *p = g_ws_ptr[dev].load(std::memory_order_acquire);
-  if (!p) {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    p = g_ws_ptr[dev].load(std::memory_order_relaxed);
-    if (!p) {
-      if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return EBV_ERR_CUDA;
-      g_ws_ptr[dev].store(p, std::memory_order_release);
-    }
+  std::lock_guard<std::mutex> lock(g_mutex);
+  Slot &slot = g_slot[dev];
+  unsigned long long id = current_ctx_id();
+  if (id == 0 || id != slot.ctx_id) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return EBV_ERR_CUDA;
+    id = current_ctx_id();  // the lookup may have made the primary context current
+    if (id == 0) return EBV_ERR_CUDA;
+    slot.ctx_id = id;
+    slot.ptr = p;
   }
-  *out = p;
+  *out = slot.ptr;
   return EBV_OK;
 }
 
