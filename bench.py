@@ -567,7 +567,37 @@ def run_configs(args):
     dev = torch.device("cuda")
     hbm = _peaks().get("hbm_gbs", 6800.0)
     out = []
+    names = set(str(args.configs).split(","))
 
+    def want(name):
+        return "all" in names or name in names
+
+    if want("dense256"):
+        out.append(_config_dense256(args, dev))
+    if want("band"):
+        out.extend(_config_band(args, dev))
+    if want("fp16"):
+        out.append(_config_fp16(args, dev))
+    if want("batched"):
+        out.extend(_config_batched(args, dev))
+    if want("adjoint"):
+        out.append(_config_adjoint(args, dev, hbm))
+    if want("inverse"):
+        out.append(run_inverse_config(args))
+    if want("profile"):
+        out.append(run_profile_config(args))
+    if want("band_mixed"):
+        out.append(run_band_mixed_config(args))
+    return out
+
+
+def _config_dense256(args, dev):
+    import torch
+
+    import oracle
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    out = []
     # n = 256 dense FP64, one RHS (L2-resident: the whole problem is 0.5 MB)
     a, x_true, b = synthetic.config0()
     n = a.shape[0]
@@ -582,19 +612,35 @@ def run_configs(args):
         ebv.ebv_factor(lu, "fp64", info=info, ws=ws)
         ebv.ebv_solve(lu, x, "fp64", ws=ws)
 
+    def c0_factor():
+        lu.copy_(A)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=ws)
+
+    ms_factor = _dev_ms(c0_factor, 200, 10)
     ms = _dev_ms(c0, 200, 10)
     x_ref = oracle.solve(oracle.lu(a)[0], b)
     xs = x.cpu().numpy()
     r = oracle.residual(a, xs, b)
-    out.append({"config": "dense FP64 n=256, 1 RHS", "ms": ms, "solves_per_s": 1e3 / ms,
+    out.append({"config": "dense FP64 n=256, 1 RHS", "ms": ms, "ms_factor_incl_copy": ms_factor,
+                "solves_per_s": 1e3 / ms,
                 "gflops": nominal_flops(n, 1) / (ms / 1e3) / 1e9,
                 "x_relerr_vs_oracle": float(np.abs(xs - x_ref).max() / np.abs(x_ref).max()),
                 "backward_error": float(np.abs(r).max() / (np.abs(a).sum(axis=1).max() * np.abs(xs).max())),
-                "note": "whole problem L2-resident; launch-latency bound (CUDA graph)"})
+                "note": "whole problem L2-resident (CUDA graph); factor on one thread-block cluster"})
     print(json.dumps(out[-1]), flush=True)
+    return out[-1]
 
-    # banded FP64 5-point Laplacian on a 512 x 512 grid, 8 RHS
-    ab, kl, ku, x_true, b = synthetic.config1()
+
+def _config_band(args, dev):
+    import torch
+
+    import oracle
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    out = []
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    # banded FP64 5-point Laplacian on a 512 x 512 grid (--band-grid), 8 RHS
+    ab, kl, ku, x_true, b = synthetic.config1(args.band_grid)
     n = ab.shape[0]
     AB, B = torch.from_numpy(ab).to(dev), torch.from_numpy(b).to(dev)
     lu, x = torch.empty_like(AB), torch.empty_like(B)
@@ -611,7 +657,8 @@ def run_configs(args):
     rows = synthetic.pick_indices(11, 512, [n])[:, 0]
     r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
     flops = 2.0 * n * kl * ku + 2.0 * n * (kl + ku) * b.shape[1]
-    out.append({"config": "band FP64 Laplacian 512x512 (n=262144, kl=ku=512), 8 RHS", "ms": ms,
+    g = args.band_grid
+    out.append({"config": f"band FP64 Laplacian {g}x{g} (n={n}, kl=ku={kl}), 8 RHS", "ms": ms,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
@@ -629,14 +676,48 @@ def run_configs(args):
     ms = _dev_ms(c1s, 3, 2)
     xs = x.cpu().numpy()
     r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
-    out.append({"config": "band FP64 Laplacian 512x512, symmetric storage mode, 8 RHS", "ms": ms,
+    out.append({"config": f"band FP64 Laplacian {g}x{g}, symmetric storage mode, 8 RHS", "ms": ms,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
                 "info": int(info.item())})
     print(json.dumps(out[-1]), flush=True)
-    del AB, B, lu, x, ws
+    del AB, lu, ws
 
+    # the same Laplacian with only the lower half of its band stored
+    # (EBV_BAND_SYM_LOWER: kl + 1 entries per row, the LDL^T factors in place)
+    ablo = np.ascontiguousarray(ab[:, :kl + 1])
+    ABL = torch.from_numpy(ablo).to(dev)
+    lul = torch.empty_like(ABL)
+    wsl = ebv.workspace(n, "fp64", b.shape[1], dev, ld=kl + 1, kl=kl, ku=ku, storage=ebv.BAND_SYM_LOWER)
+
+    def c1l():
+        lul.copy_(ABL)
+        x.copy_(B)
+        ebv.ebv_factor(lul, "fp64", info=info, ws=wsl, kl=kl, ku=ku, storage=ebv.BAND_SYM_LOWER)
+        ebv.ebv_solve(lul, x, "fp64", ws=wsl, kl=kl, ku=ku, storage=ebv.BAND_SYM_LOWER)
+
+    ms = _dev_ms(c1l, 3, 2)
+    xs = x.cpu().numpy()
+    r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
+    out.append({"config": f"band FP64 Laplacian {g}x{g}, symmetric, lower half of the band stored, 8 RHS",
+                "ms": ms,
+                "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
+                "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
+                "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
+                "band_bytes": int(ablo.nbytes), "band_bytes_full": int(ab.nbytes), "info": int(info.item())})
+    print(json.dumps(out[-1]), flush=True)
+    del ABL, lul, wsl, B, x
+    return out
+
+
+def _config_fp16(args, dev):
+    import torch
+
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    out = []
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
     # dense n = 16384, 32 RHS: FP16 updates + refinement (bf16 is the bench line)
     a, x_true, b = synthetic.config2(args.n, args.nrhs)
     n, nrhs = a.shape[0], b.shape[1]
@@ -660,18 +741,31 @@ def run_configs(args):
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max())})
     print(json.dumps(out[-1]), flush=True)
     del A, B, lowp, x, ws
+    return out[-1]
 
+
+def _config_batched(args, dev):
+    import torch
+
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    out = []
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
     # batched: 4096 systems, n ~ U{16..512}, 1-4 RHS, FP64 and FP32
     ns, rs = synthetic.config3_sizes()
     systems = [synthetic.config3_system(s, int(ns[s]), int(rs[s])) for s in range(len(ns))]
     flops = float(sum(nominal_flops(int(nn), int(rr)) for nn, rr in zip(ns, rs)))
     pick = synthetic.pick_indices(99, 16, [len(ns)])[:, 0]
     for prec in ("fp64", "fp32"):
-        bt = ebv.Batch(ns, rs, prec)
+        # the autotuner's variant per size bucket (block width x update tile)
+        vmap, tuned = ebv.batch_autotune_buckets(prec, cache_path=args.tune_cache)
+        bt = ebv.Batch(ns, rs, prec, variant_of_n=vmap)
         for s, (a, _, b) in enumerate(systems):
             bt.a_view(s).copy_(torch.from_numpy(a))
             bt.b_view(s).copy_(torch.from_numpy(b))
         a0, b0 = bt.a_buf.clone(), bt.b_buf.clone()
+        sched_tuned = bt.sched.clone()
+        sched_default = torch.from_numpy(ebv.ebv_batch_schedule(ns, rs)).to(dev)
 
         def restore():
             bt.a_buf.copy_(a0)
@@ -682,6 +776,9 @@ def run_configs(args):
             bt.run()
 
         ms_restore = _dev_ms(restore, 10, 3)
+        bt.sched = sched_default
+        ms_default = _dev_ms(c3, 10, 3) - ms_restore
+        bt.sched = sched_tuned
         ms_all = _dev_ms(c3, 10, 3)  # last: the buffers hold the factors and X
         err = 0.0
         for s in pick:
@@ -691,6 +788,7 @@ def run_configs(args):
         line = {"config": f"batched 4096 systems n~U{{16..512}}, 1-4 RHS, {prec}", "ms": ms_run,
                 "ms_incl_restore": ms_all, "solves_per_s": len(ns) * 1e3 / ms_run,
                 "gflops": flops / (ms_run / 1e3) / 1e9, "launches": 1,
+                "ms_default_variants": ms_default, "tuned_variants": tuned,
                 "err_vs_x_true_sampled": err, "info_max": int(bt.info.abs().max())}
         if prec == "fp64":
             # the same systems one at a time through ebv_factor + ebv_solve
@@ -711,7 +809,15 @@ def run_configs(args):
         print(json.dumps(out[-1]), flush=True)
         del bt, a0, b0
     del systems
+    return out
 
+
+def _config_adjoint(args, dev, hbm):
+    import torch
+
+    import oracle
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
     # differentiable batch: 256 FP64 systems n = 1024, 4 RHS; forward + adjoint
     nb, n, nrhs = 256, 1024, 4
     data = [synthetic.config4_system(i, n, nrhs) for i in range(nb)]
@@ -743,16 +849,13 @@ def run_configs(args):
     # bytes: each triangle of the factors read once, grad_A written
     bwd_flops = nb * 4.0 * n * n * nrhs
     bwd_bytes = nb * 8.0 * n * n * 2
-    out.append({"config": "adjoint batch 256 x FP64 n=1024, 4 RHS", "ms_forward": ms_f - ms_copy,
+    line = {"config": "adjoint batch 256 x FP64 n=1024, 4 RHS", "ms_forward": ms_f - ms_copy,
                 "ms_backward": ms_b, "forward_gflops": nb * nominal_flops(n, nrhs) / ((ms_f - ms_copy) / 1e3) / 1e9,
                 "backward_gflops_fp64": bwd_flops / (ms_b / 1e3) / 1e9,
                 "backward_gbs": bwd_bytes / (ms_b / 1e3) / 1e9, "backward_hbm_frac": bwd_bytes / (ms_b / 1e3) / 1e9 / hbm,
-                "grad_relerr_vs_oracle_sampled": err, "info_max": int(bt.info.abs().max())})
-    print(json.dumps(out[-1]), flush=True)
-    out.append(run_inverse_config(args))
-    out.append(run_profile_config(args))
-    out.append(run_band_mixed_config(args))
-    return out
+                "grad_relerr_vs_oracle_sampled": err, "info_max": int(bt.info.abs().max())}
+    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_band_mixed_config(args):
@@ -955,11 +1058,13 @@ def main():
                    help="time the other workloads (one JSON line each) and exit; --configs inverse / profile / band_mixed: "
                         "one alone")
     p.add_argument("--inverse-n", type=int, default=8192, help="order of the explicit-inverse workload")
+    p.add_argument("--band-grid", type=int, default=512, help="grid edge of the banded Laplacian workload")
     p.add_argument("--workload", default="dense", choices=["dense", "batched"],
                    help="batched: the 4096-system batch split across the ranks (one JSON line)")
     p.add_argument("--batched-prec", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--autotune", action="store_true", help="batched: tuned variant per size bucket")
-    p.add_argument("--tune-cache", default=None, help="batched: JSON cache of the autotuner")
+    p.add_argument("--tune-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "ebv_batch_autotune.json"),
+                   help="JSON cache of the batched autotuner (keyed by GPU, precision and repetitions)")
     args = p.parse_args()
     if args.update_only:
         print(json.dumps(run_update_only(args)), flush=True)

@@ -92,11 +92,22 @@ typedef enum {
  * ebv_solve treats both alike.  (Project addition: the LDL^T reading of the
  * method for symmetric diagonally dominant systems.)
  */
-typedef enum { EBV_DENSE = 0, EBV_BAND = 1, EBV_BAND_SYM = 2 } ebv_storage_t;
+/*
+ * EBV_BAND_SYM_LOWER: a symmetric A stored as the lower half of its band
+ * only, kl + 1 entries per row: a_ij at ab[i*ld + (j - i + kl)] for
+ * i - kl <= j <= i, ld >= kl + 1, ku == kl (half the memory of EBV_BAND_SYM).
+ * ebv_factor leaves the LDL^T form in the same array: L strictly below the
+ * diagonal (unit diagonal implied) and the pivots d_i = u_ii on it, since
+ * U = D L^T.  ebv_solve takes the factors in that storage.  The factorisation
+ * runs its panels on a thread-block cluster (EBV_ERR_UNSUPPORTED on a device
+ * that cannot, or with ebv_debug_set_cluster_panel(0)).  (Project addition,
+ * the LDL^T reading of Eq. 6a-b with both its flops and its storage halved.)
+ */
+typedef enum { EBV_DENSE = 0, EBV_BAND = 1, EBV_BAND_SYM = 2, EBV_BAND_SYM_LOWER = 3 } ebv_storage_t;
 
 typedef struct ebv_desc {
   int64_t n;       /* order of A, n >= 0 */
-  int64_t ld;      /* row stride in elements (dense: >= n; band: >= kl+ku+1) */
+  int64_t ld;      /* row stride in elements (dense: >= n; band: >= kl+ku+1; lower half: >= kl+1) */
   int64_t kl, ku;  /* band widths, 0 <= kl, ku < n (ignored for EBV_DENSE) */
   int32_t storage; /* ebv_storage_t */
   int32_t reserved;
@@ -148,7 +159,7 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *             non-finite pivot.  Always written.
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
- * Band storage (EBV_BAND, EBV_BAND_SYM) supports every precision (the mixed ones as above);
+ * Band storage (EBV_BAND, EBV_BAND_SYM, EBV_BAND_SYM_LOWER) supports every precision (the mixed ones as above);
  * fill-in stays inside the band because no rows are exchanged.  A band whose width varies row by row
  * (a profile, or skyline, matrix stored in its widest band) costs the work of
  * its profile: the factorisation first finds each 64-block's envelope and
@@ -257,7 +268,7 @@ EBV_API ebv_status_t ebv_batch_autotune(const int32_t *orders, int32_t count, in
  * and the pivot scaling.  For many right-hand sides that arrive one by one
  * (X B is one matrix product), not for single solves (ebv_solve is cheaper
  * and more accurate).
- *   desc  dense storage only (EBV_BAND, EBV_BAND_SYM: EBV_ERR_UNSUPPORTED);
+ *   desc  dense storage only (band storages: EBV_ERR_UNSUPPORTED);
  *         n and the factors' leading dimension ld.
  *   prec  EBV_FP64 (lu and x binary64) or EBV_FP32 (binary32: the factors of
  *         ebv_factor with EBV_FP32, or the binary32 lowp factors of a
@@ -374,7 +385,19 @@ EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, c
 EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
 
 /*
- * Testing hook: the banded factorisation (EBV_BAND, EBV_BAND_SYM) first finds
+ * Testing hook: panels of the banded factorisation (a 64-column panel with
+ * its kl rows below and ku columns right) and whole dense FP64 / FP32
+ * systems of order <= 256 are factored by one launch on a thread-block
+ * cluster of up to 16 CTAs (the panel's columns paired long with short over
+ * the CTAs, Eq. 7; the pivot column passed through distributed shared
+ * memory).  enable = 0 runs the one-CTA diagonal-block kernels and separate
+ * L21 / U12 launches instead (the results agree to rounding).
+ * Process-wide, default on.
+ */
+EBV_API void ebv_debug_set_cluster_panel(int32_t enable);
+
+/*
+ * Testing hook: the banded factorisation (every band storage) first finds
  * the block envelope of A -- per 64-block, the first non-zero left of the
  * diagonal over the block's rows and above it over its columns -- and skips
  * the L21, U12 and trailing-update tiles that lie outside it (no row exchanges,

@@ -34,7 +34,7 @@ OK, ERR_ARG, ERR_ZERO_PIVOT, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_
 # ebv_prec_t
 FP64, FP32, MIXED_BF16, MIXED_FP16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
-DENSE, BAND, BAND_SYM = 0, 1, 2
+DENSE, BAND, BAND_SYM, BAND_SYM_LOWER = 0, 1, 2, 3
 
 
 class EbvError(RuntimeError):
@@ -89,6 +89,7 @@ _SIGNATURES = [
     ("ebv_solve_adjoint", _I32, [_I64, _I64, _I64, _VP, _I64, _I64, _VP, _VP, _VP, _VP, _VP]),
     ("ebv_debug_set_lowp_gemm", None, [_I32]),
     ("ebv_debug_set_band_envelope", None, [_I32]),
+    ("ebv_debug_set_cluster_panel", None, [_I32]),
     ("ebv_debug_residual", _I32, [_I64, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     ("ebv_debug_lowp_update", _I32, [_I32, _I32, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _I64, _I64, _I64, _I64, _I64,
                                      _VP, _VP]),
@@ -376,22 +377,27 @@ def inverse(f: Factors) -> torch.Tensor:
     return ebv_inverse(f.lu, prec=FP64 if f.prec == FP64 else FP32)
 
 
-def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64", sym: bool = False) -> Factors:
-    """Factor a row-band matrix (n x (kl+ku+1)).  sym: A is symmetric (kl == ku,
-    both halves stored); U is formed from L and the pivots (EBV_BAND_SYM).
-    Mixed precisions: FP32 factors of the FP64 band in a new tensor, for
-    refined solves to FP64 accuracy."""
+def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64", sym=False) -> Factors:
+    """Factor a row-band matrix.  sym=False: A general, ab is n x (kl+ku+1).
+    sym=True: A symmetric (kl == ku, both halves stored); U is formed from L
+    and the pivots (EBV_BAND_SYM).  sym="lower": A symmetric with only the
+    lower half stored, ab n x (kl+1) (EBV_BAND_SYM_LOWER); the factors keep
+    that storage (L below the diagonal, the pivots on it).  Mixed precisions:
+    FP32 factors of the FP64 band in a new tensor, for refined solves to FP64
+    accuracy."""
     p = _prec(prec)
-    storage = BAND_SYM if sym else BAND
+    lower = isinstance(sym, str) and sym == "lower"
+    storage = BAND_SYM_LOWER if lower else (BAND_SYM if sym else BAND)
+    solve_storage = BAND_SYM_LOWER if lower else BAND
     if p in (MIXED_BF16, MIXED_FP16):
         a64 = ab.to(torch.float64).contiguous()
         lowp = torch.empty(a64.shape, dtype=torch.float32, device=a64.device)
         info = ebv_factor(a64, p, lowp=lowp, kl=kl, ku=ku, storage=storage)
-        return Factors(lowp, info, p, a64, kl, ku, BAND)
+        return Factors(lowp, info, p, a64, kl, ku, solve_storage)
     dt = torch.float64 if p == FP64 else torch.float32
     lu = ab.to(dt).clone().contiguous()
     info = ebv_factor(lu, p, kl=kl, ku=ku, storage=storage)
-    return Factors(lu, info, p, ab.to(torch.float64).contiguous(), kl, ku, BAND)
+    return Factors(lu, info, p, ab.to(torch.float64).contiguous(), kl, ku, solve_storage)
 
 
 def debug_residual(a: torch.Tensor, x: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
@@ -524,6 +530,7 @@ def batch_autotune(orders, prec="fp64", reps=16, device="cuda", cache_path=None)
             entry[str(o)] = {"best": int(best[i]), "ms": [float(v) for v in ms[i * nv:(i + 1) * nv]]}
         cache[key] = entry
         if cache_path:
+            os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
             with open(cache_path, "w") as fh:
                 json.dump(cache, fh, indent=1, sort_keys=True)
     tuned = sorted((int(k), v["best"]) for k, v in entry.items())

@@ -39,11 +39,11 @@ ebv_status_t check_desc(const ebv_desc_t *d, ebv_prec_t prec) {
   if (d->n < 0 || d->n > kMaxN) return EBV_ERR_ARG;
   if (d->storage == EBV_DENSE) {
     if (d->ld < std::max<int64_t>(1, d->n)) return EBV_ERR_ARG;
-  } else if (d->storage == EBV_BAND || d->storage == EBV_BAND_SYM) {
+  } else if (d->storage == EBV_BAND || d->storage == EBV_BAND_SYM || d->storage == EBV_BAND_SYM_LOWER) {
     if (d->kl < 0 || d->ku < 0) return EBV_ERR_ARG;
-    if (d->storage == EBV_BAND_SYM && d->kl != d->ku) return EBV_ERR_ARG;
+    if (d->storage != EBV_BAND && d->kl != d->ku) return EBV_ERR_ARG;
     if (d->n > 0 && (d->kl >= d->n || d->ku >= d->n)) return EBV_ERR_ARG;
-    if (d->ld < d->kl + d->ku + 1) return EBV_ERR_ARG;
+    if (d->ld < (d->storage == EBV_BAND_SYM_LOWER ? d->kl + 1 : d->kl + d->ku + 1)) return EBV_ERR_ARG;
   } else {
     return EBV_ERR_ARG;
   }
@@ -140,6 +140,9 @@ ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu
   if (!ws || !aligned(ws, 256) || ws_bytes < inverse_ws(n, prec)) return EBV_ERR_WORKSPACE;
   return inverse(n, prec, lu, desc->ld, x, ldx, ws, (cudaStream_t)stream);
 }
+
+// Testing hook: 0 = panels never run on a thread-block cluster.
+void ebv_debug_set_cluster_panel(int32_t enable) { set_cluster_panel(enable != 0); }
 
 // Testing hook: 0 = the banded factorisation ignores the block envelope.
 void ebv_debug_set_band_envelope(int32_t enable) { set_band_envelope(enable != 0); }

@@ -95,15 +95,47 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
     env.lo = env_lo;
     env.up = env_up;
   }
+  // Panels on a thread-block cluster (diagonal block, L21 and U12 in one
+  // launch) when the band's panel fits the kernel's shared memory.
+  bool cluster = cluster_panel_enabled() &&
+                 cluster_panel_fits(sizeof(T) == 8, kNB, std::min<int64_t>(n, kNB + A.kl), sym ? 0 : A.ku);
+  // Lower-half storage of a symmetric band: the one-CTA leaf kernels read the
+  // unfactored upper half through the view, which there means d_i l_ji, so
+  // only the cluster panel (which reads a_ji) can factor it.
+  if (A.symlo && !cluster) return EBV_ERR_UNSUPPORTED;
   for (int64_t c0 = 0; c0 < n; c0 += kNB) {
     const int w = (int)std::min<int64_t>(kNB, n - c0);
+    const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
+    const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
+    if (cluster) {
+      const ebv_status_t st = cluster_panel(sizeof(T) == 8, A.base, A.ld, A.kl, A.ku, A.symlo, c0, w, re - c0,
+                                            sym ? 0 : ce - cb, info, s);
+      if (st == EBV_ERR_UNSUPPORTED && c0 == 0 && !A.symlo) {
+        cluster = false;  // the device cannot run the cluster: one-CTA kernels from here on
+      } else {
+        EBV_TRY(st);
+        // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
+        if (ce > cb && sym && !A.symlo) {
+          prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
+          k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
+          EBV_TRY(launch_ok());
+        }
+        if (re > rb && ce > cb) {
+          prof::Scope ps(s, prof::kSimtGemm, 2.0 * (re - rb) * (ce - cb) * w);
+          dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
+          k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
+              <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0,
+                                                                  env);
+          EBV_TRY(launch_ok());
+        }
+        continue;
+      }
+    }
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
       k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, inv);
       EBV_TRY(launch_ok());
     }
-    const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
-    const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
     // FP64: 16-row / 16-column strips, four times the CTAs of one 64 x 64
     // tile each (a band has only kl rows / ku columns per step).
     if (re > rb) {
@@ -143,10 +175,12 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
 
 // R = B - A X for a row-band A, multi-word binary32 accumulation as in the
 // dense residual.  One warp per row; the lanes stride over the row's band.
+// symlo: ab holds the lower half of a symmetric band (ku = kl); a_ij above
+// the diagonal is read as a_ji.
 __global__ void __launch_bounds__(256)
-    k_band_residual_df(const double *ab, int64_t ldab, int64_t n, int64_t kl, int64_t ku, const float *xhi,
-                       const float *xlo, int nrhs, const double *B, int64_t ldb, double *R, int64_t ldr,
-                       unsigned long long *rmax, const DevStatus *st) {
+    k_band_residual_df(const double *ab, int64_t ldab, int64_t n, int64_t kl, int64_t ku, bool symlo,
+                       const float *xhi, const float *xlo, int nrhs, const double *B, int64_t ldb, double *R,
+                       int64_t ldr, unsigned long long *rmax, const DevStatus *st) {
   if (st && st->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -157,7 +191,7 @@ __global__ void __launch_bounds__(256)
     acc.zero();
     for (int64_t j = j0 + lane; j <= j1; j += 32) {
       float a_h, a_l;
-      split_f64(ab[i * ldab + (j - i + kl)], a_h, a_l);
+      split_f64((symlo && j > i) ? ab[j * ldab + (i - j + kl)] : ab[i * ldab + (j - i + kl)], a_h, a_l);
       acc.fma_split(a_h, a_l, xhi[j * nrhs + c], xlo[j * nrhs + c]);
     }
     // Error-free (up to the l words) warp reduction of the triples.
@@ -198,12 +232,11 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
   if (!ws || ws_bytes < band_factor_ws(d->n, d->kl, d->ku, prec)) return EBV_ERR_WORKSPACE;
   char *inv = (char *)ws + kStatusBytes;
   int32_t *env = (int32_t *)(inv + band_inv_bytes(prec));
-  const bool sym = d->storage == EBV_BAND_SYM;
-  if (prec == EBV_FP64)
-    return band_factor_t<double>(band_view((double *)a, d->ld, d->kl, d->ku), d->n, info, (double *)inv, env, sym,
-                                 s);
-  if (prec == EBV_FP32)
-    return band_factor_t<float>(band_view((float *)a, d->ld, d->kl, d->ku), d->n, info, (float *)inv, env, sym, s);
+  const bool lower = d->storage == EBV_BAND_SYM_LOWER;
+  const bool sym = d->storage == EBV_BAND_SYM || lower;
+  auto view = [&](auto *p) { return lower ? symlo_view(p, d->ld, d->kl) : band_view(p, d->ld, d->kl, d->ku); };
+  if (prec == EBV_FP64) return band_factor_t<double>(view((double *)a), d->n, info, (double *)inv, env, sym, s);
+  if (prec == EBV_FP32) return band_factor_t<float>(view((float *)a), d->n, info, (float *)inv, env, sym, s);
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
     // FP32 factors of the FP64 band in lowp (same layout); a stays untouched
     // for the refinement's residual.  The band's updates run in FP32 SIMT.
@@ -211,8 +244,7 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
     k_band_narrow<<<(unsigned)std::min<int64_t>(4096, (count + 255) / 256), 256, 0, s>>>((const double *)a,
                                                                                          (float *)lowp, count);
     EBV_TRY(launch_ok());
-    return band_factor_t<float>(band_view((float *)lowp, d->ld, d->kl, d->ku), d->n, info, (float *)inv, env, sym,
-                                s);
+    return band_factor_t<float>(view((float *)lowp), d->n, info, (float *)inv, env, sym, s);
   }
   return EBV_ERR_UNSUPPORTED;
 }
@@ -222,6 +254,7 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
                         size_t ws_bytes, cudaStream_t s) {
   const int64_t n = d->n;
   const bool fp64 = prec == EBV_FP64;
+  const bool lower = d->storage == EBV_BAND_SYM_LOWER;
   const DenseSolveLayout L = solve_layout(n, nrhs, fp64 ? 8 : 4);
   if (!ws || ws_bytes < L.total) return EBV_ERR_WORKSPACE;
   EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
@@ -231,19 +264,17 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
     k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldx, n, (int)nrhs, xhi, xlo, st);
     EBV_TRY(launch_ok());
     prof::Scope ps(s, prof::kResidual, 2.0 * n * (d->kl + d->ku + 1) * nrhs);
-    k_band_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(a_orig, d->ld, n, d->kl, d->ku, xhi, xlo, (int)nrhs, bs,
-                                                       nrhs, r, nrhs, rmax, st);
+    k_band_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(a_orig, d->ld, n, d->kl, d->ku, lower, xhi, xlo, (int)nrhs,
+                                                       bs, nrhs, r, nrhs, rmax, st);
     return launch_ok();
   };
+  auto view = [&](auto *p) { return lower ? symlo_view(p, d->ld, d->kl) : band_view(p, d->ld, d->kl, d->ku); };
   if (fp64)
-    return solve_refined<double>(band_view((double *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
-                                 (char *)ws, L, true, residual, s);
+    return solve_refined<double>(view((double *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, residual, s);
   if (prec == EBV_FP32)
-    return solve_refined<float>(band_view((float *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
-                                (char *)ws, L, false, residual, s);
+    return solve_refined<float>(view((float *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, false, residual, s);
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16)  // FP32 factors, FP64 right-hand sides and solution
-    return solve_refined<float>(band_view((float *)lu, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
-                                (char *)ws, L, true, residual, s);
+    return solve_refined<float>(view((float *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, residual, s);
   return EBV_ERR_UNSUPPORTED;
 }
 

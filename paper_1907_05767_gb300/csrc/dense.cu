@@ -454,6 +454,12 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   char *w = (char *)ws;
   DevStatus *dst = (DevStatus *)ws;
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
+  if ((prec == EBV_FP64 || prec == EBV_FP32) && n <= kClusterDenseMaxN) {
+    // A small system whole on one thread-block cluster (one launch).
+    const ebv_status_t st =
+        cluster_panel(prec == EBV_FP64, a, d->ld, kDenseBand, kDenseBand, false, 0, (int)n, n, 0, info, s);
+    if (st != EBV_ERR_UNSUPPORTED) return st;
+  }
   if (prec == EBV_FP64) {
     EBV_TRY((prepare_leaf_kernels<double, float>()));
     Factorizer<double, float> f{dense_view((double *)a, d->ld), n, info, s, none, -1, dst, (double *)(w + L.inv)};

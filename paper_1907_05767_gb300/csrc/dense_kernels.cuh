@@ -16,18 +16,28 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // elements outside that band read as 0 and are never written.  A dense matrix
 // uses a huge band.  A row-band array ab (a_ij at ab[i*ldab + j-i+kl]) is the
 // view base = ab + kl, ld = ldab - 1.
+// symlo: the factors of a symmetric band kept in its lower half only (L
+// strictly below the diagonal, the pivots d on it; kl = ku): the U entries
+// are read as u_ij = d_i l_ji (U = D L^T, the LDL^T form of Eq. 6a-b) and
+// writes above the diagonal are dropped.
 template <typename T>
 struct MatView {
   T *base;
   int64_t ld;
   int64_t kl, ku;
+  bool symlo = false;
   __device__ __forceinline__ bool in(int64_t i, int64_t j) const {
     const int64_t d = j - i;
     return d >= -kl && d <= ku;
   }
-  __device__ __forceinline__ T get(int64_t i, int64_t j) const { return in(i, j) ? base[i * ld + j] : T(0); }
+  __device__ __forceinline__ T get(int64_t i, int64_t j) const {
+    if (!in(i, j)) return T(0);
+    if (symlo && j > i) return base[j * ld + i] * base[i * ld + i];
+    return base[i * ld + j];
+  }
+  __device__ __forceinline__ bool writable(int64_t i, int64_t j) const { return in(i, j) && !(symlo && j > i); }
   __device__ __forceinline__ void put(int64_t i, int64_t j, T v) const {
-    if (in(i, j)) base[i * ld + j] = v;
+    if (writable(i, j)) base[i * ld + j] = v;
   }
 };
 
@@ -55,6 +65,11 @@ inline MatView<T> dense_view(T *a, int64_t ld) { return MatView<T>{a, ld, kDense
 template <typename T>
 inline MatView<T> band_view(T *ab, int64_t ldab, int64_t kl, int64_t ku) {
   return MatView<T>{ab + kl, ldab - 1, kl, ku};
+}
+// The lower half of a symmetric band (a_ij at ab[i*ldab + j-i+kl], j <= i).
+template <typename T>
+inline MatView<T> symlo_view(T *ab, int64_t ldab, int64_t kl) {
+  return MatView<T>{ab + kl, ldab - 1, kl, kl, true};
 }
 
 // Stage an NB x NB tile into shared memory (row stride S) with all of the
@@ -1369,7 +1384,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
     for (int b = 0; b < TN; ++b) {
       const int64_t gj = bn + tx + b * NTX;
-      if (gj < nend && A.in(gi, gj)) {
+      if (gj < nend && A.writable(gi, gj)) {
         T *c = A.base + gi * A.ld + gj;
         *c = *c - acc[a][b];
       }

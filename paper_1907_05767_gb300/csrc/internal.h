@@ -34,6 +34,22 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
                         int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
                         size_t ws_bytes, cudaStream_t s);
 
+// Panel factorisation on a thread-block cluster (cluster_panel.cu): the W
+// columns [c0, c0+W) of rows [c0, c0+R) factored (packed L\U of the diagonal
+// block and L21), and U12 = L11^{-1} A12 formed in place for the U columns
+// right of the panel, on the view base[i*ld + j] (zero outside -kl..ku).
+// EBV_ERR_UNSUPPORTED when the shape does not fit the kernel or the device
+// cannot run the cluster (the caller then uses the one-CTA leaf kernels).
+// symlo: only the lower half of a symmetric band is stored (U must be 0).
+bool cluster_panel_fits(bool fp64, int W, int64_t R, int64_t U);
+ebv_status_t cluster_panel(bool fp64, void *base, int64_t ld, int64_t kl, int64_t ku, bool symlo, int64_t c0, int W,
+                           int64_t R, int64_t U, int32_t *info, cudaStream_t s);
+// Testing hook: false = never use the cluster panel kernel.
+void set_cluster_panel(bool on);
+bool cluster_panel_enabled();
+// Orders up to which a dense FP64 / FP32 factorisation is one cluster panel.
+constexpr int64_t kClusterDenseMaxN = 256;
+
 // Product-form inverse (Eq. 4c) from packed dense factors (inverse.cu).
 size_t inverse_ws(int64_t n, ebv_prec_t prec);
 ebv_status_t inverse(int64_t n, ebv_prec_t prec, const void *lu, int64_t ldl, void *x, int64_t ldx, void *ws,

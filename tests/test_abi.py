@@ -107,6 +107,20 @@ def test_workspace_sizes(lib):
     assert lib.ebv_workspace_size(ctypes.byref(d), ebv.FP64, 0) == 0
 
 
+def test_band_storage_descriptors(lib):
+    # general band: ld >= kl + ku + 1; both symmetric storages need kl == ku;
+    # the lower half only needs ld >= kl + 1
+    def ok(n, ld, kl, ku, storage):
+        d = ebv._desc(n, ld, kl, ku, storage)
+        return lib.ebv_workspace_size(ctypes.byref(d), ebv.FP64, 1) > 0
+    assert ok(100, 9, 3, 5, ebv.BAND) and not ok(100, 8, 3, 5, ebv.BAND)
+    assert ok(100, 9, 4, 4, ebv.BAND_SYM) and not ok(100, 9, 3, 5, ebv.BAND_SYM)
+    assert ok(100, 5, 4, 4, ebv.BAND_SYM_LOWER) and not ok(100, 4, 4, 4, ebv.BAND_SYM_LOWER)
+    assert not ok(100, 9, 3, 5, ebv.BAND_SYM_LOWER)
+    assert not ok(100, 9, 100, 100, ebv.BAND_SYM_LOWER)  # kl < n
+    assert not ok(100, 100, 0, 0, 4)  # no such storage
+
+
 def test_inverse_argument_errors(lib):
     n = 100
     need = lib.ebv_inverse_workspace_size(n, ebv.FP64)

@@ -110,6 +110,21 @@ def test_batched_matches_oracle(prec):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+def test_batched_each_variant_matches_oracle(variant, prec):
+    # every block width (16, 32, 64 in FP32) and tile edge (64, 32), on orders
+    # that leave ragged blocks and tiles; in FP64 ids 2 and 5 run as id 1
+    ns = [1, 7, 31, 40, 77, 129, 150, 300]
+    rs = [1, 2, 1, 1, 3, 2, 4, 1]
+    batch = ebv.Batch(ns, rs, prec, variant_of_n=np.full(4096, variant, dtype=np.int8))
+    data = fill(batch, 322_000 + variant, w=0.9)
+    batch.run()
+    for s, (a, b) in enumerate(data):
+        check_system(batch, s, a, b, prec)
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("variant", [0, 1])
 def test_batched_each_variant(variant):
     ns = [7, 40, 77, 150]
@@ -173,9 +188,26 @@ def test_batched_config3_sampled_and_graph_replay():
 
 
 @pytest.mark.gpu
-def test_autotune_returns_valid_variants(tmp_path):
-    vmap, ms = ebv.batch_autotune([16, 100, 300], "fp32", reps=8, cache_path=str(tmp_path / "tune.json"))
-    assert vmap.shape == (4096,) and set(np.unique(vmap).tolist()) <= {0, 1}
-    assert set(ms) == {16, 100, 300} and all(len(v) == 2 and min(v) > 0 for v in ms.values())
-    vmap2, _ = ebv.batch_autotune([16, 100, 300], "fp32", reps=8, cache_path=str(tmp_path / "tune.json"))
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotune_returns_valid_variants(tmp_path, prec):
+    vmap, ms = ebv.batch_autotune([16, 100, 300], prec, reps=8, cache_path=str(tmp_path / "tune.json"))
+    offered = {0, 1, 2, 3, 4, 5} if prec == "fp32" else {0, 1, 3, 4}
+    assert vmap.shape == (4096,) and set(np.unique(vmap).tolist()) <= offered
+    assert set(ms) == {16, 100, 300}
+    for v in ms.values():  # a time for every offered variant, -1 for the others
+        assert len(v) == 6
+        assert all((t > 0) == (i in offered) for i, t in enumerate(v))
+    # the chosen variant is the fastest one timed
+    for o, v in ms.items():
+        assert v[vmap[o - 1]] == min(t for t in v if t > 0)
+    vmap2, _ = ebv.batch_autotune([16, 100, 300], prec, reps=8, cache_path=str(tmp_path / "tune.json"))
     assert np.array_equal(vmap, vmap2)  # served from the cache
+
+
+@pytest.mark.gpu
+def test_autotune_buckets_cover_the_batched_orders(tmp_path):
+    vmap, table = ebv.batch_autotune_buckets("fp32", reps=16, cache_path=str(tmp_path / "tune.json"))
+    assert sorted(table) == [32, 64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384, 416, 448, 480, 512]
+    for mid, row in table.items():  # every order of a bucket takes its middle order's choice
+        assert row["best"] == ebv.BATCH_VARIANTS[int(vmap[mid - 1])]
+    assert vmap[16 - 1] == vmap[32 - 1] and vmap[47 - 1] == vmap[32 - 1]
