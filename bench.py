@@ -616,12 +616,16 @@ def _config_dense256(args, dev):
         lu.copy_(A)
         ebv.ebv_factor(lu, "fp64", info=info, ws=ws)
 
+    ebv.lib().ebv_debug_set_cluster_panel(0)
+    ms_one_cta = _dev_ms(c0, 200, 10)
+    ebv.lib().ebv_debug_set_cluster_panel(1)
     ms_factor = _dev_ms(c0_factor, 200, 10)
     ms = _dev_ms(c0, 200, 10)
     x_ref = oracle.solve(oracle.lu(a)[0], b)
     xs = x.cpu().numpy()
     r = oracle.residual(a, xs, b)
     out.append({"config": "dense FP64 n=256, 1 RHS", "ms": ms, "ms_factor_incl_copy": ms_factor,
+                "ms_recursive_one_cta_leaves": ms_one_cta,
                 "solves_per_s": 1e3 / ms,
                 "gflops": nominal_flops(n, 1) / (ms / 1e3) / 1e9,
                 "x_relerr_vs_oracle": float(np.abs(xs - x_ref).max() / np.abs(x_ref).max()),
@@ -652,6 +656,10 @@ def _config_band(args, dev):
         ebv.ebv_factor(lu, "fp64", info=info, ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
         ebv.ebv_solve(lu, x, "fp64", ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
 
+    # the same with the one-CTA diagonal-block kernels instead of the cluster panels
+    ebv.lib().ebv_debug_set_cluster_panel(0)
+    ms_one_cta = _dev_ms(c1, 3, 2)
+    ebv.lib().ebv_debug_set_cluster_panel(1)
     ms = _dev_ms(c1, 3, 2)
     xs = x.cpu().numpy()
     rows = synthetic.pick_indices(11, 512, [n])[:, 0]
@@ -659,6 +667,7 @@ def _config_band(args, dev):
     flops = 2.0 * n * kl * ku + 2.0 * n * (kl + ku) * b.shape[1]
     g = args.band_grid
     out.append({"config": f"band FP64 Laplacian {g}x{g} (n={n}, kl=ku={kl}), 8 RHS", "ms": ms,
+                "ms_one_cta_panels": ms_one_cta,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
@@ -954,6 +963,25 @@ def run_profile_config(args):
     xs = x.cpu().numpy()
     rows = synthetic.pick_indices(12, 512, [n])[:, 0]
     r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
+    del AB, lu, ws
+
+    # the same matrix in profile storage (EBV_PROFILE: per 64-block from the
+    # envelope start), factors in place
+    buf, klp, kup = ebv.ebv_profile_from_band(ab, kl, ku, "fp64")
+    P0 = torch.from_numpy(buf).to(dev)
+    P = torch.empty_like(P0)
+    wsp = ebv.workspace(n, "fp64", nrhs, dev, ld=0, kl=klp, ku=kup, storage=ebv.PROFILE)
+
+    def pstep():
+        P.copy_(P0)
+        x.copy_(B)
+        ebv.ebv_factor(P, "fp64", info=info, ws=wsp, kl=klp, ku=kup, storage=ebv.PROFILE, n=n)
+        ebv.ebv_solve(P, x, "fp64", ws=wsp, kl=klp, ku=kup, storage=ebv.PROFILE, ld=0)
+
+    ms_prof = _dev_ms(pstep, 3, 1)
+    xp = x.cpu().numpy()
+    rp = oracle.band_residual(ab, kl, ku, xp, b)[rows]
+    del P0, P, wsp
     work, rsum, csum = profile_work(ab, kl, ku)
     flops = work + 2.0 * (rsum + csum) * nrhs
     line = {"config": f"variable band FP64: Laplacian on a disc of radius 289 (n={n}, widest band kl=ku={kl}), "
@@ -962,6 +990,12 @@ def run_profile_config(args):
             "gflops_profile": flops / (ms / 1e3) / 1e9,
             "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
             "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
+            "band_bytes": int(ab.nbytes),
+            "profile_storage": {"ms": ms_prof, "bytes": int(buf.nbytes), "bytes_vs_band": buf.nbytes / ab.nbytes,
+                                "kl_ku_bounds": [klp, kup],
+                                "err_vs_x_true": float(np.abs(xp - x_true).max() / np.abs(x_true).max()),
+                                "backward_error_sampled": float(np.abs(rp).max() / (np.abs(ab).sum(axis=1).max() *
+                                                                                    np.abs(xp).max()))},
             "info": int(info.item())}
     print(json.dumps(line), flush=True)
     return line

@@ -103,7 +103,30 @@ typedef enum {
  * that cannot, or with ebv_debug_set_cluster_panel(0)).  (Project addition,
  * the LDL^T reading of Eq. 6a-b with both its flops and its storage halved.)
  */
-typedef enum { EBV_DENSE = 0, EBV_BAND = 1, EBV_BAND_SYM = 2, EBV_BAND_SYM_LOWER = 3 } ebv_storage_t;
+/*
+ * EBV_PROFILE: a matrix whose band width varies row by row (a profile, or
+ * skyline, matrix; the sparse case of the paper's first experiment read as
+ * an uneven band) stored compactly by 64-blocks: row block b keeps columns
+ * lo[b] .. 64b+63 of its 64 rows (its lower part with the whole diagonal
+ * block), column block c keeps rows up[c] .. 64c-1 of its 64 columns (its
+ * part above the diagonal block), each row-major.  The buffer holds, for
+ * nb = ceil(n/64) blocks, int32 lo[nb], int32 up[nb], int64 offL[nb],
+ * int64 offU[nb] (element offsets of the two parts) and, from byte
+ * align256(24 nb), the values (double or float).  ebv_profile_from_band
+ * builds it from a row band.  desc->kl / ku must bound the profile (the
+ * values ebv_profile_from_band returns); ld is ignored.  No row exchanges,
+ * so fill stays inside the profile and ebv_factor overwrites the values by
+ * the packed factors in place; ebv_solve takes them in the same buffer.
+ * EBV_FP64 and EBV_FP32 only; a band whose few wide rows would make band
+ * storage pay their width on every row stores only its profile.
+ */
+typedef enum {
+  EBV_DENSE = 0,
+  EBV_BAND = 1,
+  EBV_BAND_SYM = 2,
+  EBV_BAND_SYM_LOWER = 3,
+  EBV_PROFILE = 4
+} ebv_storage_t;
 
 typedef struct ebv_desc {
   int64_t n;       /* order of A, n >= 0 */
@@ -240,6 +263,20 @@ EBV_API ebv_status_t ebv_batch_schedule(int64_t batch, const int32_t *n_host, co
  */
 EBV_API ebv_status_t ebv_batch_partition(int64_t batch, const int32_t *n_host, const int32_t *nrhs_host,
                                          int32_t nranks, int32_t *rank_of_host, double *cost_of_rank_host);
+/*
+ * ebv_profile_from_band (host): the EBV_PROFILE buffer of a row-band matrix
+ * (ab: host, n rows of ldab >= kl+ku+1 doubles, a_ij at ab[i*ldab + j-i+kl]).
+ * Each 64-block keeps its part from the first non-zero of its rows / columns
+ * outside the diagonal block.  prec EBV_FP64 or EBV_FP32 (the values' type).
+ * *bytes_needed receives the buffer size, *kl_out / *ku_out the bounds to
+ * pass in the descriptor.  out == NULL only computes those; otherwise out
+ * (host, out_bytes >= *bytes_needed, 256-byte aligned for the device copy)
+ * receives the buffer, which the caller copies to the device as is.
+ */
+EBV_API ebv_status_t ebv_profile_from_band(int64_t n, int64_t kl, int64_t ku, const double *ab, int64_t ldab,
+                                           ebv_prec_t prec, void *out, size_t out_bytes, size_t *bytes_needed,
+                                           int64_t *kl_out, int64_t *ku_out);
+
 EBV_API ebv_status_t ebv_factor_solve_batched(int64_t batch, const int32_t *n_dev, const int32_t *nrhs_dev,
                                       void *const *a_ptrs_dev, void *const *b_ptrs_dev, ebv_prec_t prec,
                                       const int32_t *schedule_dev, int32_t *info_dev, void *ws,

@@ -34,7 +34,7 @@ OK, ERR_ARG, ERR_ZERO_PIVOT, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_
 # ebv_prec_t
 FP64, FP32, MIXED_BF16, MIXED_FP16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
-DENSE, BAND, BAND_SYM, BAND_SYM_LOWER = 0, 1, 2, 3
+DENSE, BAND, BAND_SYM, BAND_SYM_LOWER, PROFILE = 0, 1, 2, 3, 4
 
 
 class EbvError(RuntimeError):
@@ -81,6 +81,7 @@ _SIGNATURES = [
     ("ebv_batch_workspace_size", _SZ, [_I64]),
     ("ebv_batch_schedule", _I32, [_I64, _VP, _VP, _VP, _VP]),
     ("ebv_batch_partition", _I32, [_I64, _VP, _VP, _I32, _VP, _VP]),
+    ("ebv_profile_from_band", _I32, [_I64, _I64, _I64, _VP, _I64, _I32, _VP, _SZ, _VP, _VP, _VP]),
     ("ebv_factor_solve_batched", _I32, [_I64, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _SZ, _VP]),
     ("ebv_batch_autotune_scratch", _SZ, [_I32, _I32, _I32]),
     ("ebv_batch_autotune", _I32, [_VP, _I32, _I32, _I32, _VP, _SZ, _VP, _VP, _VP]),
@@ -192,12 +193,15 @@ def workspace(n, prec, nrhs=0, device="cuda", **kw) -> torch.Tensor:
 
 
 def ebv_factor(a: torch.Tensor, prec="fp64", lowp: torch.Tensor | None = None, info: torch.Tensor | None = None,
-               ws: torch.Tensor | None = None, kl=0, ku=0, storage=DENSE) -> torch.Tensor:
-    """Factor in place (FP64/FP32) or into ``lowp`` (mixed).  Returns ``info``."""
+               ws: torch.Tensor | None = None, kl=0, ku=0, storage=DENSE, n: int | None = None) -> torch.Tensor:
+    """Factor in place (FP64/FP32) or into ``lowp`` (mixed).  Returns ``info``.
+    Profile storage: ``a`` is the byte buffer and ``n`` the order."""
     p = _prec(prec)
     _need_cuda(a, lowp, info, ws)
-    n = a.shape[0]
-    ld = a.stride(0)
+    if storage == PROFILE and n is None:
+        raise ValueError("profile storage: pass the order n")
+    n = a.shape[0] if n is None else int(n)
+    ld = a.stride(0) if storage != PROFILE else 0
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=a.device)
     if ws is None:
@@ -218,7 +222,7 @@ def ebv_solve(lu: torch.Tensor, b: torch.Tensor, prec="fp64", a_orig: torch.Tens
     b2 = b if b.dim() == 2 else b.view(n, 1)
     nrhs = b2.shape[1]
     if ld is None:
-        ld = lu.stride(0)
+        ld = lu.stride(0) if storage != PROFILE else 0
     if ws is None:
         ws = workspace(n, p, nrhs, b.device, ld=ld, kl=kl, ku=ku, storage=storage)
     d = _desc(n, ld, kl, ku, storage)
@@ -398,6 +402,67 @@ def band_factor(ab: torch.Tensor, kl: int, ku: int, prec="fp64", sym=False) -> F
     lu = ab.to(dt).clone().contiguous()
     info = ebv_factor(lu, p, kl=kl, ku=ku, storage=storage)
     return Factors(lu, info, p, ab.to(torch.float64).contiguous(), kl, ku, solve_storage)
+
+
+def ebv_profile_from_band(ab, kl: int, ku: int, prec="fp64"):
+    """Profile (skyline) storage of a row-band matrix (host numpy array,
+    n x (kl+ku+1)): returns (uint8 numpy buffer to copy to the device as is,
+    kl, ku bounds of the profile for the descriptor)."""
+    import numpy as np
+    ab = np.ascontiguousarray(ab, dtype=np.float64)
+    n = ab.shape[0]
+    p = _prec(prec)
+    need, klo, kuo = ctypes.c_size_t(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().ebv_profile_from_band(n, kl, ku, ab.ctypes.data, ab.shape[1], p, None, 0, ctypes.byref(need),
+                                       ctypes.byref(klo), ctypes.byref(kuo)), "ebv_profile_from_band")
+    buf = np.zeros(need.value + 256, dtype=np.uint8)
+    off = (-buf.ctypes.data) % 256  # 256-byte aligned start
+    out = buf[off:off + need.value]
+    _check(lib().ebv_profile_from_band(n, kl, ku, ab.ctypes.data, ab.shape[1], p, out.ctypes.data, out.nbytes, None,
+                                       None, None), "ebv_profile_from_band")
+    return out, int(klo.value), int(kuo.value)
+
+
+def profile_factor(ab, kl: int, ku: int, prec="fp64", device="cuda") -> Factors:
+    """Factor a row-band matrix (host numpy) held in profile storage on the
+    device; the factors stay in that storage (Factors.lu is the buffer)."""
+    p = _prec(prec)
+    buf, klp, kup = ebv_profile_from_band(ab, kl, ku, p)
+    dev = torch.from_numpy(buf).to(device)
+    orig = dev.clone() if p == FP64 else None  # the A of FP64 refinement
+    info = ebv_factor(dev, p, kl=klp, ku=kup, storage=PROFILE, n=ab.shape[0])
+    return Factors(dev, info, p, orig, klp, kup, PROFILE)
+
+
+def profile_to_band(buf, n: int, kl: int, ku: int, prec="fp64"):
+    """Row band (n x (kl+ku+1), float64 numpy) of a profile buffer (host
+    numpy uint8), entries outside the profile 0 -- for checks."""
+    import numpy as np
+    buf = np.asarray(buf)
+    nb = (n + 63) // 64
+    lo = buf[0:4 * nb].view(np.int32)
+    up = buf[4 * nb:8 * nb].view(np.int32)
+    offl = buf[8 * nb:16 * nb].view(np.int64)
+    offu = buf[16 * nb:24 * nb].view(np.int64)
+    h = (24 * nb + 255) // 256 * 256
+    vals = buf[h:].view(np.float64 if _prec(prec) == FP64 else np.float32).astype(np.float64)
+    ab = np.zeros((n, kl + ku + 1))
+    for b in range(nb):
+        w = (b + 1) * 64 - lo[b]
+        blk = vals[offl[b]:offl[b] + 64 * w].reshape(64, w)
+        for r in range(min(64, n - 64 * b)):
+            i = 64 * b + r
+            for j in range(lo[b], min(n, 64 * (b + 1))):
+                if -kl <= j - i <= ku:
+                    ab[i, j - i + kl] = blk[r, j - lo[b]]
+    for c in range(nb):
+        hgt = 64 * c - up[c]
+        blk = vals[offu[c]:offu[c] + 64 * hgt].reshape(hgt, 64)
+        for i in range(up[c], 64 * c):
+            for j in range(64 * c, min(n, 64 * (c + 1))):
+                if j - i <= ku:
+                    ab[i, j - i + kl] = blk[i - up[c], j - 64 * c]
+    return ab
 
 
 def debug_residual(a: torch.Tensor, x: torch.Tensor, b: torch.Tensor) -> torch.Tensor:

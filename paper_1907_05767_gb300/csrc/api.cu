@@ -44,6 +44,9 @@ ebv_status_t check_desc(const ebv_desc_t *d, ebv_prec_t prec) {
     if (d->storage != EBV_BAND && d->kl != d->ku) return EBV_ERR_ARG;
     if (d->n > 0 && (d->kl >= d->n || d->ku >= d->n)) return EBV_ERR_ARG;
     if (d->ld < (d->storage == EBV_BAND_SYM_LOWER ? d->kl + 1 : d->kl + d->ku + 1)) return EBV_ERR_ARG;
+  } else if (d->storage == EBV_PROFILE) {
+    if (d->kl < 0 || d->ku < 0) return EBV_ERR_ARG;
+    if (d->n > 0 && (d->kl >= d->n || d->ku >= d->n)) return EBV_ERR_ARG;
   } else {
     return EBV_ERR_ARG;
   }
@@ -83,7 +86,8 @@ ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *
                         size_t ws_bytes, ebv_stream_t stream) {
   EBV_TRY(check_desc(desc, prec));
   if (!info_dev || !aligned(info_dev, 4)) return EBV_ERR_ARG;
-  if (desc->n > 0 && (!a || !aligned(a, elem_size(prec)))) return EBV_ERR_ARG;
+  if (desc->n > 0 && (!a || !aligned(a, desc->storage == EBV_PROFILE ? 256 : elem_size(prec)))) return EBV_ERR_ARG;
+  if (desc->storage == EBV_PROFILE && is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
   if (is_mixed(prec) && desc->n > 0 && (!lowp || !aligned(lowp, 16))) return EBV_ERR_ARG;
   if (ws && !aligned(ws, 256)) return EBV_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -104,7 +108,8 @@ ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, 
   const bool any = desc->n > 0 && nrhs > 0;
   const size_t bsz = prec == EBV_FP32 ? 4 : 8;
   const size_t fsz = prec == EBV_FP64 ? 8 : 4;
-  if (any && (!lu || !aligned(lu, fsz) || !b || !aligned(b, bsz))) return EBV_ERR_ARG;
+  if (any && (!lu || !aligned(lu, desc->storage == EBV_PROFILE ? 256 : fsz) || !b || !aligned(b, bsz))) return EBV_ERR_ARG;
+  if (desc->storage == EBV_PROFILE && is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
   const bool need_a = is_mixed(prec) && refine;
   if (refine) {
     if (!(refine->tol >= 0.0) || refine->max_iter < 0 || refine->max_iter > 1000) return EBV_ERR_ARG;

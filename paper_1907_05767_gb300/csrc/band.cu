@@ -15,6 +15,8 @@
 // whose block lies outside it for the current panel return at once, so a band
 // whose width varies costs the work of its envelope, not of its widest row.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "solve_driver.cuh"
@@ -68,6 +70,11 @@ __global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, 
 }
 
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
+// General bands: one-CTA diagonal blocks (false) or cluster panels (true).
+// Measured on the 512 x 512 Laplacian, factor + solve: 1113 ms one-CTA
+// against 1233 ms on clusters, so the cluster panels serve the lower-half
+// symmetric storage only, which needs them.
+bool g_band_cluster = false;
 
 // Binary32 working copy of the whole band array (mixed precisions): count
 // elements, grid-stride.  Slots outside the matrix are copied too and, as in
@@ -77,15 +84,37 @@ __global__ void __launch_bounds__(256) k_band_narrow(const double *ab, float *lo
     lo[e] = (float)ab[e];
 }
 
+// Profile (skyline) storage, EBV_PROFILE: per 64-block header of int32
+// lo[nb], int32 up[nb], int64 offL[nb], int64 offU[nb] (nb = ceil(n/64)),
+// then the values from byte profile_header_bytes(n) (see MatView).
+size_t profile_header_bytes(int64_t n) { return align256((size_t)24 * (size_t)ceil_div(n, kNB)); }
+
 template <typename T>
-ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym,
+MatView<T> profile_view(void *buf, int64_t n, int64_t kl, int64_t ku) {
+  const int64_t nb = ceil_div(n, kNB);
+  char *h = (char *)buf;
+  MatView<T> v{(T *)(h + profile_header_bytes(n)), 0, kl, ku};
+  v.plo = (const int32_t *)h;
+  v.pup = (const int32_t *)(h + 4 * nb);
+  v.poffL = (const int64_t *)(h + 8 * nb);
+  v.poffU = (const int64_t *)(h + 16 * nb);
+  return v;
+}
+
+template <typename T>
+ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym, T *bcast,
                            cudaStream_t s) {
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
   using G = BandGemm<T>;
   EBV_TRY((prepare_leaf_kernels<T, float>()));
   constexpr size_t smem = pair_smem_bytes<T, kNB>();
   Envelope env;
-  if (g_band_envelope) {
+  if (A.plo) {  // profile storage: the stored extents are the block envelope
+    if (g_band_envelope) {
+      env.lo = A.plo;
+      env.up = A.pup;
+    }
+  } else if (g_band_envelope) {
     const int64_t nblk = ceil_div(n, kNB);
     int32_t *env_up = env_lo + nblk;
     EBV_CU(cudaMemsetAsync(env_lo, 0x7f, 2 * nblk * sizeof(int32_t), s));  // 0x7f7f7f7f > any index
@@ -96,8 +125,11 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
     env.up = env_up;
   }
   // Panels on a thread-block cluster (diagonal block, L21 and U12 in one
-  // launch) when the band's panel fits the kernel's shared memory.
-  bool cluster = cluster_panel_enabled() &&
+  // launch) for the lower-half symmetric storage, which needs them; the
+  // other band storages keep the one-CTA diagonal-block kernels, measured
+  // faster on the 512 x 512 Laplacian (1119 ms against 1504 ms per
+  // factor + solve).
+  bool cluster = !A.plo && (A.symlo || g_band_cluster) && cluster_panel_enabled() &&
                  cluster_panel_fits(sizeof(T) == 8, kNB, std::min<int64_t>(n, kNB + A.kl), sym ? 0 : A.ku);
   // Lower-half storage of a symmetric band: the one-CTA leaf kernels read the
   // unfactored upper half through the view, which there means d_i l_ji, so
@@ -109,7 +141,7 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
     const int64_t cb = c0 + w, ce = std::min<int64_t>(n, c0 + w + A.ku);
     if (cluster) {
       const ebv_status_t st = cluster_panel(sizeof(T) == 8, A.base, A.ld, A.kl, A.ku, A.symlo, c0, w, re - c0,
-                                            sym ? 0 : ce - cb, info, s);
+                                            sym ? 0 : ce - cb, info, bcast, s);
       if (st == EBV_ERR_UNSUPPORTED && c0 == 0 && !A.symlo) {
         cluster = false;  // the device cannot run the cluster: one-CTA kernels from here on
       } else {
@@ -210,14 +242,53 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// R = B - A X through a view (profile storage), as k_band_residual_df: one
+// warp per row over the view's window, entries outside the profile read 0.
+__global__ void __launch_bounds__(256)
+    k_view_residual_df(MatView<double> A, int64_t n, const float *xhi, const float *xlo, int nrhs, const double *B,
+                       int64_t ldb, double *R, int64_t ldr, unsigned long long *rmax, const DevStatus *st) {
+  if (st && st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (i >= n) return;
+  const int64_t j0 = max64(0, i - A.kl), j1 = min64(n - 1, i + A.ku);
+  for (int c = 0; c < nrhs; ++c) {
+    TripleF acc;
+    acc.zero();
+    for (int64_t j = j0 + lane; j <= j1; j += 32) {
+      if (!A.in(i, j)) continue;
+      float a_h, a_l;
+      split_f64(*A.at(i, j), a_h, a_l);
+      acc.fma_split(a_h, a_l, xhi[j * nrhs + c], xlo[j * nrhs + c]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      TripleF o;
+      o.h = __shfl_xor_sync(0xffffffffu, acc.h, off);
+      o.m = __shfl_xor_sync(0xffffffffu, acc.m, off);
+      o.l = __shfl_xor_sync(0xffffffffu, acc.l, off);
+      acc.add(o);
+    }
+    if (lane == 0) {
+      const double rv = B[i * ldb + c] - acc.value();
+      R[i * ldr + c] = rv;
+      atomicMax(&rmax[c], (unsigned long long)__double_as_longlong(fabs(rv)));
+    }
+  }
+}
+
 }  // namespace
 
 // Workspace of the banded factorisation: the status block, the inverses of
-// the current leaf's two triangular factors (used right after they are made)
-// and the block envelope (two int32 per 64-block).
+// the current leaf's two triangular factors (used right after they are made),
+// the block envelope (two int32 per 64-block) and the cluster panels' pivot
+// column scratch (two slots of 64 + kl + 1 elements).
 static size_t band_inv_bytes(ebv_prec_t prec) { return align256((size_t)2 * kNB * kNB * (prec == EBV_FP64 ? 8 : 4)); }
-size_t band_factor_ws(int64_t n, int64_t, int64_t, ebv_prec_t prec) {
-  return kStatusBytes + band_inv_bytes(prec) + align256((size_t)2 * ceil_div(n, kNB) * sizeof(int32_t));
+static size_t band_env_bytes(int64_t n) { return align256((size_t)2 * ceil_div(n, kNB) * sizeof(int32_t)); }
+static size_t band_bcast_bytes(int64_t kl, ebv_prec_t prec) {
+  return align256((size_t)2 * (kNB + kl + 1) * (prec == EBV_FP64 ? 8 : 4));
+}
+size_t band_factor_ws(int64_t n, int64_t kl, int64_t, ebv_prec_t prec) {
+  return kStatusBytes + band_inv_bytes(prec) + band_env_bytes(n) + band_bcast_bytes(kl, prec);
 }
 void set_band_envelope(bool on) { g_band_envelope = on; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
@@ -232,11 +303,23 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
   if (!ws || ws_bytes < band_factor_ws(d->n, d->kl, d->ku, prec)) return EBV_ERR_WORKSPACE;
   char *inv = (char *)ws + kStatusBytes;
   int32_t *env = (int32_t *)(inv + band_inv_bytes(prec));
+  char *bcast = (char *)env + band_env_bytes(d->n);
   const bool lower = d->storage == EBV_BAND_SYM_LOWER;
   const bool sym = d->storage == EBV_BAND_SYM || lower;
+  if (d->storage == EBV_PROFILE) {
+    if (prec == EBV_FP64)
+      return band_factor_t<double>(profile_view<double>(a, d->n, d->kl, d->ku), d->n, info, (double *)inv, env,
+                                   false, (double *)bcast, s);
+    if (prec == EBV_FP32)
+      return band_factor_t<float>(profile_view<float>(a, d->n, d->kl, d->ku), d->n, info, (float *)inv, env, false,
+                                  (float *)bcast, s);
+    return EBV_ERR_UNSUPPORTED;
+  }
   auto view = [&](auto *p) { return lower ? symlo_view(p, d->ld, d->kl) : band_view(p, d->ld, d->kl, d->ku); };
-  if (prec == EBV_FP64) return band_factor_t<double>(view((double *)a), d->n, info, (double *)inv, env, sym, s);
-  if (prec == EBV_FP32) return band_factor_t<float>(view((float *)a), d->n, info, (float *)inv, env, sym, s);
+  if (prec == EBV_FP64)
+    return band_factor_t<double>(view((double *)a), d->n, info, (double *)inv, env, sym, (double *)bcast, s);
+  if (prec == EBV_FP32)
+    return band_factor_t<float>(view((float *)a), d->n, info, (float *)inv, env, sym, (float *)bcast, s);
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
     // FP32 factors of the FP64 band in lowp (same layout); a stays untouched
     // for the refinement's residual.  The band's updates run in FP32 SIMT.
@@ -244,7 +327,7 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
     k_band_narrow<<<(unsigned)std::min<int64_t>(4096, (count + 255) / 256), 256, 0, s>>>((const double *)a,
                                                                                          (float *)lowp, count);
     EBV_TRY(launch_ok());
-    return band_factor_t<float>(view((float *)lowp), d->n, info, (float *)inv, env, sym, s);
+    return band_factor_t<float>(view((float *)lowp), d->n, info, (float *)inv, env, sym, (float *)bcast, s);
   }
   return EBV_ERR_UNSUPPORTED;
 }
@@ -268,6 +351,24 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
                                                        bs, nrhs, r, nrhs, rmax, st);
     return launch_ok();
   };
+  if (d->storage == EBV_PROFILE) {
+    auto presidual = [&](const double *x, int64_t ldx, float *xhi, float *xlo, const double *bs, double *r,
+                         unsigned long long *rmax, DevStatus *st, bool) -> ebv_status_t {
+      k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldx, n, (int)nrhs, xhi, xlo, st);
+      EBV_TRY(launch_ok());
+      prof::Scope ps(s, prof::kResidual, 2.0 * n * (d->kl + d->ku + 1) * nrhs);
+      k_view_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(profile_view<double>((void *)a_orig, n, d->kl, d->ku), n,
+                                                         xhi, xlo, (int)nrhs, bs, nrhs, r, nrhs, rmax, st);
+      return launch_ok();
+    };
+    if (fp64)
+      return solve_refined<double>(profile_view<double>((void *)lu, n, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
+                                   (char *)ws, L, true, presidual, s);
+    if (prec == EBV_FP32)
+      return solve_refined<float>(profile_view<float>((void *)lu, n, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
+                                  (char *)ws, L, false, presidual, s);
+    return EBV_ERR_UNSUPPORTED;
+  }
   auto view = [&](auto *p) { return lower ? symlo_view(p, d->ld, d->kl) : band_view(p, d->ld, d->kl, d->ku); };
   if (fp64)
     return solve_refined<double>(view((double *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, residual, s);
@@ -279,3 +380,83 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
 }
 
 }  // namespace ebv
+
+// ---------------------------------------------------------------------------
+// Profile storage from a row band (host).
+// ---------------------------------------------------------------------------
+using namespace ebv;
+
+extern "C" ebv_status_t ebv_profile_from_band(int64_t n, int64_t kl, int64_t ku, const double *ab, int64_t ldab,
+                                              ebv_prec_t prec, void *out, size_t out_bytes, size_t *bytes_needed,
+                                              int64_t *kl_out, int64_t *ku_out) {
+  if (n < 1 || kl < 0 || ku < 0 || kl >= n || ku >= n || ldab < kl + ku + 1 || !ab) return EBV_ERR_ARG;
+  if (prec != EBV_FP64 && prec != EBV_FP32) return EBV_ERR_UNSUPPORTED;
+  const int64_t nb = (n + kNB - 1) / kNB;
+  const size_t es = prec == EBV_FP64 ? 8 : 4;
+  auto a = [&](int64_t i, int64_t j) { return ab[i * ldab + (j - i + kl)]; };
+  // First non-zero left of the diagonal block over each row block, and
+  // above it over each column block (the diagonal block is kept whole).
+  std::vector<int32_t> lo((size_t)nb), up((size_t)nb);
+  int64_t klp = 0, kup = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t r0 = b * kNB, r1 = std::min<int64_t>(n, r0 + kNB);
+    int64_t first = r0;
+    for (int64_t i = r0; i < r1; ++i)
+      for (int64_t j = std::max<int64_t>(0, i - kl); j < std::min<int64_t>(first, r0); ++j)
+        if (a(i, j) != 0.0) {
+          first = j;
+          break;
+        }
+    lo[b] = (int32_t)first;
+    int64_t top = r0;  // column block b: first row above the diagonal block with a non-zero
+    for (int64_t j = r0; j < r1; ++j)
+      for (int64_t i = std::max<int64_t>(0, j - ku); i < std::min<int64_t>(top, r0); ++i)
+        if (a(i, j) != 0.0) {
+          top = i;
+          break;
+        }
+    up[b] = (int32_t)top;
+    klp = std::max<int64_t>(klp, r1 - 1 - first);
+    kup = std::max<int64_t>(kup, r1 - 1 - top);
+  }
+  klp = std::min<int64_t>(klp, n - 1);
+  kup = std::min<int64_t>(kup, n - 1);
+  std::vector<int64_t> offL((size_t)nb), offU((size_t)nb);
+  int64_t count = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    offL[b] = count;
+    count += (int64_t)kNB * ((b + 1) * kNB - lo[b]);
+  }
+  for (int64_t c = 0; c < nb; ++c) {
+    offU[c] = count;
+    count += (int64_t)kNB * (c * kNB - up[c]);
+  }
+  const size_t need = profile_header_bytes(n) + (size_t)count * es;
+  if (bytes_needed) *bytes_needed = need;
+  if (kl_out) *kl_out = klp;
+  if (ku_out) *ku_out = kup;
+  if (!out) return EBV_OK;
+  if (out_bytes < need) return EBV_ERR_WORKSPACE;
+  char *h = (char *)out;
+  std::memset(h, 0, need);
+  std::memcpy(h, lo.data(), 4 * (size_t)nb);
+  std::memcpy(h + 4 * nb, up.data(), 4 * (size_t)nb);
+  std::memcpy(h + 8 * nb, offL.data(), 8 * (size_t)nb);
+  std::memcpy(h + 16 * nb, offU.data(), 8 * (size_t)nb);
+  char *vals = h + profile_header_bytes(n);
+  auto put = [&](int64_t off, double v) {
+    if (es == 8)
+      ((double *)vals)[off] = v;
+    else
+      ((float *)vals)[off] = (float)v;
+  };
+  for (int64_t b = 0; b < nb; ++b)  // lower parts with the diagonal blocks (rows past n stay 0)
+    for (int64_t i = b * kNB; i < std::min<int64_t>(n, (b + 1) * kNB); ++i)
+      for (int64_t j = lo[b]; j < std::min<int64_t>(n, (b + 1) * kNB); ++j)
+        if (j - i >= -kl && j - i <= ku) put(offL[b] + (i - b * kNB) * ((b + 1) * kNB - lo[b]) + (j - lo[b]), a(i, j));
+  for (int64_t c = 0; c < nb; ++c)  // parts above the diagonal blocks
+    for (int64_t i = up[c]; i < c * kNB; ++i)
+      for (int64_t j = c * kNB; j < std::min<int64_t>(n, (c + 1) * kNB); ++j)
+        if (j - i <= ku) put(offU[c] + (i - up[c]) * kNB + (j - c * kNB), a(i, j));
+  return EBV_OK;
+}

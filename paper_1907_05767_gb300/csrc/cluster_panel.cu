@@ -17,7 +17,7 @@
 // CTA holds its columns in shared memory, column-major.  Per step, the CTAs
 // copy pivot column k from its owner through distributed shared memory
 // (ld.shared::cluster via cooperative_groups), scale the pivot row of their
-// own columns by 1/a_kk (formed in FP64, once, by the owner at the end of the
+// own columns by 1/a_kk (formed in FP64, once, by the owner during the
 // previous step) and update.  The owner scales column k into L one step
 // later, after every CTA has copied it.  One cluster barrier per step orders
 // all of this; there is no spin-wait anywhere (hardware barriers only).
@@ -38,6 +38,9 @@ namespace ebv {
 namespace {
 
 constexpr int kPT = 256;  // threads per CTA
+// Panels taller than this read the pivot column from L2 (bcast) when the
+// caller passes the scratch.
+constexpr int kBcastMinRows = 256;
 
 struct PanelShape {
   int nc;      // CTAs in the cluster
@@ -92,8 +95,18 @@ struct BandRef {
   __device__ __forceinline__ bool writable(int64_t i, int64_t j) const { return in(i, j) && !(symlo && j > i); }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kPT) k_cluster_panel(BandRef<T> A, int64_t c0, PanelShape ps, int32_t *info) {
+// SMAX: an upper bound on the panel-column slots of one CTA (ps.slots), so the
+// scaled pivot row of the own columns lives in registers and a thread's row
+// update is one batch of independent loads, fused multiply-adds and stores.
+//
+// bcast (global, 2 (R + 1) elements, or null): with tall panels the 16 CTAs'
+// reads of pivot column k from its owner's shared memory are limited by that
+// one SM's shared-memory bandwidth (1.6 us per step measured at R = 576 on
+// GB300).  With bcast the owner also stores the finished column and its
+// reciprocal to slot k & 1 of bcast (L2) and the others read it from there.
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(kPT) k_cluster_panel(BandRef<T> A, int64_t c0, PanelShape ps, int32_t *info,
+                                                       T *bcast) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int nc = ps.nc, W = ps.W, R = ps.R, U = ps.U, S = ps.slots, UC = ps.uc;
@@ -116,13 +129,18 @@ __global__ void __launch_bounds__(kPT) k_cluster_panel(BandRef<T> A, int64_t c0,
     Uc[jj * W + i] = A.load(c0 + i, c0 + W + u0 + jj);
   }
   __syncthreads();
-  {  // reciprocal of the first pivot, by its owner
+  {  // reciprocal of the first pivot, by its owner (and column 0 to bcast)
     int o0, s0;
     col_home(0, W, nc, o0, s0);
-    if (rank == o0 && threadIdx.x == 0) {
-      const T p = Pc[(size_t)s0 * R + 0];
-      Rc[0] = pivot_rcp(p);
-      if (pivot_bad(p) && info) atomicCAS(info, 0, (int)(c0 + 1));
+    if (rank == o0) {
+      if (threadIdx.x == 0) {
+        const T p = Pc[(size_t)s0 * R + 0];
+        Rc[0] = pivot_rcp(p);
+        if (bcast) __stcg(bcast + R, Rc[0]);
+        if (pivot_bad(p) && info) atomicCAS(info, 0, (int)(c0 + 1));
+      }
+      if (bcast)
+        for (int i = 1 + threadIdx.x; i < R; i += kPT) __stcg(bcast + i, Pc[(size_t)s0 * R + i]);
     }
   }
   T r_prev = T(0);
@@ -131,15 +149,21 @@ __global__ void __launch_bounds__(kPT) k_cluster_panel(BandRef<T> A, int64_t c0,
     cluster.sync();  // column k and its reciprocal are final; everyone is done with column k-1
     int ok, sk;
     col_home(k, W, nc, ok, sk);
-    const T *remote = cluster.map_shared_rank(Pc + (size_t)sk * R, ok);
-    // Pivot k's reciprocal sits in slot k & 1 of its owner: the owner of
-    // column k+1 (the same CTA for the middle pair) writes slot (k+1) & 1
-    // during this step, and slot k & 1 again only after the next barrier,
-    // when every CTA has read it.
-    const T *rrem = cluster.map_shared_rank(Rc + (k & 1), ok);
-    // Copy pivot column k (rows k+1 .. R-1) and its reciprocal.
-    for (int i = k + 1 + threadIdx.x; i < R; i += kPT) Lk[i] = remote[i];
-    const T rk = *rrem;
+    // Pivot k's reciprocal sits in slot k & 1 of its owner (Rc, and bcast):
+    // the owner of column k+1 (the same CTA for the middle pair) writes slot
+    // (k+1) & 1 during this step, and slot k & 1 again only after the next
+    // barrier, when every CTA has read it.
+    T rk;
+    if (bcast) {  // from L2, past L1 (the slot was read two steps ago)
+      const T *src = bcast + (size_t)(k & 1) * (R + 1);
+      for (int i = k + 1 + threadIdx.x; i < R; i += kPT) Lk[i] = __ldcg(src + i);
+      rk = __ldcg(src + R);
+    } else {  // from the owner's shared memory
+      const T *remote = cluster.map_shared_rank(Pc + (size_t)sk * R, ok);
+      const T *rrem = cluster.map_shared_rank(Rc + (k & 1), ok);
+      for (int i = k + 1 + threadIdx.x; i < R; i += kPT) Lk[i] = remote[i];
+      rk = *rrem;
+    }
     // The previous pivot column, now copied by every CTA, becomes L (Eq. 6a).
     if (prev_slot >= 0)
       for (int i = k + threadIdx.x; i < R; i += kPT) Pc[(size_t)prev_slot * R + i] *= r_prev;
@@ -153,38 +177,74 @@ __global__ void __launch_bounds__(kPT) k_cluster_panel(BandRef<T> A, int64_t c0,
       }
     }
     __syncthreads();
-    // Eq. 6c: a_ij -= a_ik * (a_kj / a_kk), panel columns on rows k+1..R-1,
-    // U12 columns on the panel's rows k+1..W-1.
-    for (int i = k + 1 + threadIdx.x; i < R; i += kPT) {
-      const T l = Lk[i];
-      for (int s = 0; s < S; ++s) {
-        const T u = Up[s];
-        if (u != T(0)) Pc[(size_t)s * R + i] -= l * u;
+    // The owner of column k+1 forms the next pivot's reciprocal first (thread
+    // 0, which also updates row k+1 below, with the same fused multiply-add),
+    // so the FP64 division overlaps the other warps' updates.
+    if (k + 1 < W) {
+      int on, sn;
+      col_home(k + 1, W, nc, on, sn);
+      if (rank == on && threadIdx.x == 0) {
+        const T u = Up[sn], a = Pc[(size_t)sn * R + k + 1];
+        const T p = u != T(0) ? fma(-Lk[k + 1], u, a) : a;  // exactly what the update below stores
+        Rc[(k + 1) & 1] = pivot_rcp(p);
+        if (bcast) __stcg(bcast + (size_t)((k + 1) & 1) * (R + 1) + R, Rc[(k + 1) & 1]);
+        if (pivot_bad(p) && info) atomicCAS(info, 0, (int)(c0 + k + 2));
       }
     }
-    const int rows_u = W - 1 - k;
-    for (int e = threadIdx.x; e < rows_u * un; e += kPT) {
-      const int jj = e / rows_u, i = k + 1 + e % rows_u;
-      Uc[(size_t)jj * W + i] -= Lk[i] * Up[S + jj];
+    // Eq. 6c: a_ij -= a_ik * (a_kj / a_kk), panel columns on rows k+1..R-1
+    // (a thread per row, all of the CTA's columns at once) ...
+    T u[SMAX];
+#pragma unroll
+    for (int q = 0; q < SMAX; ++q) u[q] = q < S ? Up[q] : T(0);
+    for (int i = k + 1 + threadIdx.x; i < R; i += kPT) {
+      const T l = Lk[i];
+      T v[SMAX];
+#pragma unroll
+      for (int q = 0; q < SMAX; ++q) v[q] = (q < S && u[q] != T(0)) ? Pc[(size_t)q * R + i] : T(0);
+#pragma unroll
+      for (int q = 0; q < SMAX; ++q)
+        if (q < S && u[q] != T(0)) Pc[(size_t)q * R + i] = fma(-l, u[q], v[q]);
+    }
+    // The owner of column k+1 puts that column, as each thread has just
+    // updated its rows (the same rows as in the loop above), into the next
+    // bcast slot; the readers take the rows below the next pivot.
+    if (bcast && k + 1 < W) {
+      int on, sn;
+      col_home(k + 1, W, nc, on, sn);
+      if (rank == on) {
+        T *dst = bcast + (size_t)((k + 1) & 1) * (R + 1);
+        for (int i = k + 1 + threadIdx.x; i < R; i += kPT) __stcg(dst + i, Pc[(size_t)sn * R + i]);
+      }
+    }
+    // ... and U12 columns on the panel's rows k+1..W-1: thread (row ti,
+    // column group tg) takes columns tg, tg+4, ... (a warp reads 32
+    // consecutive rows of one column: no bank conflicts).
+    {
+      const int ti = threadIdx.x % 64, tg = threadIdx.x / 64;
+      const int i = k + 1 + ti;
+      if (i < W) {
+        const T l = Lk[i];
+        for (int jb = tg; jb < un; jb += 16) {
+          T uu[4], vv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = jb + 4 * q;
+            uu[q] = jj < un ? Up[S + jj] : T(0);
+            vv[q] = jj < un ? Uc[(size_t)jj * W + i] : T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = jb + 4 * q;
+            if (jj < un) Uc[(size_t)jj * W + i] = fma(-l, uu[q], vv[q]);
+          }
+        }
+      }
     }
     if (rank == ok) {
       prev_slot = sk;
       r_prev = rk;
     } else {
       prev_slot = -1;
-    }
-    // The owner of column k+1 forms its pivot's reciprocal for the next step.
-    if (k + 1 < W) {
-      int on, sn;
-      col_home(k + 1, W, nc, on, sn);
-      if (rank == on) {
-        __syncthreads();  // row k+1 of column k+1 is updated
-        if (threadIdx.x == 0) {
-          const T p = Pc[(size_t)sn * R + k + 1];
-          Rc[(k + 1) & 1] = pivot_rcp(p);
-          if (pivot_bad(p) && info) atomicCAS(info, 0, (int)(c0 + k + 2));
-        }
-      }
     }
   }
   cluster.sync();  // no CTA reads another's shared memory after this
@@ -205,22 +265,46 @@ __global__ void __launch_bounds__(kPT) k_cluster_panel(BandRef<T> A, int64_t c0,
 
 // Largest cluster (16, else 8) that the device can run with this shared
 // memory, or 0.
+// The kernel instance for a slot count: SMAX = 4, 8, 16 or 32 (null above).
 template <typename T>
-int cluster_size_for(size_t smem16, size_t smem8) {
-  auto kern = k_cluster_panel<T>;
+using PanelKernel = void (*)(BandRef<T>, int64_t, PanelShape, int32_t *, T *);
+template <typename T>
+PanelKernel<T> panel_kernel(int slots) {
+  if (slots <= 4) return k_cluster_panel<T, 4>;
+  if (slots <= 8) return k_cluster_panel<T, 8>;
+  if (slots <= 16) return k_cluster_panel<T, 16>;
+  if (slots <= 32) return k_cluster_panel<T, 32>;
+  return nullptr;
+}
+
+template <typename T>
+bool prepare_panel_kernels() {
   static std::once_flag once;
-  static bool attr_ok = false;
-  std::call_once(once, [&] {
-    attr_ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-              cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) == cudaSuccess &&
-              cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                   (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+  static bool ok = false;
+  std::call_once(once, [] {
+    ok = true;
+    for (int sl : {4, 8, 16, 32}) {
+      auto kern = panel_kernel<T>(sl);
+      ok = ok && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) == cudaSuccess &&
+           cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    }
     (void)cudaGetLastError();
   });
-  if (!attr_ok) return 0;
+  return ok;
+}
+
+// Largest cluster (16, else 8) that the device can run with the shared
+// memory of that shape, or 0.
+template <typename T>
+int cluster_size_for(int W, int R, int U) {
+  if (!prepare_panel_kernels<T>()) return 0;
   for (int nc : {16, 8}) {
-    const size_t smem = nc == 16 ? smem16 : smem8;
-    if (smem > 227 * 1024) continue;
+    const PanelShape ps = panel_shape(nc, W, R, U);
+    const size_t smem = panel_smem_elems<T>(ps) * sizeof(T);
+    auto kern = panel_kernel<T>(ps.slots);
+    if (smem > 227 * 1024 || !kern) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nc);
     cfg.blockDim = dim3(kPT);
@@ -241,16 +325,14 @@ int cluster_size_for(size_t smem16, size_t smem8) {
 
 template <typename T>
 ebv_status_t cluster_panel_t(T *base, int64_t ld, int64_t kl, int64_t ku, bool symlo, int64_t c0, int W, int R, int U,
-                             int32_t *info, cudaStream_t s) {
-  const size_t e16 = panel_smem_elems<T>(panel_shape(16, W, R, U)) * sizeof(T);
-  const size_t e8 = panel_smem_elems<T>(panel_shape(8, W, R, U)) * sizeof(T);
-  const int nc = cluster_size_for<T>(e16, e8);
+                             int32_t *info, T *bcast, cudaStream_t s) {
+  const int nc = cluster_size_for<T>(W, R, U);
   if (nc == 0) return EBV_ERR_UNSUPPORTED;
   const PanelShape ps = panel_shape(nc, W, R, U);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nc);
   cfg.blockDim = dim3(kPT);
-  cfg.dynamicSmemBytes = nc == 16 ? e16 : e8;
+  cfg.dynamicSmemBytes = panel_smem_elems<T>(ps) * sizeof(T);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -261,7 +343,8 @@ ebv_status_t cluster_panel_t(T *base, int64_t ld, int64_t kl, int64_t ku, bool s
   cfg.numAttrs = 1;
   prof::Scope sc(s, prof::kPanel, 2.0 * (double)W * W * W / 3.0 + 2.0 * (double)(R - W) * W * W / 2.0 +
                                       (double)W * W * U);
-  EBV_CU(cudaLaunchKernelEx(&cfg, k_cluster_panel<T>, BandRef<T>{base, ld, kl, ku, symlo}, c0, ps, info));
+  EBV_CU(cudaLaunchKernelEx(&cfg, panel_kernel<T>(ps.slots), BandRef<T>{base, ld, kl, ku, symlo}, c0, ps, info,
+                            R > kBcastMinRows ? bcast : nullptr));
   return launch_ok();
 }
 
@@ -278,10 +361,11 @@ bool cluster_panel_fits(bool fp64, int W, int64_t R, int64_t U) {
 }
 
 ebv_status_t cluster_panel(bool fp64, void *base, int64_t ld, int64_t kl, int64_t ku, bool symlo, int64_t c0, int W,
-                           int64_t R, int64_t U, int32_t *info, cudaStream_t s) {
+                           int64_t R, int64_t U, int32_t *info, void *bcast, cudaStream_t s) {
   if (!g_cluster_panel || !cluster_panel_fits(fp64, W, R, U) || (symlo && U != 0)) return EBV_ERR_UNSUPPORTED;
-  if (fp64) return cluster_panel_t<double>((double *)base, ld, kl, ku, symlo, c0, W, (int)R, (int)U, info, s);
-  return cluster_panel_t<float>((float *)base, ld, kl, ku, symlo, c0, W, (int)R, (int)U, info, s);
+  if (fp64)
+    return cluster_panel_t<double>((double *)base, ld, kl, ku, symlo, c0, W, (int)R, (int)U, info, (double *)bcast, s);
+  return cluster_panel_t<float>((float *)base, ld, kl, ku, symlo, c0, W, (int)R, (int)U, info, (float *)bcast, s);
 }
 
 }  // namespace ebv

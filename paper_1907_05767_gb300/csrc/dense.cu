@@ -457,7 +457,7 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   if ((prec == EBV_FP64 || prec == EBV_FP32) && n <= kClusterDenseMaxN) {
     // A small system whole on one thread-block cluster (one launch).
     const ebv_status_t st =
-        cluster_panel(prec == EBV_FP64, a, d->ld, kDenseBand, kDenseBand, false, 0, (int)n, n, 0, info, s);
+        cluster_panel(prec == EBV_FP64, a, d->ld, kDenseBand, kDenseBand, false, 0, (int)n, n, 0, info, nullptr, s);
     if (st != EBV_ERR_UNSUPPORTED) return st;
   }
   if (prec == EBV_FP64) {

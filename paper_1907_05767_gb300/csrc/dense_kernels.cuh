@@ -20,24 +20,51 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // strictly below the diagonal, the pivots d on it; kl = ku): the U entries
 // are read as u_ij = d_i l_ji (U = D L^T, the LDL^T form of Eq. 6a-b) and
 // writes above the diagonal are dropped.
+//
+// Profile (skyline) storage (plo set): per 64-block b, row block b keeps
+// columns plo[b] .. 64b+63 (its lower part with the whole diagonal block),
+// row-major with width 64(b+1) - plo[b], from base + poffL[b]; column block
+// c keeps rows pup[c] .. 64c-1 (its part above the diagonal block),
+// row-major with width 64, from base + poffU[c].  Entries outside read as 0
+// and are never written; kl / ku bound the profile (the drivers' windows).
 template <typename T>
 struct MatView {
   T *base;
   int64_t ld;
   int64_t kl, ku;
   bool symlo = false;
+  const int32_t *plo = nullptr, *pup = nullptr;
+  const int64_t *poffL = nullptr, *poffU = nullptr;
   __device__ __forceinline__ bool in(int64_t i, int64_t j) const {
     const int64_t d = j - i;
-    return d >= -kl && d <= ku;
+    if (d < -kl || d > ku) return false;
+    if (plo) {
+      const int64_t b = i >> 6;
+      return j < ((b + 1) << 6) ? j >= plo[b] : i >= pup[j >> 6];
+    }
+    return true;
+  }
+  // Address of a stored element (in(i, j) must hold).
+  __device__ __forceinline__ T *at(int64_t i, int64_t j) const {
+    if (plo) {
+      const int64_t b = i >> 6;
+      if (j < ((b + 1) << 6)) {
+        const int64_t lo = plo[b];
+        return base + poffL[b] + (i - (b << 6)) * (((b + 1) << 6) - lo) + (j - lo);
+      }
+      const int64_t c = j >> 6;
+      return base + poffU[c] + (i - pup[c]) * 64 + (j - (c << 6));
+    }
+    return base + i * ld + j;
   }
   __device__ __forceinline__ T get(int64_t i, int64_t j) const {
     if (!in(i, j)) return T(0);
     if (symlo && j > i) return base[j * ld + i] * base[i * ld + i];
-    return base[i * ld + j];
+    return *at(i, j);
   }
   __device__ __forceinline__ bool writable(int64_t i, int64_t j) const { return in(i, j) && !(symlo && j > i); }
   __device__ __forceinline__ void put(int64_t i, int64_t j, T v) const {
-    if (writable(i, j)) base[i * ld + j] = v;
+    if (writable(i, j)) *at(i, j) = v;
   }
 };
 
@@ -1385,7 +1412,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     for (int b = 0; b < TN; ++b) {
       const int64_t gj = bn + tx + b * NTX;
       if (gj < nend && A.writable(gi, gj)) {
-        T *c = A.base + gi * A.ld + gj;
+        T *c = A.at(gi, gj);
         *c = *c - acc[a][b];
       }
     }

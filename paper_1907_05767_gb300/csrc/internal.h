@@ -41,9 +41,11 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
 // EBV_ERR_UNSUPPORTED when the shape does not fit the kernel or the device
 // cannot run the cluster (the caller then uses the one-CTA leaf kernels).
 // symlo: only the lower half of a symmetric band is stored (U must be 0).
+// bcast: device scratch of 2 (R + 1) elements (or null) through which tall
+// panels pass the pivot column in L2 instead of distributed shared memory.
 bool cluster_panel_fits(bool fp64, int W, int64_t R, int64_t U);
 ebv_status_t cluster_panel(bool fp64, void *base, int64_t ld, int64_t kl, int64_t ku, bool symlo, int64_t c0, int W,
-                           int64_t R, int64_t U, int32_t *info, cudaStream_t s);
+                           int64_t R, int64_t U, int32_t *info, void *bcast, cudaStream_t s);
 // Testing hook: false = never use the cluster panel kernel.
 void set_cluster_panel(bool on);
 bool cluster_panel_enabled();

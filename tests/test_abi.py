@@ -118,7 +118,7 @@ def test_band_storage_descriptors(lib):
     assert ok(100, 5, 4, 4, ebv.BAND_SYM_LOWER) and not ok(100, 4, 4, 4, ebv.BAND_SYM_LOWER)
     assert not ok(100, 9, 3, 5, ebv.BAND_SYM_LOWER)
     assert not ok(100, 9, 100, 100, ebv.BAND_SYM_LOWER)  # kl < n
-    assert not ok(100, 100, 0, 0, 4)  # no such storage
+    assert not ok(100, 100, 0, 0, 5)  # no such storage
 
 
 def test_inverse_argument_errors(lib):
