@@ -616,21 +616,22 @@ def _config_dense256(args, dev):
         lu.copy_(A)
         ebv.ebv_factor(lu, "fp64", info=info, ws=ws)
 
-    ebv.lib().ebv_debug_set_cluster_panel(0)
-    ms_one_cta = _dev_ms(c0, 200, 10)
-    ebv.lib().ebv_debug_set_cluster_panel(1)
+    ebv.lib().ebv_debug_set_small_dense(0)  # the same on one thread-block cluster
+    ms_cluster = _dev_ms(c0, 200, 10)
+    ebv.lib().ebv_debug_set_small_dense(1)
     ms_factor = _dev_ms(c0_factor, 200, 10)
     ms = _dev_ms(c0, 200, 10)
     x_ref = oracle.solve(oracle.lu(a)[0], b)
     xs = x.cpu().numpy()
     r = oracle.residual(a, xs, b)
     out.append({"config": "dense FP64 n=256, 1 RHS", "ms": ms, "ms_factor_incl_copy": ms_factor,
-                "ms_recursive_one_cta_leaves": ms_one_cta,
+                "ms_on_cluster_panel": ms_cluster,
                 "solves_per_s": 1e3 / ms,
                 "gflops": nominal_flops(n, 1) / (ms / 1e3) / 1e9,
                 "x_relerr_vs_oracle": float(np.abs(xs - x_ref).max() / np.abs(x_ref).max()),
                 "backward_error": float(np.abs(r).max() / (np.abs(a).sum(axis=1).max() * np.abs(xs).max())),
-                "note": "whole problem L2-resident (CUDA graph); factor on one thread-block cluster"})
+                "note": "whole problem L2-resident (CUDA graph); 64-column panels with substitution L21/U12, "
+                        "one-CTA block substitution solve"})
     print(json.dumps(out[-1]), flush=True)
     return out[-1]
 
@@ -656,10 +657,10 @@ def _config_band(args, dev):
         ebv.ebv_factor(lu, "fp64", info=info, ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
         ebv.ebv_solve(lu, x, "fp64", ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
 
-    # the same with the one-CTA diagonal-block kernels instead of the cluster panels
-    ebv.lib().ebv_debug_set_cluster_panel(0)
-    ms_one_cta = _dev_ms(c1, 3, 2)
-    ebv.lib().ebv_debug_set_cluster_panel(1)
+    # the same with the panels on thread-block clusters
+    ebv.lib().ebv_debug_set_band_cluster(1)
+    ms_cluster = _dev_ms(c1, 3, 2)
+    ebv.lib().ebv_debug_set_band_cluster(0)
     ms = _dev_ms(c1, 3, 2)
     xs = x.cpu().numpy()
     rows = synthetic.pick_indices(11, 512, [n])[:, 0]
@@ -667,7 +668,7 @@ def _config_band(args, dev):
     flops = 2.0 * n * kl * ku + 2.0 * n * (kl + ku) * b.shape[1]
     g = args.band_grid
     out.append({"config": f"band FP64 Laplacian {g}x{g} (n={n}, kl=ku={kl}), 8 RHS", "ms": ms,
-                "ms_one_cta_panels": ms_one_cta,
+                "ms_cluster_panels": ms_cluster,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),

@@ -422,16 +422,28 @@ EBV_API ebv_status_t ebv_solve_static(const ebv_desc_t *desc, ebv_prec_t prec, c
 EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
 
 /*
- * Testing hook: panels of the banded factorisation (a 64-column panel with
- * its kl rows below and ku columns right) and whole dense FP64 / FP32
- * systems of order <= 256 are factored by one launch on a thread-block
- * cluster of up to 16 CTAs (the panel's columns paired long with short over
- * the CTAs, Eq. 7; the pivot column passed through distributed shared
- * memory).  enable = 0 runs the one-CTA diagonal-block kernels and separate
- * L21 / U12 launches instead (the results agree to rounding).
- * Process-wide, default on.
+ * Testing hooks of the thread-block-cluster panel kernel, which factors a
+ * panel (its diagonal block, L21 and U12) in one launch on up to 16 CTAs,
+ * the panel's columns paired long with short over the CTAs (Eq. 7), the
+ * pivot column passed through distributed shared memory (or L2 for tall
+ * panels).  ebv_debug_set_band_cluster(1) makes the banded factorisation use
+ * it for every 64-column panel (default 0: the diagonal block on one CTA and
+ * L21 / U12 as separate launches, measured faster).  ebv_debug_set_cluster_panel
+ * (0) switches the kernel off wherever it would run (default 1).  The
+ * results agree to rounding.  Process-wide.
  */
+EBV_API void ebv_debug_set_band_cluster(int32_t enable);
 EBV_API void ebv_debug_set_cluster_panel(int32_t enable);
+
+/*
+ * Testing hook: dense FP64 systems of order <= 256 are factored as
+ * right-looking 64-column panels (the diagonal block on one CTA without its
+ * inverses, L21 and U12 by substitution on many CTAs, one trailing update)
+ * and solved by one CTA's block substitution when panels != 0 (default);
+ * else factored on one thread-block cluster and solved by the general
+ * substitution kernels.  The results agree to rounding.  Process-wide.
+ */
+EBV_API void ebv_debug_set_small_dense(int32_t panels);
 
 /*
  * Testing hook: the banded factorisation (every band storage) first finds

@@ -146,6 +146,13 @@ ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu
   return inverse(n, prec, lu, desc->ld, x, ldx, ws, (cudaStream_t)stream);
 }
 
+// Testing hook: 0 = small dense FP64 systems on one thread-block cluster
+// instead of substitution panels.
+void ebv_debug_set_small_dense(int32_t panels) { set_small_dense_panels(panels != 0); }
+
+// Testing hook: 1 = band panels on thread-block clusters.
+void ebv_debug_set_band_cluster(int32_t enable) { set_band_cluster(enable != 0); }
+
 // Testing hook: 0 = panels never run on a thread-block cluster.
 void ebv_debug_set_cluster_panel(int32_t enable) { set_cluster_panel(enable != 0); }
 

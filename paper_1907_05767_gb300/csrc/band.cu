@@ -69,7 +69,183 @@ __global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, 
   if (lane == 0) atomicMin(&up[i / 64], (int32_t)first);
 }
 
+// LU of one 64 x 64 diagonal block (FP64 panels; no inverses), unblocked
+// Doolittle with the block in registers: warp w owns the column pairs
+// {p, 63-p} for p = 4w .. 4w+3 (the long/short pairing of Eq. 7: every warp
+// holds the same amount of work over the 64 steps), lane l rows 2l and 2l+1.
+// Step k: every warp takes the L vector of column k from shared memory
+// (Eq. 6a) and row k of its own columns from the lane holding it, and
+// updates its columns right of k (Eq. 6c).  The owner of column k+1 updates
+// that column first, then forms its pivot's FP64 reciprocal and L vector
+// into the other half of a double buffer, so one block barrier per step
+// orders everything and the division overlaps the other warps' updates.
+// The block's rows and columns past w are an identity (no pivot there).
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_lu64(MatView<T> A, int64_t k0, int w, int32_t *info) {
+  constexpr int NB = 64;
+  __shared__ T Lb[2][NB];
+  __shared__ int bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = 2 * lane, r1 = r0 + 1;
+  auto col_of = [&](int s) { return s < 4 ? 4 * warp + s : NB - 1 - (4 * warp + s - 4); };
+  T v[8][2];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int c = col_of(s);
+    v[s][0] = (r0 < w && c < w) ? A.get(k0 + r0, k0 + c) : (r0 == c ? T(1) : T(0));
+    v[s][1] = (r1 < w && c < w) ? A.get(k0 + r1, k0 + c) : (r1 == c ? T(1) : T(0));
+  }
+  if (threadIdx.x == 0) bad = NB;
+  // owner (warp, slot) of column j
+  auto owner = [](int j, int &ow, int &os) {
+    const int p = min(j, NB - 1 - j);
+    ow = p / 4;
+    os = (j == p) ? p % 4 : 4 + p % 4;
+  };
+  // column j (held in slot s of this warp) becomes L: reciprocal of its pivot
+  // (FP64), rows below scaled and published to Lb[buf]
+  auto publish = [&](int j, int s, int buf) {
+    T pv = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q == s) pv = __shfl_sync(0xffffffffu, (j & 1) ? v[q][1] : v[q][0], j >> 1);
+    T rc = T(0);
+    if (lane == 0) {
+      rc = pivot_rcp(pv);
+      if (pivot_bad(pv) && j < w) atomicMin(&bad, j);
+    }
+    rc = __shfl_sync(0xffffffffu, rc, 0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q == s) {
+        if (r0 > j) v[q][0] *= rc;
+        if (r1 > j) v[q][1] *= rc;
+        Lb[buf][r0] = r0 > j ? v[q][0] : T(0);
+        Lb[buf][r1] = r1 > j ? v[q][1] : T(0);
+      }
+  };
+  {
+    int ow, os;
+    owner(0, ow, os);
+    if (warp == ow) publish(0, os, 0);
+  }
+  __syncthreads();
+  for (int k = 0; k < NB - 1; ++k) {
+    const T l0 = Lb[k & 1][r0], l1 = Lb[k & 1][r1];
+    int ow, os;
+    owner(k + 1, ow, os);
+    const int first = (warp == ow) ? os : -1;
+    // row k of slot s from the lane holding it, then Eq. 6c on rows > k
+    auto update = [&](int s) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q == s) {
+          const T u = __shfl_sync(0xffffffffu, (k & 1) ? v[q][1] : v[q][0], k >> 1);
+          if (col_of(q) > k) {
+            v[q][0] -= l0 * u;
+            v[q][1] -= l1 * u;
+          }
+        }
+    };
+    if (first >= 0) {
+      update(first);
+      publish(k + 1, first, (k + 1) & 1);
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+      if (s != first) update(s);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad < w && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int c = col_of(s);
+    if (c < w) {
+      if (r0 < w) A.put(k0 + r0, k0 + c, v[s][0]);
+      if (r1 < w) A.put(k0 + r1, k0 + c, v[s][1]);
+    }
+  }
+}
+
+// L21 = A21 U11^{-1} by substitution (FP64 panels): one warp per row of
+// A21; lane l holds columns l and l+32 of the row.  Step j: the lane holding
+// column j forms l_ij = (a_ij - sum_{k<j} l_ik u_kj) / u_jj with the FP64
+// reciprocal and passes it by shuffle; every lane subtracts l_ij u_jc from
+// its later columns c (U11 and the reciprocals staged in shared memory).  The
+// 64-step chain per row needs no inverse of U11, so the diagonal-block kernel
+// only factors; rows run on many SMs.  Rows of 64-blocks outside the
+// envelope hold zeros and are skipped.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_trsm_ru_subst(MatView<T> A, int64_t c0, int w, int64_t rb, int64_t re,
+                                                       Envelope env) {
+  __shared__ T Us[NB][NB + 1];
+  __shared__ T rc[NB];
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int k = e / NB, c = e % NB;
+    Us[k][c] = (k < w && c < w && c >= k) ? A.get(c0 + k, c0 + c) : T(0);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NB; k += 256) rc[k] = k < w ? pivot_rcp(Us[k][k]) : T(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t i = rb + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= re || env.rows_empty(i, c0 + w)) return;
+  T a0 = lane < w ? A.get(i, c0 + lane) : T(0);
+  T a1 = lane + 32 < w ? A.get(i, c0 + lane + 32) : T(0);
+  for (int j = 0; j < w; ++j) {
+    const T mine = j < 32 ? a0 : a1;
+    const T l = __shfl_sync(0xffffffffu, mine, j & 31) * rc[j];  // Eq. 6a
+    if (lane == (j & 31)) {
+      if (j < 32) a0 = l;
+      else a1 = l;
+    }
+    if (lane > j) a0 -= l * Us[j][lane];
+    if (lane + 32 > j) a1 -= l * Us[j][lane + 32];
+  }
+  if (lane < w) A.put(i, c0 + lane, a0);
+  if (lane + 32 < w) A.put(i, c0 + lane + 32, a1);
+}
+
+// U12 = L11^{-1} A12 by substitution (FP64 panels): one warp per column of
+// A12 (8 per CTA, the 64 x 8 block staged with whole rows); lane l holds rows
+// l and l+32.  Step k: u_kj is final; it goes by shuffle to every lane,
+// which subtracts l_rk u_kj from its later rows r (Eq. 6b; L11 unit lower).
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_trsm_ll_subst(MatView<T> A, int64_t c0, int w, int64_t cb, int64_t ce,
+                                                       Envelope env) {
+  __shared__ T Ls[NB][NB + 1];
+  __shared__ T Bs[NB][8 + 1];
+  const int64_t j0 = cb + (int64_t)blockIdx.x * 8;
+  if (env.cols_empty(j0, c0 + w) && env.cols_empty(min64(ce - 1, j0 + 7), c0 + w)) return;
+  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+    const int r = e / NB, k = e % NB;
+    Ls[r][k] = (r < w && k < r) ? A.get(c0 + r, c0 + k) : T(0);
+  }
+  for (int e = threadIdx.x; e < NB * 8; e += 256) {
+    const int r = e / 8, c = e % 8;
+    Bs[r][c] = (r < w && j0 + c < ce) ? A.get(c0 + r, j0 + c) : T(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, cw = threadIdx.x >> 5;
+  if (j0 + cw < ce) {
+    T b0 = Bs[lane][cw], b1 = Bs[lane + 32][cw];
+    for (int k = 0; k < w; ++k) {
+      const T u = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
+      if (lane > k) b0 -= Ls[lane][k] * u;
+      if (lane + 32 > k) b1 -= Ls[lane + 32][k] * u;
+    }
+    Bs[lane][cw] = b0;
+    Bs[lane + 32][cw] = b1;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * 8; e += 256) {
+    const int r = e / 8, c = e % 8;
+    if (r < w && j0 + c < ce) A.put(c0 + r, j0 + c, Bs[r][c]);
+  }
+}
+
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
+bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
 // General bands: one-CTA diagonal blocks (false) or cluster panels (true).
 // Measured on the 512 x 512 Laplacian, factor + solve: 1113 ms one-CTA
 // against 1233 ms on clusters, so the cluster panels serve the lower-half
@@ -103,7 +279,7 @@ MatView<T> profile_view(void *buf, int64_t n, int64_t kl, int64_t ku) {
 
 template <typename T>
 ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym, T *bcast,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool envelope = true) {
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
   using G = BandGemm<T>;
   EBV_TRY((prepare_leaf_kernels<T, float>()));
@@ -114,7 +290,7 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
       env.lo = A.plo;
       env.up = A.pup;
     }
-  } else if (g_band_envelope) {
+  } else if (g_band_envelope && envelope) {
     const int64_t nblk = ceil_div(n, kNB);
     int32_t *env_up = env_lo + nblk;
     EBV_CU(cudaMemsetAsync(env_lo, 0x7f, 2 * nblk * sizeof(int32_t), s));  // 0x7f7f7f7f > any index
@@ -129,12 +305,12 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
   // other band storages keep the one-CTA diagonal-block kernels, measured
   // faster on the 512 x 512 Laplacian (1119 ms against 1504 ms per
   // factor + solve).
-  bool cluster = !A.plo && (A.symlo || g_band_cluster) && cluster_panel_enabled() &&
+  bool cluster = !A.plo && g_band_cluster && cluster_panel_enabled() &&
                  cluster_panel_fits(sizeof(T) == 8, kNB, std::min<int64_t>(n, kNB + A.kl), sym ? 0 : A.ku);
-  // Lower-half storage of a symmetric band: the one-CTA leaf kernels read the
-  // unfactored upper half through the view, which there means d_i l_ji, so
-  // only the cluster panel (which reads a_ji) can factor it.
-  if (A.symlo && !cluster) return EBV_ERR_UNSUPPORTED;
+  // The diagonal-block kernel reads its still unfactored block; in the
+  // lower-half symmetric storage that view reads a_ji above the diagonal.
+  MatView<T> Araw = A;
+  Araw.symraw = true;
   for (int64_t c0 = 0; c0 < n; c0 += kNB) {
     const int w = (int)std::min<int64_t>(kNB, n - c0);
     const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
@@ -163,9 +339,45 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
         continue;
       }
     }
+    if constexpr (sizeof(T) == 8) {
+      if (g_band_subst) {
+        // FP64: the diagonal block factored alone (no inverses: two thirds of
+        // its FP64 work), then L21 and U12 by substitution over many SMs.
+        {
+          prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
+          k_diag_lu64<T><<<1, 256, 0, s>>>(Araw, c0, w, info);
+          EBV_TRY(launch_ok());
+        }
+        if (re > rb) {
+          prof::Scope ps(s, prof::kL21, 1.0 * (re - rb) * w * w);
+          k_trsm_ru_subst<T, kNB><<<ceil_div(re - rb, 8), 256, 0, s>>>(A, c0, w, rb, re, env);
+          EBV_TRY(launch_ok());
+        }
+        if (ce > cb && sym) {
+          if (!A.symlo) {  // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
+            prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
+            k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
+            EBV_TRY(launch_ok());
+          }
+        } else if (ce > cb) {
+          prof::Scope ps(s, prof::kTrsm, 1.0 * w * w * (ce - cb));
+          k_trsm_ll_subst<T, kNB><<<ceil_div(ce - cb, 8), 256, 0, s>>>(A, c0, w, cb, ce, env);
+          EBV_TRY(launch_ok());
+        }
+        if (re > rb && ce > cb) {
+          prof::Scope ps(s, prof::kSimtGemm, 2.0 * (re - rb) * (ce - cb) * w);
+          dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
+          k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
+              <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0,
+                                                                  env);
+          EBV_TRY(launch_ok());
+        }
+        continue;
+      }
+    }
     {
       prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(A, c0, w, info, inv);
+      k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, inv);
       EBV_TRY(launch_ok());
     }
     // FP64: 16-row / 16-column strips, four times the CTAs of one 64 x 64
@@ -179,10 +391,12 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
         k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none, env);
       EBV_TRY(launch_ok());
     }
-    if (ce > cb && sym) {  // U12 = D11 L21^T
-      prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
-      k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
-      EBV_TRY(launch_ok());
+    if (ce > cb && sym) {  // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
+      if (!A.symlo) {
+        prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
+        k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
+        EBV_TRY(launch_ok());
+      }
     } else if (ce > cb) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * w * w * (ce - cb));
       if constexpr (sizeof(T) == 8)
@@ -291,6 +505,7 @@ size_t band_factor_ws(int64_t n, int64_t kl, int64_t, ebv_prec_t prec) {
   return kStatusBytes + band_inv_bytes(prec) + band_env_bytes(n) + band_bcast_bytes(kl, prec);
 }
 void set_band_envelope(bool on) { g_band_envelope = on; }
+void set_band_cluster(bool on) { g_band_cluster = on; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
 }
@@ -377,6 +592,13 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16)  // FP32 factors, FP64 right-hand sides and solution
     return solve_refined<float>(view((float *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, residual, s);
   return EBV_ERR_UNSUPPORTED;
+}
+
+// Small dense FP64 systems: the panel loop above on a dense view (64-column
+// panels: the diagonal block alone on one CTA, L21 / U12 by substitution on
+// many, one trailing update), without the envelope scan.
+ebv_status_t dense_small_factor(double *a, int64_t ld, int64_t n, int32_t *info, void *ws, cudaStream_t s) {
+  return band_factor_t<double>(dense_view(a, ld), n, info, nullptr, nullptr, false, nullptr, s, false);
 }
 
 }  // namespace ebv

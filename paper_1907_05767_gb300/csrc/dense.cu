@@ -124,6 +124,10 @@ struct SimtGemm<float> {
 // Mixed-precision GEMM dispatch.
 // ---------------------------------------------------------------------------
 static int g_lowp_mode = 0;
+// Small dense FP64 factorisations as substitution panels (true) or on one
+// thread-block cluster (false); testing hook ebv_debug_set_small_dense.
+static bool g_small_dense_panels = true;
+void set_small_dense_panels(bool on) { g_small_dense_panels = on; }
 void set_lowp_gemm_mode(int mode) { g_lowp_mode = mode; }
 int get_lowp_gemm_mode() { return g_lowp_mode; }
 
@@ -454,6 +458,11 @@ ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *l
   char *w = (char *)ws;
   DevStatus *dst = (DevStatus *)ws;
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
+  if (prec == EBV_FP64 && n <= kSmallDenseMaxN && g_small_dense_panels) {
+    // Small FP64 systems as 64-column panels: the diagonal block factored
+    // alone, L21 / U12 by substitution (no FP64 inverses on the chain).
+    return dense_small_factor((double *)a, d->ld, n, info, ws, s);
+  }
   if ((prec == EBV_FP64 || prec == EBV_FP32) && n <= kClusterDenseMaxN) {
     // A small system whole on one thread-block cluster (one launch).
     const ebv_status_t st =
@@ -547,6 +556,12 @@ ebv_status_t dense_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, c
     return dense_residual(a_orig, d->ld, n, x, ldx, nrhs, bs, r, rmax, w, L, first, st, s);
   };
   const bool b_double = prec != EBV_FP32;
+  if (fp64 && !refine && n <= kSmallSolveMaxN && nrhs <= 8 && g_small_dense_panels) {
+    // small systems: direct block substitution in one CTA (no diagonal-block inverses)
+    prof::Scope ps(s, prof::kTrsv, 2.0 * n * n * nrhs);
+    k_small_solve<double><<<1, 256, 0, s>>>(dense_view((double *)lu, d->ld), (int)n, (double *)b, ldb, (int)nrhs);
+    return launch_ok();
+  }
   if (fp64)
     return solve_refined<double>(dense_view((double *)lu, d->ld), n, b, nrhs, ldb, refine, rep, w, L, b_double,
                                  residual, s);

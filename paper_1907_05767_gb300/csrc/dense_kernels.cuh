@@ -19,7 +19,8 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // symlo: the factors of a symmetric band kept in its lower half only (L
 // strictly below the diagonal, the pivots d on it; kl = ku): the U entries
 // are read as u_ij = d_i l_ji (U = D L^T, the LDL^T form of Eq. 6a-b) and
-// writes above the diagonal are dropped.
+// writes above the diagonal are dropped.  symraw (with symlo): entries above
+// the diagonal read as a_ji instead -- the view of a still unfactored block.
 //
 // Profile (skyline) storage (plo set): per 64-block b, row block b keeps
 // columns plo[b] .. 64b+63 (its lower part with the whole diagonal block),
@@ -33,6 +34,7 @@ struct MatView {
   int64_t ld;
   int64_t kl, ku;
   bool symlo = false;
+  bool symraw = false;
   const int32_t *plo = nullptr, *pup = nullptr;
   const int64_t *poffL = nullptr, *poffU = nullptr;
   __device__ __forceinline__ bool in(int64_t i, int64_t j) const {
@@ -59,7 +61,7 @@ struct MatView {
   }
   __device__ __forceinline__ T get(int64_t i, int64_t j) const {
     if (!in(i, j)) return T(0);
-    if (symlo && j > i) return base[j * ld + i] * base[i * ld + i];
+    if (symlo && j > i) return symraw ? base[j * ld + i] : base[j * ld + i] * base[i * ld + i];
     return *at(i, j);
   }
   __device__ __forceinline__ bool writable(int64_t i, int64_t j) const { return in(i, j) && !(symlo && j > i); }
@@ -96,7 +98,7 @@ inline MatView<T> band_view(T *ab, int64_t ldab, int64_t kl, int64_t ku) {
 // The lower half of a symmetric band (a_ij at ab[i*ldab + j-i+kl], j <= i).
 template <typename T>
 inline MatView<T> symlo_view(T *ab, int64_t ldab, int64_t kl) {
-  return MatView<T>{ab + kl, ldab - 1, kl, kl, true};
+  return MatView<T>{ab + kl, ldab - 1, kl, kl, true, false};
 }
 
 // Stage an NB x NB tile into shared memory (row stride S) with all of the

@@ -30,6 +30,13 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
 // Testing hook of the banded factorisation: false = no block envelope (every
 // CTA of the band window works; the results are the same).
 void set_band_envelope(bool on);
+// Testing hook: true = band panels on thread-block clusters (default false).
+void set_band_cluster(bool on);
+// Dense FP64 factorisation of a small system as right-looking 64-column
+// panels (band.cu); orders up to kSmallDenseMaxN use it.
+ebv_status_t dense_small_factor(double *a, int64_t ld, int64_t n, int32_t *info, void *ws, cudaStream_t s);
+constexpr int64_t kSmallDenseMaxN = 256;
+void set_small_dense_panels(bool on);
 ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, const double *a_orig, void *b,
                         int64_t nrhs, int64_t ldb, const ebv_refine_t *refine, ebv_refine_report_t *rep, void *ws,
                         size_t ws_bytes, cudaStream_t s);

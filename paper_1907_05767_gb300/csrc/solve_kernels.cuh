@@ -398,6 +398,101 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n
 }
 
 // ---------------------------------------------------------------------------
+// Small systems (n <= kSmallSolveMaxN): LY = B then UX = Y (Eq. 1) by one CTA
+// of 8 warps, 32-row blocks.  Per block: 8 threads share each row's sum over
+// the finished blocks (strided columns, four independent partial sums so all
+// loads of a block are in flight at once, shuffle reduction; accumulated
+// from zero and subtracted from b once), then warp 0 solves the
+// 32 x 32 diagonal block, lane l holding row r0+l's block entries in
+// registers and the solved values passed by shuffle.  No inverse of any
+// diagonal block is formed.  Right-hand sides one column at a time.
+// ---------------------------------------------------------------------------
+constexpr int kSmallSolveMaxN = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_solve(MatView<T> F, int n, T *B, int64_t ldb, int nrhs) {
+  __shared__ T ys[kSmallSolveMaxN];
+  __shared__ T acc[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rq = threadIdx.x >> 3, part = threadIdx.x & 7;  // 8 threads per row of a block
+  const int nb = (n + 31) / 32;
+  for (int c = 0; c < nrhs; ++c) {
+    for (int i = threadIdx.x; i < n; i += 256) ys[i] = B[(int64_t)i * ldb + c];
+    __syncthreads();
+    // forward: unit lower L, y overwrites ys
+    for (int blk = 0; blk < nb; ++blk) {
+      const int r0 = 32 * blk;
+      {
+        const int r = r0 + rq, j1 = r0;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        if (r < n)
+          for (int j = part; j < j1; j += 32) {
+            s0 += F.get(r, j) * ys[j];
+            if (j + 8 < j1) s1 += F.get(r, j + 8) * ys[j + 8];
+            if (j + 16 < j1) s2 += F.get(r, j + 16) * ys[j + 16];
+            if (j + 24 < j1) s3 += F.get(r, j + 24) * ys[j + 24];
+          }
+        T sum = (s0 + s1) + (s2 + s3);
+        for (int off = 4; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (part == 0) acc[rq] = (r < n) ? ys[r] - sum : T(0);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const int rl = r0 + lane;
+        T lrow[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) lrow[k] = (rl < n && k < lane && r0 + k < n) ? F.get(rl, r0 + k) : T(0);
+        T v = acc[lane];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const T yk = __shfl_sync(0xffffffffu, v, k);
+          if (lane > k) v -= lrow[k] * yk;
+        }
+        if (rl < n) ys[rl] = v;
+      }
+      __syncthreads();
+    }
+    // backward: U with its diagonal, x overwrites ys
+    for (int blk = nb - 1; blk >= 0; --blk) {
+      const int r0 = 32 * blk, rend = min(n, r0 + 32);
+      {
+        const int r = r0 + rq;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        if (r < n)
+          for (int j = rend + part; j < n; j += 32) {
+            s0 += F.get(r, j) * ys[j];
+            if (j + 8 < n) s1 += F.get(r, j + 8) * ys[j + 8];
+            if (j + 16 < n) s2 += F.get(r, j + 16) * ys[j + 16];
+            if (j + 24 < n) s3 += F.get(r, j + 24) * ys[j + 24];
+          }
+        T sum = (s0 + s1) + (s2 + s3);
+        for (int off = 4; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (part == 0) acc[rq] = (r < n) ? ys[r] - sum : T(0);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const int rl = r0 + lane;
+        T urow[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) urow[k] = (rl < n && k > lane && r0 + k < n) ? F.get(rl, r0 + k) : T(0);
+        const T rc = rl < n ? pivot_rcp(F.get(rl, rl)) : T(0);
+        T v = acc[lane];
+#pragma unroll
+        for (int k = 31; k >= 0; --k) {
+          if (lane == k) v *= rc;
+          const T xk = __shfl_sync(0xffffffffu, v, k);
+          if (lane < k) v -= urow[k] * xk;
+        }
+        if (rl < n) ys[rl] = v;
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += 256) B[(int64_t)i * ldb + c] = ys[i];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Iterative refinement helpers.
 // ---------------------------------------------------------------------------
 

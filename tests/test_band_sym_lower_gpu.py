@@ -80,7 +80,7 @@ def test_lower_half_fp32_and_mixed():
         assert (np.abs(r).max(axis=0) / np.abs(b).max(axis=0)).max() <= 1e-12
 
 
-def test_lower_half_zero_pivot_and_no_cluster():
+def test_lower_half_zero_pivot_and_cluster_path():
     ab = sym_band(200, 20, 73_000, w=0.5)
     kl = 20
     k = 77
@@ -91,10 +91,16 @@ def test_lower_half_zero_pivot_and_no_cluster():
     lower = np.ascontiguousarray(synthetic.dense_to_band(a, kl, kl)[:, :kl + 1])
     f = ebv.band_factor(torch.from_numpy(lower).to(DEV), kl, kl, "fp64", sym="lower")
     assert int(f.info.item()) == k + 1
+    # the cluster-panel factorisation of the same storage gives the same factors
+    ab = sym_band(300, 40, 73_100)
+    kl = 40
+    lower = np.ascontiguousarray(ab[:, :kl + 1])
+    fb, _ = oracle.band_lu(ab, kl, kl)
     lib = ebv.lib()
-    lib.ebv_debug_set_cluster_panel(0)
+    lib.ebv_debug_set_band_cluster(1)
     try:
-        with pytest.raises(ebv.EbvError):
-            ebv.band_factor(torch.from_numpy(lower).to(DEV), kl, kl, "fp64", sym="lower")
+        f = ebv.band_factor(torch.from_numpy(lower).to(DEV), kl, kl, "fp64", sym="lower")
+        assert int(f.info.item()) == 0
+        assert np.abs(f.lu.cpu().numpy() - fb[:, :kl + 1]).max() <= 1e-13
     finally:
-        lib.ebv_debug_set_cluster_panel(1)
+        lib.ebv_debug_set_band_cluster(0)

@@ -1,8 +1,9 @@
 """The thread-block-cluster panel kernel against the CPU oracle, and against
-the one-CTA leaf kernels it replaces (ebv_debug_set_cluster_panel(0)).
+the default paths (one-CTA diagonal blocks with separate L21 / U12 launches).
 
-It factors whole dense systems of order <= 256 and every 64-column panel of
-the banded factorisation (diagonal block, L21 and U12 in one launch).  The
+Switched on (ebv_debug_set_band_cluster(1), ebv_debug_set_small_dense(0)) it
+factors every 64-column panel of the banded factorisation (diagonal block,
+L21 and U12 in one launch) and whole dense systems of order <= 256.  The
 shapes below give panels narrower than 64 (the last one), odd widths (a
 middle column without a partner), bands narrower and wider than a panel,
 and kl != ku.  Tolerances as for the other FP64 paths: factors within 1e-13
@@ -24,8 +25,14 @@ DEV = "cuda"
 @pytest.fixture
 def cluster_switch():
     lib = ebv.lib()
-    yield lib.ebv_debug_set_cluster_panel
-    lib.ebv_debug_set_cluster_panel(1)
+
+    def mode(on):  # on: the cluster panel wherever it can run; off: the defaults
+        lib.ebv_debug_set_cluster_panel(1)
+        lib.ebv_debug_set_band_cluster(1 if on else 0)
+        lib.ebv_debug_set_small_dense(0 if on else 1)
+
+    yield mode
+    mode(0)
 
 
 def _dense(a, prec):

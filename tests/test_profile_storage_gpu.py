@@ -87,11 +87,13 @@ def test_profile_fp64_matches_oracle(name, ab, kl, ku):
     assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-11
     r = oracle.band_residual(ab, kl, ku, x, b)
     assert np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(x).max()) <= 1e-14
-    # FP64 refinement against the profile-stored A (the same residual path)
+    # FP64 refinement against the profile-stored A (its residual kernel reads
+    # the profile; triple-binary32, accurate to ~2^-44 sum |a x|)
     rep = torch.zeros(3, dtype=torch.float64, device=DEV)
-    xr = ebv.solve(f, torch.from_numpy(b).to(DEV), refine=(1e-15, 2), report=rep).cpu().numpy()
+    xr = ebv.solve(f, torch.from_numpy(b).to(DEV), refine=(1e-12, 3), report=rep).cpu().numpy()
     assert np.abs(xr - x_ref).max() / np.abs(x_ref).max() <= 1e-11
-    assert ebv.read_report(rep)["resid_final"] <= 1e-14
+    r_info = ebv.read_report(rep)
+    assert r_info["status"] == 0 and r_info["resid_final"] <= 1e-12
 
 
 @pytest.mark.gpu
