@@ -661,6 +661,13 @@ def _config_band(args, dev):
     ebv.lib().ebv_debug_set_band_cluster(1)
     ms_cluster = _dev_ms(c1, 3, 2)
     ebv.lib().ebv_debug_set_band_cluster(0)
+    # per kernel class (CUDA events around every launch; classes on the
+    # look-ahead's side stream overlap the others)
+    ebv.profile(True)
+    c1()
+    torch.cuda.synchronize()
+    classes = {k: round(v[0], 2) for k, v in ebv.profile_read().items() if v[2] > 0}
+    ebv.profile(False)
     ms = _dev_ms(c1, 3, 2)
     xs = x.cpu().numpy()
     rows = synthetic.pick_indices(11, 512, [n])[:, 0]
@@ -668,7 +675,7 @@ def _config_band(args, dev):
     flops = 2.0 * n * kl * ku + 2.0 * n * (kl + ku) * b.shape[1]
     g = args.band_grid
     out.append({"config": f"band FP64 Laplacian {g}x{g} (n={n}, kl=ku={kl}), 8 RHS", "ms": ms,
-                "ms_cluster_panels": ms_cluster,
+                "ms_cluster_panels": ms_cluster, "class_ms_profiled_run": classes,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
@@ -683,10 +690,14 @@ def _config_band(args, dev):
         ebv.ebv_factor(lu, "fp64", info=info, ws=ws, kl=kl, ku=ku, storage=ebv.BAND_SYM)
         ebv.ebv_solve(lu, x, "fp64", ws=ws, kl=kl, ku=ku, storage=ebv.BAND)
 
+    ebv.lib().ebv_debug_set_band_lookahead(0)
+    ms_sym_no_lookahead = _dev_ms(c1s, 3, 2)
+    ebv.lib().ebv_debug_set_band_lookahead(1)
     ms = _dev_ms(c1s, 3, 2)
     xs = x.cpu().numpy()
     r = oracle.band_residual(ab, kl, ku, xs, b)[rows]
     out.append({"config": f"band FP64 Laplacian {g}x{g}, symmetric storage mode, 8 RHS", "ms": ms,
+                "ms_without_lookahead": ms_sym_no_lookahead,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),

@@ -182,6 +182,12 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *             non-finite pivot.  Always written.
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
+ * FP64 factorisations of the symmetric band storages overlap each panel's
+ * trailing update with the next panel's diagonal block on an internal side
+ * stream of the device, forked from and joined back to `stream` inside the
+ * call (so the call stays stream-ordered and capturable); the first such
+ * call on a device creates that stream and its events: make it before any
+ * stream capture.
  * Band storage (EBV_BAND, EBV_BAND_SYM, EBV_BAND_SYM_LOWER) supports every precision (the mixed ones as above);
  * fill-in stays inside the band because no rows are exchanged.  A band whose width varies row by row
  * (a profile, or skyline, matrix stored in its widest band) costs the work of
@@ -433,6 +439,9 @@ EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
  * results agree to rounding.  Process-wide.
  */
 EBV_API void ebv_debug_set_band_cluster(int32_t enable);
+/* Testing hook: 0 = FP64 band panels without the side-stream look-ahead
+ * (the same results; default 1). */
+EBV_API void ebv_debug_set_band_lookahead(int32_t enable);
 EBV_API void ebv_debug_set_cluster_panel(int32_t enable);
 
 /*

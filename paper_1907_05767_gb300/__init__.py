@@ -92,6 +92,7 @@ _SIGNATURES = [
     ("ebv_debug_set_band_envelope", None, [_I32]),
     ("ebv_debug_set_cluster_panel", None, [_I32]),
     ("ebv_debug_set_band_cluster", None, [_I32]),
+    ("ebv_debug_set_band_lookahead", None, [_I32]),
     ("ebv_debug_set_small_dense", None, [_I32]),
     ("ebv_debug_residual", _I32, [_I64, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     ("ebv_debug_lowp_update", _I32, [_I32, _I32, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _I64, _I64, _I64, _I64, _I64,

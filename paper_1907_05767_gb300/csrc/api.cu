@@ -150,6 +150,9 @@ ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu
 // instead of substitution panels.
 void ebv_debug_set_small_dense(int32_t panels) { set_small_dense_panels(panels != 0); }
 
+// Testing hook: 0 = FP64 band panels without the look-ahead side stream.
+void ebv_debug_set_band_lookahead(int32_t enable) { set_band_lookahead(enable != 0); }
+
 // Testing hook: 1 = band panels on thread-block clusters.
 void ebv_debug_set_band_cluster(int32_t enable) { set_band_cluster(enable != 0); }
 

@@ -16,6 +16,7 @@
 // whose width varies costs the work of its envelope, not of its widest row.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -67,104 +68,6 @@ __global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, 
     }
   }
   if (lane == 0) atomicMin(&up[i / 64], (int32_t)first);
-}
-
-// LU of one 64 x 64 diagonal block (FP64 panels; no inverses), unblocked
-// Doolittle with the block in registers: warp w owns the column pairs
-// {p, 63-p} for p = 4w .. 4w+3 (the long/short pairing of Eq. 7: every warp
-// holds the same amount of work over the 64 steps), lane l rows 2l and 2l+1.
-// Step k: every warp takes the L vector of column k from shared memory
-// (Eq. 6a) and row k of its own columns from the lane holding it, and
-// updates its columns right of k (Eq. 6c).  The owner of column k+1 updates
-// that column first, then forms its pivot's FP64 reciprocal and L vector
-// into the other half of a double buffer, so one block barrier per step
-// orders everything and the division overlaps the other warps' updates.
-// The block's rows and columns past w are an identity (no pivot there).
-template <typename T>
-__global__ void __launch_bounds__(256) k_diag_lu64(MatView<T> A, int64_t k0, int w, int32_t *info) {
-  constexpr int NB = 64;
-  __shared__ T Lb[2][NB];
-  __shared__ int bad;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r0 = 2 * lane, r1 = r0 + 1;
-  auto col_of = [&](int s) { return s < 4 ? 4 * warp + s : NB - 1 - (4 * warp + s - 4); };
-  T v[8][2];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int c = col_of(s);
-    v[s][0] = (r0 < w && c < w) ? A.get(k0 + r0, k0 + c) : (r0 == c ? T(1) : T(0));
-    v[s][1] = (r1 < w && c < w) ? A.get(k0 + r1, k0 + c) : (r1 == c ? T(1) : T(0));
-  }
-  if (threadIdx.x == 0) bad = NB;
-  // owner (warp, slot) of column j
-  auto owner = [](int j, int &ow, int &os) {
-    const int p = min(j, NB - 1 - j);
-    ow = p / 4;
-    os = (j == p) ? p % 4 : 4 + p % 4;
-  };
-  // column j (held in slot s of this warp) becomes L: reciprocal of its pivot
-  // (FP64), rows below scaled and published to Lb[buf]
-  auto publish = [&](int j, int s, int buf) {
-    T pv = T(0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (q == s) pv = __shfl_sync(0xffffffffu, (j & 1) ? v[q][1] : v[q][0], j >> 1);
-    T rc = T(0);
-    if (lane == 0) {
-      rc = pivot_rcp(pv);
-      if (pivot_bad(pv) && j < w) atomicMin(&bad, j);
-    }
-    rc = __shfl_sync(0xffffffffu, rc, 0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (q == s) {
-        if (r0 > j) v[q][0] *= rc;
-        if (r1 > j) v[q][1] *= rc;
-        Lb[buf][r0] = r0 > j ? v[q][0] : T(0);
-        Lb[buf][r1] = r1 > j ? v[q][1] : T(0);
-      }
-  };
-  {
-    int ow, os;
-    owner(0, ow, os);
-    if (warp == ow) publish(0, os, 0);
-  }
-  __syncthreads();
-  for (int k = 0; k < NB - 1; ++k) {
-    const T l0 = Lb[k & 1][r0], l1 = Lb[k & 1][r1];
-    int ow, os;
-    owner(k + 1, ow, os);
-    const int first = (warp == ow) ? os : -1;
-    // row k of slot s from the lane holding it, then Eq. 6c on rows > k
-    auto update = [&](int s) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q == s) {
-          const T u = __shfl_sync(0xffffffffu, (k & 1) ? v[q][1] : v[q][0], k >> 1);
-          if (col_of(q) > k) {
-            v[q][0] -= l0 * u;
-            v[q][1] -= l1 * u;
-          }
-        }
-    };
-    if (first >= 0) {
-      update(first);
-      publish(k + 1, first, (k + 1) & 1);
-    }
-#pragma unroll
-    for (int s = 0; s < 8; ++s)
-      if (s != first) update(s);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && bad < w && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int c = col_of(s);
-    if (c < w) {
-      if (r0 < w) A.put(k0 + r0, k0 + c, v[s][0]);
-      if (r1 < w) A.put(k0 + r1, k0 + c, v[s][1]);
-    }
-  }
 }
 
 // L21 = A21 U11^{-1} by substitution (FP64 panels): one warp per row of
@@ -244,7 +147,35 @@ __global__ void __launch_bounds__(256) k_trsm_ll_subst(MatView<T> A, int64_t c0,
   }
 }
 
+// Side stream and events of the FP64 panels' look-ahead, one set per device,
+// made by the first factorisation on the device.
+struct BandPipe {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, go = nullptr, join = nullptr, done[2] = {};
+  bool ready = false;
+};
+constexpr int kMaxPipeDevices = 64;
+BandPipe g_band_pipe[kMaxPipeDevices];
+std::mutex g_band_pipe_mutex;
+
+ebv_status_t band_pipe(BandPipe **out) {
+  int dev = 0;
+  EBV_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxPipeDevices) return EBV_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_band_pipe_mutex);
+  BandPipe &p = g_band_pipe[dev];
+  if (!p.ready) {
+    EBV_CU(cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&p.fork, &p.go, &p.join, &p.done[0], &p.done[1]})
+      EBV_CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    p.ready = true;
+  }
+  *out = &p;
+  return EBV_OK;
+}
+
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
+bool g_band_lookahead = true; // FP64 panels: trailing update split for look-ahead (testing hook)
 bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
 // General bands: one-CTA diagonal blocks (false) or cluster panels (true).
 // Measured on the 512 x 512 Laplacian, factor + solve: 1113 ms one-CTA
@@ -311,6 +242,17 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
   // lower-half symmetric storage that view reads a_ji above the diagonal.
   MatView<T> Araw = A;
   Araw.symraw = true;
+  // FP64 look-ahead for the symmetric storages (whose trailing updates, the
+  // block-lower half only, leave the diagonal block's SM its FP64 units;
+  // measured on the 512 x 512 Laplacian: 899 -> 843 ms, while the general
+  // band's full updates made it slower, 933 -> 1009 ms).  The side stream
+  // joins `s` here and `s` waits for it at the end.
+  BandPipe *pipe = nullptr;
+  if (sizeof(T) == 8 && sym && g_band_subst && g_band_lookahead && !cluster && n > 2 * kNB) {
+    EBV_TRY(band_pipe(&pipe));
+    EBV_CU(cudaEventRecord(pipe->fork, s));
+    EBV_CU(cudaStreamWaitEvent(pipe->side, pipe->fork, 0));
+  }
   for (int64_t c0 = 0; c0 < n; c0 += kNB) {
     const int w = (int)std::min<int64_t>(kNB, n - c0);
     const int64_t rb = c0 + w, re = std::min<int64_t>(n, c0 + w + A.kl);
@@ -341,11 +283,19 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
     }
     if constexpr (sizeof(T) == 8) {
       if (g_band_subst) {
-        // FP64: the diagonal block factored alone (no inverses: two thirds of
-        // its FP64 work), then L21 and U12 by substitution over many SMs.
+        // FP64: the diagonal block factored alone (no inverses: two thirds
+        // of its FP64 work), then L21 and U12 by substitution over many SMs.
+        // Look-ahead (symmetric storages): the trailing update is split into
+        // the next panel's 64 columns (on `s`, the critical path) and the
+        // rest (on the side stream, overlapping the next diagonal block,
+        // which runs on one SM).  Panel p's diagonal block and L21 wait for
+        // the rest-update of panel p-2, its U12 for that of panel p-1 (the
+        // only ones touching those entries).
+        const int64_t p = c0 / kNB;
+        if (pipe && p >= 2) EBV_CU(cudaStreamWaitEvent(s, pipe->done[p & 1], 0));
         {
           prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-          k_diag_lu64<T><<<1, 256, 0, s>>>(Araw, c0, w, info);
+          k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, nullptr);
           EBV_TRY(launch_ok());
         }
         if (re > rb) {
@@ -353,6 +303,7 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
           k_trsm_ru_subst<T, kNB><<<ceil_div(re - rb, 8), 256, 0, s>>>(A, c0, w, rb, re, env);
           EBV_TRY(launch_ok());
         }
+        if (pipe && p >= 1) EBV_CU(cudaStreamWaitEvent(s, pipe->done[(p - 1) & 1], 0));
         if (ce > cb && sym) {
           if (!A.symlo) {  // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
             prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
@@ -365,13 +316,24 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
           EBV_TRY(launch_ok());
         }
         if (re > rb && ce > cb) {
-          prof::Scope ps(s, prof::kSimtGemm, 2.0 * (re - rb) * (ce - cb) * w);
-          dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
-          k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
-              <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0,
-                                                                  env);
-          EBV_TRY(launch_ok());
+          auto gemm = [&](int64_t n0, int64_t n1, cudaStream_t st) -> ebv_status_t {
+            if (n1 <= n0) return EBV_OK;
+            prof::Scope ps(st, prof::kSimtGemm, 2.0 * (re - rb) * (n1 - n0) * w);
+            dim3 grid(ceil_div(n1 - n0, G::BN), ceil_div(re - rb, G::BM));
+            k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
+                <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(A, rb, n0, c0, re - rb, n1 - n0, w,
+                                                                     sym ? 1 : 0, env);
+            return launch_ok();
+          };
+          const int64_t split = pipe ? std::min<int64_t>(ce, cb + kNB) : ce;
+          EBV_TRY(gemm(cb, split, s));
+          if (split < ce) {
+            EBV_CU(cudaEventRecord(pipe->go, s));
+            EBV_CU(cudaStreamWaitEvent(pipe->side, pipe->go, 0));
+            EBV_TRY(gemm(split, ce, pipe->side));
+          }
         }
+        if (pipe) EBV_CU(cudaEventRecord(pipe->done[p & 1], pipe->side));
         continue;
       }
     }
@@ -415,6 +377,10 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
           <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, s>>>(A, rb, cb, c0, re - rb, ce - cb, w, sym ? 1 : 0, env);
       EBV_TRY(launch_ok());
     }
+  }
+  if (pipe) {
+    EBV_CU(cudaEventRecord(pipe->join, pipe->side));
+    EBV_CU(cudaStreamWaitEvent(s, pipe->join, 0));
   }
   return EBV_OK;
 }
@@ -506,6 +472,7 @@ size_t band_factor_ws(int64_t n, int64_t kl, int64_t, ebv_prec_t prec) {
 }
 void set_band_envelope(bool on) { g_band_envelope = on; }
 void set_band_cluster(bool on) { g_band_cluster = on; }
+void set_band_lookahead(bool on) { g_band_lookahead = on; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
 }

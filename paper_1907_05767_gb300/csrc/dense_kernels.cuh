@@ -1370,9 +1370,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
   const int64_t bm = m0 + (int64_t)blockIdx.y * BM, bn = n0 + (int64_t)blockIdx.x * BN;
   const int64_t mend = m0 + M, nend = n0 + N, kend = k0 + K;
-  // lower64 (symmetric update, m0 == n0): only the tiles of 64-blocks on or
-  // below the diagonal (BM, BN divide 64).
-  if (lower64 && (bn - n0) / 64 > (bm - m0) / 64) return;
+  // lower64 (symmetric update): only the tiles of 64-blocks on or below the
+  // diagonal (absolute block indices; BM, BN divide 64).
+  if (lower64 && bn / 64 > bm / 64) return;
   // outside the envelope (BM, BN divide 64 and m0, n0 start 64-blocks): nothing to subtract
   if (env.rows_empty(bm, k0 + K) || env.cols_empty(bn, k0 + K)) return;
   T acc[TM][TN];

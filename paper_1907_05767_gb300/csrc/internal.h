@@ -32,6 +32,8 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
 void set_band_envelope(bool on);
 // Testing hook: true = band panels on thread-block clusters (default false).
 void set_band_cluster(bool on);
+// Testing hook: false = FP64 band panels without look-ahead (default true).
+void set_band_lookahead(bool on);
 // Dense FP64 factorisation of a small system as right-looking 64-column
 // panels (band.cu); orders up to kSmallDenseMaxN use it.
 ebv_status_t dense_small_factor(double *a, int64_t ld, int64_t n, int32_t *info, void *ws, cudaStream_t s);
