@@ -588,6 +588,8 @@ def run_configs(args):
         out.append(run_profile_config(args))
     if want("band_mixed"):
         out.append(run_band_mixed_config(args))
+    if want("dense_sym"):
+        out.append(_config_dense_sym(args, dev))
     return out
 
 
@@ -661,6 +663,10 @@ def _config_band(args, dev):
     ebv.lib().ebv_debug_set_band_cluster(1)
     ms_cluster = _dev_ms(c1, 3, 2)
     ebv.lib().ebv_debug_set_band_cluster(0)
+    # the same with the blocked 16 x 16 sub-block diagonal-block kernel
+    ebv.lib().ebv_debug_set_diag_lu(0)
+    ms_diag_blocked = _dev_ms(c1, 3, 2)
+    ebv.lib().ebv_debug_set_diag_lu(1)
     # per kernel class (CUDA events around every launch; classes on the
     # look-ahead's side stream overlap the others)
     ebv.profile(True)
@@ -675,7 +681,8 @@ def _config_band(args, dev):
     flops = 2.0 * n * kl * ku + 2.0 * n * (kl + ku) * b.shape[1]
     g = args.band_grid
     out.append({"config": f"band FP64 Laplacian {g}x{g} (n={n}, kl=ku={kl}), 8 RHS", "ms": ms,
-                "ms_cluster_panels": ms_cluster, "class_ms_profiled_run": classes,
+                "ms_cluster_panels": ms_cluster, "ms_blocked_diag_kernel": ms_diag_blocked,
+                "class_ms_profiled_run": classes,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
                 "backward_error_sampled": float(np.abs(r).max() / (np.abs(ab).sum(axis=1).max() * np.abs(xs).max())),
@@ -763,6 +770,55 @@ def _config_fp16(args, dev):
     print(json.dumps(out[-1]), flush=True)
     del A, B, lowp, x, ws
     return out[-1]
+
+
+def _config_dense_sym(args, dev):
+    """The symmetric mode on the dense n = 16384, 32 RHS matrix made
+    symmetric: FP64 LDL^T in the lower triangle (n^3/3 flops) against the
+    general FP64 factorisation of the same matrix (2n^3/3)."""
+    import torch
+
+    import oracle
+    import paper_1907_05767_gb300 as ebv
+    import synthetic
+    a, _, _ = synthetic.config2(args.n, args.nrhs)
+    a = np.tril(a) + np.tril(a, -1).T  # symmetric, still strictly diagonally dominant
+    n, nrhs = a.shape[0], args.nrhs
+    x_true = synthetic.planted_x(n, nrhs, 90_001)
+    b = synthetic.rhs_for(a, x_true)
+    A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    lu, x = torch.empty_like(A), torch.empty_like(B)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ebv.workspace(n, "fp64", nrhs, dev, storage=ebv.DENSE_SYM)
+    wsg = ebv.workspace(n, "fp64", nrhs, dev)
+
+    def sym():
+        lu.copy_(A)
+        x.copy_(B)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=ws, storage=ebv.DENSE_SYM)
+        ebv.ebv_solve(lu, x, "fp64", ws=ws, storage=ebv.DENSE_SYM)
+
+    def gen():
+        lu.copy_(A)
+        x.copy_(B)
+        ebv.ebv_factor(lu, "fp64", info=info, ws=wsg)
+        ebv.ebv_solve(lu, x, "fp64", ws=wsg)
+
+    ms_gen = _dev_ms(gen, 1, 1)
+    ms = _dev_ms(sym, 2, 1)
+    xs = x.cpu().numpy()
+    r = oracle.residual(a, xs, b)
+    flops = n ** 3 / 3 + 2 * n * n * nrhs
+    line = {"config": f"dense symmetric n={n}, {nrhs} RHS, FP64 LDL^T in the lower triangle", "ms": ms,
+            "gflops": flops / (ms / 1e3) / 1e9, "ms_general_fp64": ms_gen,
+            "speedup_vs_general": ms_gen / ms, "info": int(info.item()),
+            "backward_error": float(np.abs(r).max() / (np.abs(a).sum(axis=1).max() * np.abs(xs).max())),
+            "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
+            "note": "flops credited: n^3/3 + 2 n^2 nrhs (the symmetric factorisation's own work)"}
+    print(json.dumps(line), flush=True)
+    del A, B, lu, x, ws, wsg
+    torch.cuda.empty_cache()
+    return line
 
 
 def _config_batched(args, dev):
@@ -1101,7 +1157,7 @@ def main():
     p.add_argument("--no-graph", dest="graph", action="store_false")
     p.add_argument("--update-only", default=None, help="M,N,K: time the tensor-core update alone and exit")
     p.add_argument("--configs", nargs="?", const="all", default=None,
-                   help="time the other workloads (one JSON line each) and exit; --configs inverse / profile / band_mixed: "
+                   help="time the other workloads (one JSON line each) and exit; --configs inverse / profile / band_mixed / dense_sym: "
                         "one alone")
     p.add_argument("--inverse-n", type=int, default=8192, help="order of the explicit-inverse workload")
     p.add_argument("--band-grid", type=int, default=512, help="grid edge of the banded Laplacian workload")

@@ -98,10 +98,9 @@ typedef enum {
  * i - kl <= j <= i, ld >= kl + 1, ku == kl (half the memory of EBV_BAND_SYM).
  * ebv_factor leaves the LDL^T form in the same array: L strictly below the
  * diagonal (unit diagonal implied) and the pivots d_i = u_ii on it, since
- * U = D L^T.  ebv_solve takes the factors in that storage.  The factorisation
- * runs its panels on a thread-block cluster (EBV_ERR_UNSUPPORTED on a device
- * that cannot, or with ebv_debug_set_cluster_panel(0)).  (Project addition,
- * the LDL^T reading of Eq. 6a-b with both its flops and its storage halved.)
+ * U = D L^T.  ebv_solve takes the factors in that storage.  (Project
+ * addition, the LDL^T reading of Eq. 6a-b with both its flops and its
+ * storage halved.)
  */
 /*
  * EBV_PROFILE: a matrix whose band width varies row by row (a profile, or
@@ -120,18 +119,31 @@ typedef enum {
  * EBV_FP64 and EBV_FP32 only; a band whose few wide rows would make band
  * storage pay their width on every row stores only its profile.
  */
+/*
+ * EBV_DENSE_SYM: a symmetric dense A, row-major with ld >= n, of which only
+ * the lower triangle (a_ij, j <= i) is read; the entries above the diagonal
+ * are never read nor written.  ebv_factor leaves the LDL^T form in the lower
+ * triangle (L strictly below the diagonal, unit diagonal implied, the pivots
+ * d_i = u_ii on it; U = D L^T, Eq. 6a-b), forming only the block-lower part
+ * of each trailing update: n^3/3 flops instead of 2n^3/3.  ebv_solve takes the
+ * factors in that storage (refinement, FP64 only, reads A's lower triangle
+ * from a_orig).  EBV_FP64 and EBV_FP32; the mixed precisions return
+ * EBV_ERR_UNSUPPORTED, as do ebv_inverse and ebv_gesv_host.  desc->kl / ku
+ * are ignored.  (Project addition: the dense form of the symmetric mode.)
+ */
 typedef enum {
   EBV_DENSE = 0,
   EBV_BAND = 1,
   EBV_BAND_SYM = 2,
   EBV_BAND_SYM_LOWER = 3,
-  EBV_PROFILE = 4
+  EBV_PROFILE = 4,
+  EBV_DENSE_SYM = 5
 } ebv_storage_t;
 
 typedef struct ebv_desc {
   int64_t n;       /* order of A, n >= 0 */
   int64_t ld;      /* row stride in elements (dense: >= n; band: >= kl+ku+1; lower half: >= kl+1) */
-  int64_t kl, ku;  /* band widths, 0 <= kl, ku < n (ignored for EBV_DENSE) */
+  int64_t kl, ku;  /* band widths, 0 <= kl, ku < n (ignored for EBV_DENSE and EBV_DENSE_SYM) */
   int32_t storage; /* ebv_storage_t */
   int32_t reserved;
 } ebv_desc_t;
@@ -443,6 +455,12 @@ EBV_API void ebv_debug_set_band_cluster(int32_t enable);
  * (the same results; default 1). */
 EBV_API void ebv_debug_set_band_lookahead(int32_t enable);
 EBV_API void ebv_debug_set_cluster_panel(int32_t enable);
+/* Testing hook: 0 = the FP64 panels' 64 x 64 diagonal blocks (band storages,
+ * dense FP64 systems of order <= 256) on the blocked 16 x 16 sub-block
+ * kernel instead of the register-resident one (default 1).  Both compute
+ * the same Doolittle factors; the rounding of the updates may differ.
+ * Process-wide. */
+EBV_API void ebv_debug_set_diag_lu(int32_t enable);
 
 /*
  * Testing hook: dense FP64 systems of order <= 256 are factored as

@@ -34,7 +34,7 @@ OK, ERR_ARG, ERR_ZERO_PIVOT, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_
 # ebv_prec_t
 FP64, FP32, MIXED_BF16, MIXED_FP16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
-DENSE, BAND, BAND_SYM, BAND_SYM_LOWER, PROFILE = 0, 1, 2, 3, 4
+DENSE, BAND, BAND_SYM, BAND_SYM_LOWER, PROFILE, DENSE_SYM = 0, 1, 2, 3, 4, 5
 
 
 class EbvError(RuntimeError):
@@ -93,6 +93,7 @@ _SIGNATURES = [
     ("ebv_debug_set_cluster_panel", None, [_I32]),
     ("ebv_debug_set_band_cluster", None, [_I32]),
     ("ebv_debug_set_band_lookahead", None, [_I32]),
+    ("ebv_debug_set_diag_lu", None, [_I32]),
     ("ebv_debug_set_small_dense", None, [_I32]),
     ("ebv_debug_residual", _I32, [_I64, _VP, _I64, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     ("ebv_debug_lowp_update", _I32, [_I32, _I32, _VP, _I64, _VP, _VP, _I64, _VP, _I64, _I64, _I64, _I64, _I64, _I64,
@@ -185,7 +186,8 @@ def _need_cuda(*ts):
 # ----------------------------------------------------------------------------
 
 def ebv_workspace_size(n, prec, nrhs=0, ld=None, kl=0, ku=0, storage=DENSE) -> int:
-    d = _desc(n, ld if ld is not None else (max(1, n) if storage == DENSE else kl + ku + 1), kl, ku, storage)
+    d = _desc(n, ld if ld is not None else (max(1, n) if storage in (DENSE, DENSE_SYM) else kl + ku + 1), kl, ku,
+              storage)
     return int(lib().ebv_workspace_size(ctypes.byref(d), _prec(prec), int(nrhs)))
 
 
@@ -352,11 +354,18 @@ class Factors:
     storage: int = DENSE
 
 
-def factor(a: torch.Tensor, prec="fp64", keep_a: bool = True) -> Factors:
+def factor(a: torch.Tensor, prec="fp64", keep_a: bool = True, sym: bool = False) -> Factors:
     """Factor a dense matrix.  FP64/FP32: a copy of ``a`` is factored.  Mixed:
-    ``a`` (FP64) is kept and the FP32 factors go to a new tensor."""
+    ``a`` (FP64) is kept and the FP32 factors go to a new tensor.  sym=True
+    (FP64/FP32): A symmetric, only its lower triangle read; the factors keep
+    L below the diagonal and the pivots on it (EBV_DENSE_SYM)."""
     p = _prec(prec)
     n = a.shape[0]
+    if sym:
+        dt = torch.float64 if p == FP64 else torch.float32
+        lu = a.to(dt).clone().contiguous()
+        info = ebv_factor(lu, p, storage=DENSE_SYM)
+        return Factors(lu, info, p, a.to(torch.float64).contiguous() if keep_a else None, storage=DENSE_SYM)
     if p in (MIXED_BF16, MIXED_FP16):
         a64 = a.to(torch.float64).contiguous()
         lowp = torch.empty((n, n), dtype=torch.float32, device=a.device)

@@ -37,7 +37,7 @@ bool is_mixed(ebv_prec_t p) { return p == EBV_MIXED_BF16 || p == EBV_MIXED_FP16;
 ebv_status_t check_desc(const ebv_desc_t *d, ebv_prec_t prec) {
   if (!d || !valid_prec(prec)) return EBV_ERR_ARG;
   if (d->n < 0 || d->n > kMaxN) return EBV_ERR_ARG;
-  if (d->storage == EBV_DENSE) {
+  if (d->storage == EBV_DENSE || d->storage == EBV_DENSE_SYM) {
     if (d->ld < std::max<int64_t>(1, d->n)) return EBV_ERR_ARG;
   } else if (d->storage == EBV_BAND || d->storage == EBV_BAND_SYM || d->storage == EBV_BAND_SYM_LOWER) {
     if (d->kl < 0 || d->ku < 0) return EBV_ERR_ARG;
@@ -78,7 +78,7 @@ size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64_t nrhs)
   if (check_desc(desc, prec) != EBV_OK || nrhs < 0) return 0;
   const int64_t n = desc->n;
   if (desc->storage != EBV_DENSE)
-    return std::max(band_factor_ws(n, desc->kl, desc->ku, prec), band_solve_ws(n, nrhs, prec));
+    return std::max(band_factor_ws(n, ws_kl(desc), desc->ku, prec), band_solve_ws(n, nrhs, prec));
   return std::max(dense_factor_ws(n, prec), dense_solve_ws(n, nrhs, prec));
 }
 
@@ -87,12 +87,12 @@ ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *
   EBV_TRY(check_desc(desc, prec));
   if (!info_dev || !aligned(info_dev, 4)) return EBV_ERR_ARG;
   if (desc->n > 0 && (!a || !aligned(a, desc->storage == EBV_PROFILE ? 256 : elem_size(prec)))) return EBV_ERR_ARG;
-  if (desc->storage == EBV_PROFILE && is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
+  if ((desc->storage == EBV_PROFILE || desc->storage == EBV_DENSE_SYM) && is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
   if (is_mixed(prec) && desc->n > 0 && (!lowp || !aligned(lowp, 16))) return EBV_ERR_ARG;
   if (ws && !aligned(ws, 256)) return EBV_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (desc->storage != EBV_DENSE) {
-    if (!ws || ws_bytes < band_factor_ws(desc->n, desc->kl, desc->ku, prec)) return EBV_ERR_WORKSPACE;
+    if (!ws || ws_bytes < band_factor_ws(desc->n, ws_kl(desc), desc->ku, prec)) return EBV_ERR_WORKSPACE;
     return band_factor(desc, prec, a, lowp, info_dev, ws, ws_bytes, s);
   }
   const size_t need = dense_factor_ws(desc->n, prec);
@@ -109,7 +109,7 @@ ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, 
   const size_t bsz = prec == EBV_FP32 ? 4 : 8;
   const size_t fsz = prec == EBV_FP64 ? 8 : 4;
   if (any && (!lu || !aligned(lu, desc->storage == EBV_PROFILE ? 256 : fsz) || !b || !aligned(b, bsz))) return EBV_ERR_ARG;
-  if (desc->storage == EBV_PROFILE && is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
+  if ((desc->storage == EBV_PROFILE || desc->storage == EBV_DENSE_SYM) && is_mixed(prec)) return EBV_ERR_UNSUPPORTED;
   const bool need_a = is_mixed(prec) && refine;
   if (refine) {
     if (!(refine->tol >= 0.0) || refine->max_iter < 0 || refine->max_iter > 1000) return EBV_ERR_ARG;
@@ -149,6 +149,9 @@ ebv_status_t ebv_inverse(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu
 // Testing hook: 0 = small dense FP64 systems on one thread-block cluster
 // instead of substitution panels.
 void ebv_debug_set_small_dense(int32_t panels) { set_small_dense_panels(panels != 0); }
+
+// Testing hook: 0 = FP64 panels' diagonal blocks on the blocked sub-block kernel.
+void ebv_debug_set_diag_lu(int32_t enable) { set_diag_lu(enable != 0); }
 
 // Testing hook: 0 = FP64 band panels without the look-ahead side stream.
 void ebv_debug_set_band_lookahead(int32_t enable) { set_band_lookahead(enable != 0); }

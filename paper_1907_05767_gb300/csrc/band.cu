@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -43,8 +44,8 @@ struct BandGemm<float> {
 // what it found (i itself when the part is empty).  lo and up start above any
 // index.  The column scan reads one element per row (stride ld) but stops at
 // the first non-zero, which for a band matrix is near the band edge.
-template <typename T>
-__global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, int32_t *lo, int32_t *up) {
+template <typename T, bool XV>
+__global__ void __launch_bounds__(256) k_band_envelope(MatView<T, XV> A, int64_t n, int32_t *lo, int32_t *up) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
   if (i >= n) return;
@@ -78,8 +79,8 @@ __global__ void __launch_bounds__(256) k_band_envelope(MatView<T> A, int64_t n, 
 // 64-step chain per row needs no inverse of U11, so the diagonal-block kernel
 // only factors; rows run on many SMs.  Rows of 64-blocks outside the
 // envelope hold zeros and are skipped.
-template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_trsm_ru_subst(MatView<T> A, int64_t c0, int w, int64_t rb, int64_t re,
+template <typename T, int NB, bool XV>
+__global__ void __launch_bounds__(256) k_trsm_ru_subst(MatView<T, XV> A, int64_t c0, int w, int64_t rb, int64_t re,
                                                        Envelope env) {
   __shared__ T Us[NB][NB + 1];
   __shared__ T rc[NB];
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(256) k_trsm_ru_subst(MatView<T> A, int64_t c0,
 // A12 (8 per CTA, the 64 x 8 block staged with whole rows); lane l holds rows
 // l and l+32.  Step k: u_kj is final; it goes by shuffle to every lane,
 // which subtracts l_rk u_kj from its later rows r (Eq. 6b; L11 unit lower).
-template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_trsm_ll_subst(MatView<T> A, int64_t c0, int w, int64_t cb, int64_t ce,
+template <typename T, int NB, bool XV>
+__global__ void __launch_bounds__(256) k_trsm_ll_subst(MatView<T, XV> A, int64_t c0, int w, int64_t cb, int64_t ce,
                                                        Envelope env) {
   __shared__ T Ls[NB][NB + 1];
   __shared__ T Bs[NB][8 + 1];
@@ -177,6 +178,9 @@ ebv_status_t band_pipe(BandPipe **out) {
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
 bool g_band_lookahead = true; // FP64 panels: trailing update split for look-ahead (testing hook)
 bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
+// FP64 panels' diagonal blocks: the register-resident kernel (true) or the
+// blocked 16 x 16 sub-block kernel (testing hook)
+bool g_diag_lu = true;
 // General bands: one-CTA diagonal blocks (false) or cluster panels (true).
 // Measured on the 512 x 512 Laplacian, factor + solve: 1113 ms one-CTA
 // against 1233 ms on clusters, so the cluster panels serve the lower-half
@@ -197,10 +201,10 @@ __global__ void __launch_bounds__(256) k_band_narrow(const double *ab, float *lo
 size_t profile_header_bytes(int64_t n) { return align256((size_t)24 * (size_t)ceil_div(n, kNB)); }
 
 template <typename T>
-MatView<T> profile_view(void *buf, int64_t n, int64_t kl, int64_t ku) {
+XView<T> profile_view(void *buf, int64_t n, int64_t kl, int64_t ku) {
   const int64_t nb = ceil_div(n, kNB);
   char *h = (char *)buf;
-  MatView<T> v{(T *)(h + profile_header_bytes(n)), 0, kl, ku};
+  XView<T> v{(T *)(h + profile_header_bytes(n)), 0, kl, ku};
   v.plo = (const int32_t *)h;
   v.pup = (const int32_t *)(h + 4 * nb);
   v.poffL = (const int64_t *)(h + 8 * nb);
@@ -208,12 +212,13 @@ MatView<T> profile_view(void *buf, int64_t n, int64_t kl, int64_t ku) {
   return v;
 }
 
-template <typename T>
-ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym, T *bcast,
+template <typename T, bool XV>
+ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, int32_t *env_lo, bool sym, T *bcast,
                            cudaStream_t s, bool envelope = true) {
   const Shadow<float> none{nullptr, nullptr, 0, nullptr};
   using G = BandGemm<T>;
   EBV_TRY((prepare_leaf_kernels<T, float>()));
+  if constexpr (XV) EBV_TRY(prepare_xview_kernels<T>());
   constexpr size_t smem = pair_smem_bytes<T, kNB>();
   Envelope env;
   if (A.plo) {  // profile storage: the stored extents are the block envelope
@@ -236,11 +241,11 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
   // other band storages keep the one-CTA diagonal-block kernels, measured
   // faster on the 512 x 512 Laplacian (1119 ms against 1504 ms per
   // factor + solve).
-  bool cluster = !A.plo && g_band_cluster && cluster_panel_enabled() &&
+  bool cluster = !A.plo && A.kl < kDenseBand && g_band_cluster && cluster_panel_enabled() &&
                  cluster_panel_fits(sizeof(T) == 8, kNB, std::min<int64_t>(n, kNB + A.kl), sym ? 0 : A.ku);
   // The diagonal-block kernel reads its still unfactored block; in the
   // lower-half symmetric storage that view reads a_ji above the diagonal.
-  MatView<T> Araw = A;
+  MatView<T, XV> Araw = A;
   Araw.symraw = true;
   // FP64 look-ahead for the symmetric storages (whose trailing updates, the
   // block-lower half only, leave the diagonal block's SM its FP64 units;
@@ -295,7 +300,10 @@ ebv_status_t band_factor_t(MatView<T> A, int64_t n, int32_t *info, T *inv, int32
         if (pipe && p >= 2) EBV_CU(cudaStreamWaitEvent(s, pipe->done[p & 1], 0));
         {
           prof::Scope ps(s, prof::kPanel, 2.0 * w * w * w / 3.0);
-          k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, nullptr);
+          if (g_diag_lu)
+            k_diag_lu<T><<<1, 256, 0, s>>>(Araw, c0, w, info);
+          else
+            k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, nullptr);
           EBV_TRY(launch_ok());
         }
         if (re > rb) {
@@ -422,10 +430,11 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// R = B - A X through a view (profile storage), as k_band_residual_df: one
-// warp per row over the view's window, entries outside the profile read 0.
+// R = B - A X through a view (profile storage, the lower triangle of a
+// symmetric dense matrix), as k_band_residual_df: one warp per row over the
+// view's window, entries outside the profile read 0.
 __global__ void __launch_bounds__(256)
-    k_view_residual_df(MatView<double> A, int64_t n, const float *xhi, const float *xlo, int nrhs, const double *B,
+    k_view_residual_df(XView<double> A, int64_t n, const float *xhi, const float *xlo, int nrhs, const double *B,
                        int64_t ldb, double *R, int64_t ldr, unsigned long long *rmax, const DevStatus *st) {
   if (st && st->done) return;
   const int lane = threadIdx.x & 31;
@@ -438,7 +447,7 @@ __global__ void __launch_bounds__(256)
     for (int64_t j = j0 + lane; j <= j1; j += 32) {
       if (!A.in(i, j)) continue;
       float a_h, a_l;
-      split_f64(*A.at(i, j), a_h, a_l);
+      split_f64(A.raw(i, j), a_h, a_l);
       acc.fma_split(a_h, a_l, xhi[j * nrhs + c], xlo[j * nrhs + c]);
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -473,6 +482,7 @@ size_t band_factor_ws(int64_t n, int64_t kl, int64_t, ebv_prec_t prec) {
 void set_band_envelope(bool on) { g_band_envelope = on; }
 void set_band_cluster(bool on) { g_band_cluster = on; }
 void set_band_lookahead(bool on) { g_band_lookahead = on; }
+void set_diag_lu(bool on) { g_diag_lu = on; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;
 }
@@ -482,12 +492,21 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
   EBV_CU(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   if (ws) EBV_CU(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
   if (d->n == 0) return EBV_OK;
-  if (!ws || ws_bytes < band_factor_ws(d->n, d->kl, d->ku, prec)) return EBV_ERR_WORKSPACE;
+  if (!ws || ws_bytes < band_factor_ws(d->n, ws_kl(d), d->ku, prec)) return EBV_ERR_WORKSPACE;
   char *inv = (char *)ws + kStatusBytes;
   int32_t *env = (int32_t *)(inv + band_inv_bytes(prec));
   char *bcast = (char *)env + band_env_bytes(d->n);
   const bool lower = d->storage == EBV_BAND_SYM_LOWER;
   const bool sym = d->storage == EBV_BAND_SYM || lower;
+  if (d->storage == EBV_DENSE_SYM) {  // the band panels on the lower triangle of a dense array
+    if (prec == EBV_FP64)
+      return band_factor_t<double>(dense_symlo_view((double *)a, d->ld), d->n, info, (double *)inv, env, true,
+                                   (double *)bcast, s);
+    if (prec == EBV_FP32)
+      return band_factor_t<float>(dense_symlo_view((float *)a, d->ld), d->n, info, (float *)inv, env, true,
+                                  (float *)bcast, s);
+    return EBV_ERR_UNSUPPORTED;
+  }
   if (d->storage == EBV_PROFILE) {
     if (prec == EBV_FP64)
       return band_factor_t<double>(profile_view<double>(a, d->n, d->kl, d->ku), d->n, info, (double *)inv, env,
@@ -497,11 +516,13 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
                                   (float *)bcast, s);
     return EBV_ERR_UNSUPPORTED;
   }
-  auto view = [&](auto *p) { return lower ? symlo_view(p, d->ld, d->kl) : band_view(p, d->ld, d->kl, d->ku); };
-  if (prec == EBV_FP64)
-    return band_factor_t<double>(view((double *)a), d->n, info, (double *)inv, env, sym, (double *)bcast, s);
-  if (prec == EBV_FP32)
-    return band_factor_t<float>(view((float *)a), d->n, info, (float *)inv, env, sym, (float *)bcast, s);
+  // the factorisation in the view of the stored half or the whole band
+  auto run = [&](auto *p, auto *iv, auto *bc) {
+    return lower ? band_factor_t(symlo_view(p, d->ld, d->kl), d->n, info, iv, env, sym, bc, s)
+                 : band_factor_t(band_view(p, d->ld, d->kl, d->ku), d->n, info, iv, env, sym, bc, s);
+  };
+  if (prec == EBV_FP64) return run((double *)a, (double *)inv, (double *)bcast);
+  if (prec == EBV_FP32) return run((float *)a, (float *)inv, (float *)bcast);
   if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) {
     // FP32 factors of the FP64 band in lowp (same layout); a stays untouched
     // for the refinement's residual.  The band's updates run in FP32 SIMT.
@@ -509,7 +530,7 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
     k_band_narrow<<<(unsigned)std::min<int64_t>(4096, (count + 255) / 256), 256, 0, s>>>((const double *)a,
                                                                                          (float *)lowp, count);
     EBV_TRY(launch_ok());
-    return band_factor_t<float>(view((float *)lowp), d->n, info, (float *)inv, env, sym, (float *)bcast, s);
+    return run((float *)lowp, (float *)inv, (float *)bcast);
   }
   return EBV_ERR_UNSUPPORTED;
 }
@@ -533,31 +554,40 @@ ebv_status_t band_solve(const ebv_desc_t *d, ebv_prec_t prec, const void *lu, co
                                                        bs, nrhs, r, nrhs, rmax, st);
     return launch_ok();
   };
-  if (d->storage == EBV_PROFILE) {
+  if (d->storage == EBV_PROFILE || d->storage == EBV_DENSE_SYM) {
+    const bool dsym = d->storage == EBV_DENSE_SYM;
+    auto aview = [&](auto *p) {
+      using E = std::remove_pointer_t<decltype(p)>;
+      return dsym ? dense_symlo_view(p, d->ld) : profile_view<E>(p, n, d->kl, d->ku);
+    };
     auto presidual = [&](const double *x, int64_t ldx, float *xhi, float *xlo, const double *bs, double *r,
                          unsigned long long *rmax, DevStatus *st, bool) -> ebv_status_t {
       k_split_x<<<grid_for(n * nrhs), 256, 0, s>>>(x, ldx, n, (int)nrhs, xhi, xlo, st);
       EBV_TRY(launch_ok());
-      prof::Scope ps(s, prof::kResidual, 2.0 * n * (d->kl + d->ku + 1) * nrhs);
-      k_view_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(profile_view<double>((void *)a_orig, n, d->kl, d->ku), n,
-                                                         xhi, xlo, (int)nrhs, bs, nrhs, r, nrhs, rmax, st);
+      prof::Scope ps(s, prof::kResidual, 2.0 * n * (dsym ? n : d->kl + d->ku + 1) * nrhs);
+      k_view_residual_df<<<ceil_div(n, 8), 256, 0, s>>>(aview(const_cast<double *>(a_orig)), n, xhi, xlo,
+                                                         (int)nrhs, bs, nrhs, r, nrhs, rmax, st);
       return launch_ok();
     };
     if (fp64)
-      return solve_refined<double>(profile_view<double>((void *)lu, n, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
-                                   (char *)ws, L, true, presidual, s);
+      return solve_refined<double>(aview((double *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, presidual,
+                                   s);
     if (prec == EBV_FP32)
-      return solve_refined<float>(profile_view<float>((void *)lu, n, d->kl, d->ku), n, b, nrhs, ldb, refine, rep,
-                                  (char *)ws, L, false, presidual, s);
+      return solve_refined<float>(aview((float *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, false, presidual,
+                                  s);
     return EBV_ERR_UNSUPPORTED;
   }
-  auto view = [&](auto *p) { return lower ? symlo_view(p, d->ld, d->kl) : band_view(p, d->ld, d->kl, d->ku); };
-  if (fp64)
-    return solve_refined<double>(view((double *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, residual, s);
-  if (prec == EBV_FP32)
-    return solve_refined<float>(view((float *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, false, residual, s);
-  if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16)  // FP32 factors, FP64 right-hand sides and solution
-    return solve_refined<float>(view((float *)lu), n, b, nrhs, ldb, refine, rep, (char *)ws, L, true, residual, s);
+  // b_double: FP64 right-hand sides and solution (FP64 factors, or the
+  // mixed precisions' FP32 factors); FP32 ones for EBV_FP32
+  auto run = [&](auto *p, bool b_double) {
+    return lower ? solve_refined(symlo_view(p, d->ld, d->kl), n, b, nrhs, ldb, refine, rep, (char *)ws, L, b_double,
+                                 residual, s)
+                 : solve_refined(band_view(p, d->ld, d->kl, d->ku), n, b, nrhs, ldb, refine, rep, (char *)ws, L,
+                                 b_double, residual, s);
+  };
+  if (fp64) return run((double *)lu, true);
+  if (prec == EBV_FP32) return run((float *)lu, false);
+  if (prec == EBV_MIXED_BF16 || prec == EBV_MIXED_FP16) return run((float *)lu, true);
   return EBV_ERR_UNSUPPORTED;
 }
 

@@ -264,50 +264,71 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
   }
   if (threadIdx.x == 0) *info = sm.bad == INT32_MAX ? 0 : sm.bad + 1;
   if (nrhs <= 0) return;
-  // Forward substitution LY = B (unit lower), block by block.
+  // Forward substitution LY = B (unit lower), block by block (Eq. 1): the
+  // diagonal block of L and the block's right-hand-side rows in shared
+  // memory (the factorisation is done with D and As), warp 0 solving the
+  // block there; then every later row takes the block's contribution,
+  // accumulated from zero and subtracted once.
+  T(*Ts)[NB + 1] = sm.D;
+  T(*Bs)[64 + 1] = sm.As;  // NB x nrhs (nrhs <= 64)
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int w = min(NB, n - k0);
+    for (int e = threadIdx.x; e < w * w; e += BT) {
+      const int i = e / w, j = e % w;
+      Ts[i][j] = j < i ? A[(int64_t)(k0 + i) * n + k0 + j] : T(0);
+    }
+    for (int e = threadIdx.x; e < w * nrhs; e += BT) Bs[e / nrhs][e % nrhs] = B[(int64_t)k0 * nrhs + e];
+    __syncthreads();
     if (warp == 0) {
       for (int r = 0; r < w; ++r) {
         for (int e = lane; e < (w - 1 - r) * nrhs; e += 32) {
           const int i = r + 1 + e / nrhs, c = e % nrhs;
-          B[(int64_t)(k0 + i) * nrhs + c] -= A[(int64_t)(k0 + i) * n + k0 + r] * B[(int64_t)(k0 + r) * nrhs + c];
+          Bs[i][c] -= Ts[i][r] * Bs[r][c];
         }
         __syncwarp();
       }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < w * nrhs; e += BT) B[(int64_t)k0 * nrhs + e] = Bs[e / nrhs][e % nrhs];
     for (int e = threadIdx.x; e < (n - k0 - w) * nrhs; e += BT) {
       const int i = k0 + w + e / nrhs, c = e % nrhs;
-      T s = B[(int64_t)i * nrhs + c];
       const T *li = A + (int64_t)i * n + k0;
-      for (int r = 0; r < w; ++r) s -= li[r] * B[(int64_t)(k0 + r) * nrhs + c];
-      B[(int64_t)i * nrhs + c] = s;
+      T s = T(0);
+      for (int r = 0; r < w; ++r) s += li[r] * Bs[r][c];
+      B[(int64_t)i * nrhs + c] -= s;
     }
     __syncthreads();
   }
-  // Backward substitution UX = Y, diagonal through pivot reciprocals.
+  // Backward substitution UX = Y, diagonal through pivot reciprocals, the
+  // same way from the last block up.
   for (int kend = n; kend > 0; kend -= NB) {
     const int k0 = max(0, kend - NB), w = kend - k0;
+    for (int e = threadIdx.x; e < w * w; e += BT) {
+      const int i = e / w, j = e % w;
+      Ts[i][j] = j >= i ? A[(int64_t)(k0 + i) * n + k0 + j] : T(0);
+    }
+    for (int e = threadIdx.x; e < w * nrhs; e += BT) Bs[e / nrhs][e % nrhs] = B[(int64_t)k0 * nrhs + e];
+    __syncthreads();
     if (warp == 0) {
       for (int r = w - 1; r >= 0; --r) {
-        const T rc = pivot_rcp(A[(int64_t)(k0 + r) * n + k0 + r]);
-        for (int c = lane; c < nrhs; c += 32) B[(int64_t)(k0 + r) * nrhs + c] *= rc;
+        const T rc = pivot_rcp(Ts[r][r]);
+        for (int c = lane; c < nrhs; c += 32) Bs[r][c] *= rc;
         __syncwarp();
         for (int e = lane; e < r * nrhs; e += 32) {
           const int i = e / nrhs, c = e % nrhs;
-          B[(int64_t)(k0 + i) * nrhs + c] -= A[(int64_t)(k0 + i) * n + k0 + r] * B[(int64_t)(k0 + r) * nrhs + c];
+          Bs[i][c] -= Ts[i][r] * Bs[r][c];
         }
         __syncwarp();
       }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < w * nrhs; e += BT) B[(int64_t)k0 * nrhs + e] = Bs[e / nrhs][e % nrhs];
     for (int e = threadIdx.x; e < k0 * nrhs; e += BT) {
       const int i = e / nrhs, c = e % nrhs;
-      T s = B[(int64_t)i * nrhs + c];
       const T *ui = A + (int64_t)i * n + k0;
-      for (int r = 0; r < w; ++r) s -= ui[r] * B[(int64_t)(k0 + r) * nrhs + c];
-      B[(int64_t)i * nrhs + c] = s;
+      T s = T(0);
+      for (int r = 0; r < w; ++r) s += ui[r] * Bs[r][c];
+      B[(int64_t)i * nrhs + c] -= s;
     }
     __syncthreads();
   }

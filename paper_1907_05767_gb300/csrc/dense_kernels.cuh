@@ -28,11 +28,14 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // c keeps rows pup[c] .. 64c-1 (its part above the diagonal block),
 // row-major with width 64, from base + poffU[c].  Entries outside read as 0
 // and are never written; kl / ku bound the profile (the drivers' windows).
-template <typename T>
+template <typename T, bool XV = false>
 struct MatView {
   T *base;
   int64_t ld;
   int64_t kl, ku;
+  // XV (compile time): the view may be symlo / symraw or profile storage.
+  // The plain views (dense, row band) leave these fields unused, so their
+  // kernels carry none of the extra index arithmetic.
   bool symlo = false;
   bool symraw = false;
   const int32_t *plo = nullptr, *pup = nullptr;
@@ -40,35 +43,55 @@ struct MatView {
   __device__ __forceinline__ bool in(int64_t i, int64_t j) const {
     const int64_t d = j - i;
     if (d < -kl || d > ku) return false;
-    if (plo) {
-      const int64_t b = i >> 6;
-      return j < ((b + 1) << 6) ? j >= plo[b] : i >= pup[j >> 6];
+    if constexpr (XV) {
+      if (plo) {
+        const int64_t b = i >> 6;
+        return j < ((b + 1) << 6) ? j >= plo[b] : i >= pup[j >> 6];
+      }
     }
     return true;
   }
   // Address of a stored element (in(i, j) must hold).
   __device__ __forceinline__ T *at(int64_t i, int64_t j) const {
-    if (plo) {
-      const int64_t b = i >> 6;
-      if (j < ((b + 1) << 6)) {
-        const int64_t lo = plo[b];
-        return base + poffL[b] + (i - (b << 6)) * (((b + 1) << 6) - lo) + (j - lo);
+    if constexpr (XV) {
+      if (plo) {
+        const int64_t b = i >> 6;
+        if (j < ((b + 1) << 6)) {
+          const int64_t lo = plo[b];
+          return base + poffL[b] + (i - (b << 6)) * (((b + 1) << 6) - lo) + (j - lo);
+        }
+        const int64_t c = j >> 6;
+        return base + poffU[c] + (i - pup[c]) * 64 + (j - (c << 6));
       }
-      const int64_t c = j >> 6;
-      return base + poffU[c] + (i - pup[c]) * 64 + (j - (c << 6));
     }
     return base + i * ld + j;
   }
   __device__ __forceinline__ T get(int64_t i, int64_t j) const {
     if (!in(i, j)) return T(0);
-    if (symlo && j > i) return symraw ? base[j * ld + i] : base[j * ld + i] * base[i * ld + i];
+    if constexpr (XV) {
+      if (symlo && j > i) return symraw ? base[j * ld + i] : base[j * ld + i] * base[i * ld + i];
+    }
     return *at(i, j);
   }
-  __device__ __forceinline__ bool writable(int64_t i, int64_t j) const { return in(i, j) && !(symlo && j > i); }
+  // The stored entry a_ij of an unfactored matrix (in(i, j) must hold); the
+  // lower-half storages hold a_ij above the diagonal as a_ji.
+  __device__ __forceinline__ T raw(int64_t i, int64_t j) const {
+    if constexpr (XV) {
+      if (symlo && j > i) return base[j * ld + i];
+    }
+    return *at(i, j);
+  }
+  __device__ __forceinline__ bool writable(int64_t i, int64_t j) const {
+    if constexpr (XV) return in(i, j) && !(symlo && j > i);
+    return in(i, j);
+  }
   __device__ __forceinline__ void put(int64_t i, int64_t j, T v) const {
     if (writable(i, j)) *at(i, j) = v;
   }
 };
+// The views with lower-half symmetric or profile storage.
+template <typename T>
+using XView = MatView<T, true>;
 
 constexpr int64_t kDenseBand = int64_t(1) << 60;
 
@@ -95,10 +118,13 @@ template <typename T>
 inline MatView<T> band_view(T *ab, int64_t ldab, int64_t kl, int64_t ku) {
   return MatView<T>{ab + kl, ldab - 1, kl, ku};
 }
+// The lower triangle of a symmetric dense matrix (a_ij at a[i*ld + j], j <= i).
+template <typename T>
+inline XView<T> dense_symlo_view(T *a, int64_t ld) { return XView<T>{a, ld, kDenseBand, kDenseBand, true, false}; }
 // The lower half of a symmetric band (a_ij at ab[i*ldab + j-i+kl], j <= i).
 template <typename T>
-inline MatView<T> symlo_view(T *ab, int64_t ldab, int64_t kl) {
-  return MatView<T>{ab + kl, ldab - 1, kl, kl, true, false};
+inline XView<T> symlo_view(T *ab, int64_t ldab, int64_t kl) {
+  return XView<T>{ab + kl, ldab - 1, kl, kl, true, false};
 }
 
 // Stage an NB x NB tile into shared memory (row stride S) with all of the
@@ -396,8 +422,8 @@ __device__ __forceinline__ void warp_tri_inv16(const T *D, T *Z, int ld, int o, 
   }
 }
 
-template <typename T, int NB, int NT>
-__device__ __forceinline__ void diag_factor_cta(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv,
+template <typename T, int NB, int NT, bool XV>
+__device__ __forceinline__ void diag_factor_cta(MatView<T, XV> A, int64_t k0, int w, int32_t *info, T *inv,
                                                 unsigned char *dsm) {
   static_assert(NB == 64 && NT == 256, "4 x 4 sub-blocks of 16, 8 warps");
   constexpr int LD = NB + 1, NSB = NB / kSB;
@@ -487,10 +513,126 @@ __device__ __forceinline__ void diag_factor_cta(MatView<T> A, int64_t k0, int w,
 
 // One launch of the diagonal-block factorisation (dynamic shared memory:
 // diagb_smem_bytes<T, NB>()).
-template <typename T, int NB, int NT>
-__global__ void __launch_bounds__(NT) k_diag_factor(MatView<T> A, int64_t k0, int w, int32_t *info, T *inv) {
+template <typename T, int NB, int NT, bool XV = false>
+__global__ void __launch_bounds__(NT) k_diag_factor(MatView<T, XV> A, int64_t k0, int w, int32_t *info, T *inv) {
   extern __shared__ __align__(16) unsigned char dsm[];
   diag_factor_cta<T, NB, NT>(A, k0, w, info, inv, dsm);
+}
+
+// One slot row of the register-resident diagonal block's step-k update:
+// v[j] -= l u[j] for the columns tx + 16 j > k (live: some row of the warp's
+// slot is still active, warp-uniform; rok: this thread's row is).
+template <typename T>
+__device__ __forceinline__ void lu_slot_update(T (&v)[4], T l, const T (&u)[4], bool live, bool rok, int tx, int k) {
+  if (!live) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (16 * j + 15 > k && rok && tx + 16 * j > k) v[j] -= l * u[j];
+}
+
+// The diagonal block alone (no inverses), right-looking Doolittle (Eq. 6a-c)
+// on the block held in registers: element (r, c) lives in thread
+// (r % 16, c % 16), slot [r / 16][c / 16], so every thread holds rows and
+// columns from each quarter of the block and does the same share of every
+// step's update (the balance Eq. 7's long/short pairing gives).  A warp owns
+// eight whole rows (threads 16 ty .. 16 ty + 15 share a row); row k's entries
+// of column k are shuffled inside the owning warp, the pivot row goes through
+// shared memory.  Step k: l_rk = a_rk / u_kk (FP64 reciprocal), then
+// a_rc -= l_rk u_kc for r, c > k.  Look-ahead: the warp owning row k+1
+// updates that row first and publishes it with its reciprocal (buffer
+// (k+1) & 1) before the rest of its update, so the next step's pivot chain
+// runs under the other warps' updates; one barrier per step.  Rows and
+// columns past w hold the identity.  A zero or non-finite pivot k reports
+// info = k0 + k + 1 (the first one), and the elimination goes on.
+template <typename T, bool XV = false>
+__global__ void __launch_bounds__(256) k_diag_lu(MatView<T, XV> A, int64_t k0, int w, int32_t *info) {
+  constexpr int NB = 64;
+  __shared__ T urow[2][NB];
+  __shared__ T rcps[2];
+  __shared__ int bad;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int lane = threadIdx.x & 31;
+  T v[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      v[i][j] = (r < w && c < w) ? A.get(k0 + r, k0 + c) : (r == c ? T(1) : T(0));
+    }
+  if (threadIdx.x == 0) bad = NB;
+  if (ty == 0) {  // row 0 and its reciprocal
+#pragma unroll
+    for (int j = 0; j < 4; ++j) urow[0][tx + 16 * j] = v[0][j];
+    if (tx == 0) {
+      const T p = v[0][0];
+      rcps[0] = pivot_rcp(p);
+      if (pivot_bad(p) && w > 0) bad = 0;
+    }
+  }
+  __syncthreads();
+  const int wrow = ty & ~1;  // this warp's rows: wrow, wrow + 1 (+ 16 i)
+  for (int k = 0; k + 1 < w; ++k) {
+    const int kt = k & 15, kb = k >> 4, buf = k & 1;
+    const T rk = rcps[buf];
+    // l_rk for this thread's rows (the lane of column k in its row shares it)
+    T l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T a = v[i][0];
+#pragma unroll
+      for (int j = 1; j < 4; ++j)
+        if (kb == j) a = v[i][j];
+      a = __shfl_sync(0xffffffffu, a, (lane & 16) | kt);
+      l[i] = (16 * i + wrow + 1 > k) ? a * rk : T(0);  // warp-uniform skip of finished slots
+    }
+    T u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = urow[buf][tx + 16 * j];
+    // column k becomes L
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j == kb && tx == kt && ty + 16 * i > k) v[i][j] = l[i];
+    const int n1 = k + 1, i1 = n1 >> 4;
+    const bool owner = (n1 & 15) >> 1 == (ty >> 1);
+    if (owner) {  // row k+1 first, then publish it and its reciprocal
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i == i1) lu_slot_update(v[i], l[i], u, 16 * i + wrow + 1 > k, ty + 16 * i > k, tx, k);
+      if (ty == (n1 & 15)) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i == i1) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) urow[buf ^ 1][tx + 16 * j] = v[i][j];
+          }
+        if (tx == (n1 & 15)) {
+          T p = v[0][0];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (i == i1 && j == i1) p = v[i][j];
+          rcps[buf ^ 1] = pivot_rcp(p);
+          if (pivot_bad(p)) atomicMin(&bad, n1);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (!owner || i != i1) lu_slot_update(v[i], l[i], u, 16 * i + wrow + 1 > k, ty + 16 * i > k, tx, k);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad < w && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < w && c < w) A.put(k0 + r, k0 + c, v[i][j]);
+    }
 }
 
 // L21 = A21 U11^{-1} and U12 = L11^{-1} A12 are 64 x 64 x 64 tile products
@@ -582,8 +724,8 @@ __device__ __forceinline__ void tile_product(const T *P, T *Q) {
 // back coalesced (plus the scaled low-precision shadow of L).
 // Dynamic shared memory: pair_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
-template <typename T, typename SH, int NB>
-__global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w, int64_t r_begin, int64_t r_end,
+template <typename T, typename SH, int NB, bool XV = false>
+__global__ void __launch_bounds__(256) k_trsm_ru(MatView<T, XV> A, int64_t k0, int w, int64_t r_begin, int64_t r_end,
                                                  const T *inv, Shadow<SH> sh, Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
@@ -614,8 +756,8 @@ __global__ void __launch_bounds__(256) k_trsm_ru(MatView<T> A, int64_t k0, int w
 // product per CTA slow.  Computed transposed, (L21)^T = (U11^{-1})^T A21^T,
 // so the strip is the tile product's column strip.
 // Dynamic shared memory: pair_smem_bytes<T, NB>().
-template <typename T, typename SH, int NB, int RW>
-__global__ void __launch_bounds__(256) k_trsm_ru_strip(MatView<T> A, int64_t k0, int w, int64_t r_begin,
+template <typename T, typename SH, int NB, int RW, bool XV = false>
+__global__ void __launch_bounds__(256) k_trsm_ru_strip(MatView<T, XV> A, int64_t k0, int w, int64_t r_begin,
                                                        int64_t r_end, const T *inv, Shadow<SH> sh,
                                                        Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
@@ -651,8 +793,8 @@ __global__ void __launch_bounds__(256) k_trsm_ru_strip(MatView<T> A, int64_t k0,
 // from L11^{-1}.  Also writes the scaled low-precision shadow of U^T.
 // Dynamic shared memory: pair_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
-template <typename T, typename SH, int NB>
-__global__ void __launch_bounds__(256) k_trsm_ll(MatView<T> A, int64_t r0, int h, int64_t c_begin, int64_t c_end,
+template <typename T, typename SH, int NB, bool XV = false>
+__global__ void __launch_bounds__(256) k_trsm_ll(MatView<T, XV> A, int64_t r0, int h, int64_t c_begin, int64_t c_end,
                                                  const T *inv, Shadow<SH> sh, Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
   constexpr int TS = diag_tstride<T, NB>();
@@ -1064,8 +1206,8 @@ __global__ void __launch_bounds__(256) k_diag_l21_update(MatView<T> A, int64_t c
 template <typename T, int NB, int MAXB>
 constexpr size_t trsm_multi_smem_bytes() { return sizeof(T) * (MAXB + 2) * (size_t)NB * diag_tstride<T, NB>(); }
 
-template <typename T, typename SH, int NB, int MAXB, int CW>
-__global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T> A, int64_t r0, int h, int64_t c_begin,
+template <typename T, typename SH, int NB, int MAXB, int CW, bool XV = false>
+__global__ void __launch_bounds__(256) k_trsm_ll_multi(MatView<T, XV> A, int64_t r0, int h, int64_t c_begin,
                                                        int64_t c_end, const T *inv, Shadow<SH> sh,
                                                        Envelope env = {}) {
   static_assert(NB == 64, "tile mapping assumes 64");
@@ -1331,14 +1473,32 @@ ebv_status_t prepare_leaf_kernels() {
   return err == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
 }
 
+// The same opt-in for the kernels the banded factorisation runs through the
+// lower-half symmetric and profile views (their own instantiations).
+template <typename T>
+ebv_status_t prepare_xview_kernels() {
+  static const cudaError_t err = [] {
+    const int bytes = (int)pair_smem_bytes<T, kNB>();
+    cudaError_t e = set_smem(k_diag_factor<T, kNB, 4 * kNB, true>, (int)diagb_smem_bytes<T, kNB>());
+    if (e == cudaSuccess) e = set_smem(k_trsm_ru<T, float, kNB, true>, bytes);
+    if (e == cudaSuccess) e = set_smem(k_trsm_ll<T, float, kNB, true>, bytes);
+    if (e == cudaSuccess) e = set_smem(k_trsm_ru_strip<T, float, kNB, 16, true>, bytes);
+    if (e == cudaSuccess)
+      e = set_smem(k_trsm_ll_multi<T, float, kNB, kTrsmMaxBlocks, 16, true>,
+                   (int)trsm_multi_smem_bytes<T, kNB, kTrsmMaxBlocks>());
+    return e;
+  }();
+  return err == cudaSuccess ? EBV_OK : EBV_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // Symmetric band: U12 = D11 L21^T for the block row of the leaf at c0 (w
 // columns): u(c0+k, cb+j) = u_kk * l(cb+j, c0+k).  One CTA per 64 columns of
 // U12; the L21 block is read by rows and written transposed through shared
 // memory, so both sides are coalesced.
 // ---------------------------------------------------------------------------
-template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_sym_u12(MatView<T> A, int64_t c0, int w, int64_t cb, int64_t ce) {
+template <typename T, int NB, bool XV = false>
+__global__ void __launch_bounds__(256) k_sym_u12(MatView<T, XV> A, int64_t c0, int w, int64_t cb, int64_t ce) {
   __shared__ T t[NB][NB + 1];
   __shared__ T d[NB];
   const int64_t j0 = cb + (int64_t)blockIdx.x * NB;
@@ -1360,9 +1520,9 @@ __global__ void __launch_bounds__(256) k_sym_u12(MatView<T> A, int64_t c0, int w
 // steps):  A(m0+i, n0+j) -= sum_k A(m0+i, k0+k) * A(k0+k, n0+j).
 // Register-tiled: each thread owns a TM x TN block of C.
 // ---------------------------------------------------------------------------
-template <typename T, int BM, int BN, int BK, int TM, int TN>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool XV = false>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    k_gemm_nn(MatView<T> A, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, int lower64 = 0,
+    k_gemm_nn(MatView<T, XV> A, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, int lower64 = 0,
               Envelope env = {}) {
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
   __shared__ T As[BK][BM + 1];

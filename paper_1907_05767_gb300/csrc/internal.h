@@ -14,6 +14,9 @@ namespace ebv {
 size_t dense_factor_ws(int64_t n, ebv_prec_t prec);
 size_t dense_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec);
 size_t band_factor_ws(int64_t n, int64_t kl, int64_t ku, ebv_prec_t prec);
+// The lower band width that sizes the band paths' workspace (the dense
+// symmetric storage ignores desc->kl and never runs the cluster panels).
+inline int64_t ws_kl(const ebv_desc_t *d) { return d->storage == EBV_DENSE_SYM ? 0 : d->kl; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec);
 
 ebv_status_t dense_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lowp, int32_t *info, void *ws,
@@ -34,6 +37,7 @@ void set_band_envelope(bool on);
 void set_band_cluster(bool on);
 // Testing hook: false = FP64 band panels without look-ahead (default true).
 void set_band_lookahead(bool on);
+void set_diag_lu(bool on);
 // Dense FP64 factorisation of a small system as right-looking 64-column
 // panels (band.cu); orders up to kSmallDenseMaxN use it.
 ebv_status_t dense_small_factor(double *a, int64_t ld, int64_t n, int32_t *info, void *ws, cudaStream_t s);

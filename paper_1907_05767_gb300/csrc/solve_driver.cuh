@@ -55,9 +55,9 @@ DenseSolveLayout solve_layout(int64_t n, int64_t nrhs, size_t tsize, bool tc_res
 inline int grid_for(int64_t elems) { return (int)std::min<int64_t>(4096, std::max<int64_t>(1, (elems + 255) / 256)); }
 
 // Inverses of the diagonal blocks of the factors (once per solve call).
-template <typename T>
-ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
-  static const cudaError_t attr = set_smem(k_diag_inverses<T, kNB>, (int)diag_smem_bytes<T, kNB>());
+template <typename T, bool XV>
+ebv_status_t diag_inverses(MatView<T, XV> F, int64_t n, T *dinv, cudaStream_t s) {
+  static const cudaError_t attr = set_smem(k_diag_inverses<T, kNB, XV>, (int)diag_smem_bytes<T, kNB>());
   if (attr != cudaSuccess) return EBV_ERR_CUDA;
   prof::Scope ps(s, prof::kTrsv, 2.0 * ceil_div(n, kNB) * kNB * kNB * kNB * (2.0 / 3.0 + 4.0));
   k_diag_inverses<T, kNB><<<ceil_div(n, kNB), 4 * kNB, diag_smem_bytes<T, kNB>(), s>>>(F, n, dinv);
@@ -67,13 +67,13 @@ ebv_status_t diag_inverses(MatView<T> F, int64_t n, T *dinv, cudaStream_t s) {
 // One triangle of the substitution as a cooperative persistent launch: at
 // most as many CTAs per right-hand-side chunk as can be resident at once
 // (the CTAs wait on one another's published blocks).
-template <typename T, bool UPPER, int RCW>
-ebv_status_t trsv_launch(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+template <typename T, bool UPPER, int RCW, bool XV>
+ebv_status_t trsv_launch(MatView<T, XV> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
                          unsigned long long *xw, DevStatus *st, cudaStream_t s) {
   using C = TrsvCfg<T, RCW>;
   constexpr int RC = C::RC;
   constexpr size_t smem = trsvl_smem_bytes<T, kNB, RC, C::NS>();
-  auto kern = k_trsv_left<T, kNB, RC, UPPER, C::NS, C::MINB>;
+  auto kern = k_trsv_left<T, kNB, RC, UPPER, C::NS, C::MINB, XV>;
   static int resident = [&] {
     int dev = 0, sms = 0, per_sm = 0;
     if (set_smem(kern, (int)smem) != cudaSuccess) return 0;
@@ -101,27 +101,27 @@ ebv_status_t trsv_launch(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, c
   return launch_ok();
 }
 
-template <typename T, bool UPPER>
-ebv_status_t trsv_one(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+template <typename T, bool UPPER, bool XV>
+ebv_status_t trsv_one(MatView<T, XV> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
                       unsigned long long *xw, DevStatus *st, cudaStream_t s) {
-  if (nrhs <= 8) return trsv_launch<T, UPPER, 8>(F, n, B, ldb, nrhs, dinv, xw, st, s);
-  return trsv_launch<T, UPPER, 32>(F, n, B, ldb, nrhs, dinv, xw, st, s);
+  if (nrhs <= 8) return trsv_launch<T, UPPER, 8, XV>(F, n, B, ldb, nrhs, dinv, xw, st, s);
+  return trsv_launch<T, UPPER, 32, XV>(F, n, B, ldb, nrhs, dinv, xw, st, s);
 }
 
 // Forward then backward block substitution of B (n x nrhs, T) in place.
-template <typename T>
-ebv_status_t trsv_pair(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
+template <typename T, bool XV>
+ebv_status_t trsv_pair(MatView<T, XV> F, int64_t n, T *B, int64_t ldb, int nrhs, const T *dinv,
                        unsigned long long *xw, DevStatus *st, cudaStream_t s) {
-  EBV_TRY((trsv_one<T, false>(F, n, B, ldb, nrhs, dinv, xw, st, s)));
-  return trsv_one<T, true>(F, n, B, ldb, nrhs, dinv, xw, st, s);
+  EBV_TRY((trsv_one<T, false, XV>(F, n, B, ldb, nrhs, dinv, xw, st, s)));
+  return trsv_one<T, true, XV>(F, n, B, ldb, nrhs, dinv, xw, st, s);
 }
 
 // ---------------------------------------------------------------------------
 // Solve with optional refinement.  Shared by the dense and banded paths
 // through the factor view F and the residual callback.
 // ---------------------------------------------------------------------------
-template <typename T, typename ResidualFn>
-ebv_status_t solve_refined(MatView<T> F, int64_t n, void *b, int64_t nrhs, int64_t ldb, const ebv_refine_t *refine,
+template <typename T, bool XV, typename ResidualFn>
+ebv_status_t solve_refined(MatView<T, XV> F, int64_t n, void *b, int64_t nrhs, int64_t ldb, const ebv_refine_t *refine,
                            ebv_refine_report_t *rep, char *w, const DenseSolveLayout &L, bool b_is_double,
                            ResidualFn residual, cudaStream_t s) {
   DevStatus *st = (DevStatus *)w;

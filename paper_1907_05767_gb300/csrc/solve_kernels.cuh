@@ -17,8 +17,8 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // product: x_b = L_bb^{-1} acc - (L_bb^{-1} L_b,b-1) x_{b-1}.
 // Dynamic shared memory: diag_smem_bytes<T, NB>().
 // ---------------------------------------------------------------------------
-template <typename T, int NB>
-__global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T> F, int64_t n, T *dinv) {
+template <typename T, int NB, bool XV = false>
+__global__ void __launch_bounds__(4 * NB) k_diag_inverses(MatView<T, XV> F, int64_t n, T *dinv) {
   extern __shared__ __align__(16) unsigned char dsm[];
   T(*D)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(dsm);
   T *LT = reinterpret_cast<T *>(dsm + sizeof(T) * NB * (NB + 1));
@@ -206,8 +206,8 @@ __device__ __forceinline__ void ring_fold(const T *P, const T (*xs)[RC + 1], int
   }
 }
 
-template <typename T, int NB, int RC, bool UPPER, int NS, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n, T *B, int64_t ldb, int nrhs,
+template <typename T, int NB, int RC, bool UPPER, int NS, int MINB, bool XV = false>
+__global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T, XV> F, int64_t n, T *B, int64_t ldb, int nrhs,
                                                          const T *dinv, unsigned long long *xw, DevStatus *st) {
   constexpr int NT = 256, DS = trsvl_stride<T, NB>(), E = 16 / (int)sizeof(T), CPR = NB / E;
   constexpr int PASS = NT / RC, OPT = NB / PASS;
@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T> F, int64_t n
   // Blocks s >= t - reach couple into block t (a band limits reach).
   const int reach = (int)max64(1, min64((UPPER ? F.ku + NB - 1 : F.kl + NB - 1) / NB, (int64_t)nblk));
   const int tc = threadIdx.x % RC, tr = threadIdx.x / RC;
-  const bool direct = F.kl >= kDenseBand && F.ku >= kDenseBand && F.ld % E == 0 &&
+  // plain dense storage: tiles copied as they are (a lower-triangle view reads U through get())
+  const bool direct = !XV && F.kl >= kDenseBand && F.ku >= kDenseBand && F.ld % E == 0 &&
                       ((uintptr_t)F.base % 16) == 0;
 
   // Ring tile j of block t: F(t, sb + j) for j < m, then the coupling tile.

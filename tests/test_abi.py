@@ -118,7 +118,19 @@ def test_band_storage_descriptors(lib):
     assert ok(100, 5, 4, 4, ebv.BAND_SYM_LOWER) and not ok(100, 4, 4, 4, ebv.BAND_SYM_LOWER)
     assert not ok(100, 9, 3, 5, ebv.BAND_SYM_LOWER)
     assert not ok(100, 9, 100, 100, ebv.BAND_SYM_LOWER)  # kl < n
-    assert not ok(100, 100, 0, 0, 5)  # no such storage
+    assert not ok(100, 100, 0, 0, 6)  # no such storage
+    # dense symmetric (lower triangle): ld >= n, kl / ku ignored
+    assert ok(100, 100, 0, 0, ebv.DENSE_SYM) and ok(100, 128, 7, 3, ebv.DENSE_SYM)
+    assert not ok(100, 99, 0, 0, ebv.DENSE_SYM)
+
+
+def test_dense_sym_rejects_mixed_and_inverse(lib):
+    d = ebv._desc(64, 64, 0, 0, ebv.DENSE_SYM)
+    info = ctypes.c_void_p(0x100000)
+    a = ctypes.c_void_p(0x200000)
+    ws = ctypes.c_void_p(0x300000)
+    assert lib.ebv_factor(ctypes.byref(d), ebv.MIXED_BF16, a, a, info, ws, 1 << 20, None) == ebv.ERR_UNSUPPORTED
+    assert lib.ebv_inverse(ctypes.byref(d), ebv.FP64, a, ws, 64, ws, 1 << 20, None) == ebv.ERR_UNSUPPORTED
 
 
 def test_inverse_argument_errors(lib):
