@@ -303,7 +303,8 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
           if (g_diag_lu)
             k_diag_lu<T><<<1, 256, 0, s>>>(Araw, c0, w, info);
           else
-            k_diag_factor<T, kNB, 4 * kNB><<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, nullptr);
+            k_diag_factor<T, kNB, 4 * kNB, XV, false>
+                <<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, nullptr);
           EBV_TRY(launch_ok());
         }
         if (re > rb) {

@@ -422,7 +422,144 @@ __device__ __forceinline__ void warp_tri_inv16(const T *D, T *Z, int ld, int o, 
   }
 }
 
-template <typename T, int NB, int NT, bool XV>
+// One slot row of the register-resident diagonal block's step-k update:
+// v[j] -= a w[j] for the columns tx + 16 j > k (live: some row of the warp's
+// slot is still active, warp-uniform; rok: this thread's row is).
+template <typename T>
+__device__ __forceinline__ void lu_slot_update(T (&v)[4], T a, const T (&w)[4], bool live, bool rok, int tx, int k) {
+  if (!live) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (16 * j + 15 > k && rok && tx + 16 * j > k) v[j] -= a * w[j];
+}
+
+// Publish pivot row n of the register-resident diagonal block from the warp
+// owning it (x: this lane's slot row holding row n or its partner row): the
+// FP64 reciprocal of u_nn to rcp[n], the row scaled by it to ws.  The
+// half-warp holding row n scales columns tx + 16 j for j < 2, the other half
+// (same tx) those for j >= 2, taken by shuffle: two DMUL per lane.
+template <typename T>
+__device__ __forceinline__ void lu_publish(int n, const T (&x)[4], T *ws, T *rcp, int *bad, int w) {
+  const int lane = threadIdx.x & 31, ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int nt = n & 15;
+  const int src = ((nt & 1) << 4) | nt;  // lane of (n, n)
+  T p = x[0];
+#pragma unroll
+  for (int j = 1; j < 4; ++j)
+    if ((n >> 4) == j) p = x[j];
+  p = __shfl_sync(0xffffffffu, p, src);
+  const T r = pivot_rcp(p);
+  const bool mine = ty == nt;  // this half-warp holds row n
+  const T y2 = __shfl_xor_sync(0xffffffffu, x[2], 16);
+  const T y3 = __shfl_xor_sync(0xffffffffu, x[3], 16);
+  const T d0 = (mine ? x[0] : y2) * r;
+  const T d1 = (mine ? x[1] : y3) * r;
+  ws[tx + (mine ? 0 : 32)] = d0;
+  ws[tx + (mine ? 16 : 48)] = d1;
+  if (lane == src) {
+    rcp[n] = r;
+    if (pivot_bad(p) && n < w) atomicMin(bad, n);
+  }
+}
+
+// The 64 x 64 diagonal block in registers, right-looking Doolittle (Eq.
+// 6a-c), one CTA of 256 threads: element (r, c) lives in thread
+// (r % 16, c % 16), slot [r / 16][c / 16], so every thread holds rows and
+// columns from each quarter of the block and does the same share of every
+// step's update (the balance Eq. 7's long/short pairing gives).  A warp owns
+// eight whole rows (threads 16 ty .. 16 ty + 15 share a row).
+// Step k: a_rc -= a_rk w_kc for r, c > k, with w_kc = u_kc / u_kk the pivot
+// row scaled once by its reciprocal (published in shared memory, buffer
+// k & 1) and a_rk shuffled inside the owning warp; l_rk = a_rk / u_kk is
+// formed for every column at the end.  (An FP64 instruction costs a warp
+// slot of the SM's FP64 pipe whatever its active lanes, so the scaling is two
+// instructions of one warp per step instead of one per row in every warp.)
+// Look-ahead: the warp owning row k+1 updates that row first and publishes
+// it before the rest of its update, so the next pivot's chain runs under the
+// other warps' updates; one barrier per step.  Rows and columns past w hold
+// the identity (and rcp 1).  A zero or non-finite pivot k lowers *bad to k;
+// the elimination goes on.  Result: the packed factors to D (shared memory,
+// row stride ld, all 64 x 64) when D is set, else to A (the w x w block);
+// rcp[k] = 1 / u_kk.  Shared: ws[2][64], rcp[64], *bad (set to 64 here).
+template <typename T, bool XV>
+__device__ __forceinline__ void diag_lu_regs(MatView<T, XV> A, int64_t k0, int w, T (*ws)[64], T *rcp, int *bad,
+                                             T *D, int ld) {
+  constexpr int NB = 64;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int lane = threadIdx.x & 31;
+  T v[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      v[i][j] = (r < w && c < w) ? A.get(k0 + r, k0 + c) : (r == c ? T(1) : T(0));
+    }
+  if (threadIdx.x == 0) *bad = NB;
+  if (threadIdx.x >= w && threadIdx.x < NB) rcp[threadIdx.x] = T(1);
+  __syncthreads();
+  const int wrow = ty & ~1;  // this warp's rows: wrow, wrow + 1 (+ 16 i)
+  auto slot_row = [&](int i1, T (&x)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = v[0][j];
+#pragma unroll
+      for (int i = 1; i < 4; ++i)
+        if (i == i1) x[j] = v[i][j];
+    }
+  };
+  if (wrow == 0) {  // warp 0: row 0
+    T x[4];
+    slot_row(0, x);
+    lu_publish(0, x, ws[0], rcp, bad, w);
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < w; ++k) {
+    const int kt = k & 15, kb = k >> 4, buf = k & 1;
+    // a_rk for this thread's rows (the lane of column k in its row shares it)
+    T a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T s = v[i][0];
+#pragma unroll
+      for (int j = 1; j < 4; ++j)
+        if (kb == j) s = v[i][j];
+      a[i] = __shfl_sync(0xffffffffu, s, (lane & 16) | kt);
+    }
+    T u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = ws[buf][tx + 16 * j];
+    const int n1 = k + 1, i1 = n1 >> 4;
+    const bool owner = (n1 & 15) >> 1 == (ty >> 1);
+    if (owner) {  // row k+1 first, then publish it
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i == i1) lu_slot_update(v[i], a[i], u, 16 * i + wrow + 1 > k, ty + 16 * i > k, tx, k);
+      T x[4];
+      slot_row(i1, x);
+      lu_publish(n1, x, ws[buf ^ 1], rcp, bad, w);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (!owner || i != i1) lu_slot_update(v[i], a[i], u, 16 * i + wrow + 1 > k, ty + 16 * i > k, tx, k);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      const T f = c < r ? v[i][j] * rcp[c] : v[i][j];  // l_rc = a_rc / u_cc
+      if (D) D[r * ld + c] = f;
+      else if (r < w && c < w) A.put(k0 + r, k0 + c, f);
+    }
+}
+
+// REGS: the elimination by diag_lu_regs (the FP64 default); else the
+// blocked one of 16 x 16 sub-blocks below (the binary32 default: measured on
+// one 64 x 64 block, FP64 86 us in registers against 119 us blocked, binary32
+// 36 us against 18 us).
+template <typename T, int NB, int NT, bool XV, bool REGS = (sizeof(T) == 8)>
 __device__ __forceinline__ void diag_factor_cta(MatView<T, XV> A, int64_t k0, int w, int32_t *info, T *inv,
                                                 unsigned char *dsm) {
   static_assert(NB == 64 && NT == 256, "4 x 4 sub-blocks of 16, 8 warps");
@@ -436,6 +573,18 @@ __device__ __forceinline__ void diag_factor_cta(MatView<T, XV> A, int64_t k0, in
   const int warp = threadIdx.x >> 5;
   T *S = scratch + warp * kSB * (kSB + 1);
   auto blk = [&](T *M, int bi, int bj) { return M + (bi * kSB) * LD + bj * kSB; };
+  if constexpr (REGS) {
+    // X holds the pivot-row buffers during the elimination
+    diag_lu_regs<T, XV>(A, k0, w, reinterpret_cast<T (*)[64]>(X), rcp, &bad, D, LD);
+    __syncthreads();
+    if (inv) {  // the 16 x 16 diagonal sub-blocks of L11^{-1} (warps 0-3) and U11^{-1} (4-7)
+      for (int e = threadIdx.x; e < NB * LD; e += NT) X[e] = Y[e] = T(0);
+      __syncthreads();
+      if (warp < NSB) warp_tri_inv16<T, true>(D, X, LD, warp * kSB, rcp);
+      else warp_tri_inv16<T, false>(D, Y, LD, (warp - NSB) * kSB, rcp);
+      __syncthreads();
+    }
+  } else {
   stage_tile<NB, NT, LD>(D, [&](int i, int j) {
     return (i < w && j < w) ? A.get(k0 + i, k0 + j) : (i == j ? T(1) : T(0));
   });
@@ -473,6 +622,7 @@ __device__ __forceinline__ void diag_factor_cta(MatView<T, XV> A, int64_t k0, in
       wtile_put(blk(D, bi, bj), LD, c);
     }
     __syncthreads();
+  }
   }
   if (threadIdx.x == 0 && bad < NB && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
   for (int e = threadIdx.x; e < NB * NB; e += NT) {
@@ -513,127 +663,24 @@ __device__ __forceinline__ void diag_factor_cta(MatView<T, XV> A, int64_t k0, in
 
 // One launch of the diagonal-block factorisation (dynamic shared memory:
 // diagb_smem_bytes<T, NB>()).
-template <typename T, int NB, int NT, bool XV = false>
+template <typename T, int NB, int NT, bool XV = false, bool REGS = (sizeof(T) == 8)>
 __global__ void __launch_bounds__(NT) k_diag_factor(MatView<T, XV> A, int64_t k0, int w, int32_t *info, T *inv) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  diag_factor_cta<T, NB, NT>(A, k0, w, info, inv, dsm);
+  diag_factor_cta<T, NB, NT, XV, REGS>(A, k0, w, info, inv, dsm);
 }
 
-// One slot row of the register-resident diagonal block's step-k update:
-// v[j] -= l u[j] for the columns tx + 16 j > k (live: some row of the warp's
-// slot is still active, warp-uniform; rok: this thread's row is).
-template <typename T>
-__device__ __forceinline__ void lu_slot_update(T (&v)[4], T l, const T (&u)[4], bool live, bool rok, int tx, int k) {
-  if (!live) return;
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (16 * j + 15 > k && rok && tx + 16 * j > k) v[j] -= l * u[j];
-}
-
-// The diagonal block alone (no inverses), right-looking Doolittle (Eq. 6a-c)
-// on the block held in registers: element (r, c) lives in thread
-// (r % 16, c % 16), slot [r / 16][c / 16], so every thread holds rows and
-// columns from each quarter of the block and does the same share of every
-// step's update (the balance Eq. 7's long/short pairing gives).  A warp owns
-// eight whole rows (threads 16 ty .. 16 ty + 15 share a row); row k's entries
-// of column k are shuffled inside the owning warp, the pivot row goes through
-// shared memory.  Step k: l_rk = a_rk / u_kk (FP64 reciprocal), then
-// a_rc -= l_rk u_kc for r, c > k.  Look-ahead: the warp owning row k+1
-// updates that row first and publishes it with its reciprocal (buffer
-// (k+1) & 1) before the rest of its update, so the next step's pivot chain
-// runs under the other warps' updates; one barrier per step.  Rows and
-// columns past w hold the identity.  A zero or non-finite pivot k reports
-// info = k0 + k + 1 (the first one), and the elimination goes on.
+// The diagonal block alone (no inverses) as its own launch: the FP64 panels
+// of the band storages and of small dense systems.  info = k0 + k + 1 for the
+// first zero or non-finite pivot k.
 template <typename T, bool XV = false>
 __global__ void __launch_bounds__(256) k_diag_lu(MatView<T, XV> A, int64_t k0, int w, int32_t *info) {
-  constexpr int NB = 64;
-  __shared__ T urow[2][NB];
-  __shared__ T rcps[2];
+  __shared__ T ws[2][64];
+  __shared__ T rcp[64];
   __shared__ int bad;
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  const int lane = threadIdx.x & 31;
-  T v[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = ty + 16 * i, c = tx + 16 * j;
-      v[i][j] = (r < w && c < w) ? A.get(k0 + r, k0 + c) : (r == c ? T(1) : T(0));
-    }
-  if (threadIdx.x == 0) bad = NB;
-  if (ty == 0) {  // row 0 and its reciprocal
-#pragma unroll
-    for (int j = 0; j < 4; ++j) urow[0][tx + 16 * j] = v[0][j];
-    if (tx == 0) {
-      const T p = v[0][0];
-      rcps[0] = pivot_rcp(p);
-      if (pivot_bad(p) && w > 0) bad = 0;
-    }
-  }
-  __syncthreads();
-  const int wrow = ty & ~1;  // this warp's rows: wrow, wrow + 1 (+ 16 i)
-  for (int k = 0; k + 1 < w; ++k) {
-    const int kt = k & 15, kb = k >> 4, buf = k & 1;
-    const T rk = rcps[buf];
-    // l_rk for this thread's rows (the lane of column k in its row shares it)
-    T l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      T a = v[i][0];
-#pragma unroll
-      for (int j = 1; j < 4; ++j)
-        if (kb == j) a = v[i][j];
-      a = __shfl_sync(0xffffffffu, a, (lane & 16) | kt);
-      l[i] = (16 * i + wrow + 1 > k) ? a * rk : T(0);  // warp-uniform skip of finished slots
-    }
-    T u[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) u[j] = urow[buf][tx + 16 * j];
-    // column k becomes L
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j == kb && tx == kt && ty + 16 * i > k) v[i][j] = l[i];
-    const int n1 = k + 1, i1 = n1 >> 4;
-    const bool owner = (n1 & 15) >> 1 == (ty >> 1);
-    if (owner) {  // row k+1 first, then publish it and its reciprocal
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i == i1) lu_slot_update(v[i], l[i], u, 16 * i + wrow + 1 > k, ty + 16 * i > k, tx, k);
-      if (ty == (n1 & 15)) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (i == i1) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) urow[buf ^ 1][tx + 16 * j] = v[i][j];
-          }
-        if (tx == (n1 & 15)) {
-          T p = v[0][0];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (i == i1 && j == i1) p = v[i][j];
-          rcps[buf ^ 1] = pivot_rcp(p);
-          if (pivot_bad(p)) atomicMin(&bad, n1);
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (!owner || i != i1) lu_slot_update(v[i], l[i], u, 16 * i + wrow + 1 > k, ty + 16 * i > k, tx, k);
-    __syncthreads();
-  }
+  diag_lu_regs<T, XV>(A, k0, w, ws, rcp, &bad, nullptr, 0);
   if (threadIdx.x == 0 && bad < w && info) atomicCAS(info, 0, (int)(k0 + bad + 1));
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = ty + 16 * i, c = tx + 16 * j;
-      if (r < w && c < w) A.put(k0 + r, k0 + c, v[i][j]);
-    }
 }
+
 
 // L21 = A21 U11^{-1} and U12 = L11^{-1} A12 are 64 x 64 x 64 tile products
 // against the diagonal-block inverses.  tile_fma: c +/-= P Q for P, Q in
@@ -1442,6 +1489,8 @@ ebv_status_t prepare_leaf_kernels() {
     const int bytes = (int)pair_smem_bytes<T, kNB>();
     cudaError_t e = set_smem(k_diag_factor<T, kNB, 4 * kNB>, (int)diagb_smem_bytes<T, kNB>());
     if (e == cudaSuccess)
+      e = set_smem(k_diag_factor<T, kNB, 4 * kNB, false, !(sizeof(T) == 8)>, (int)diagb_smem_bytes<T, kNB>());
+    if (e == cudaSuccess)
       e = set_smem(k_trsm_ru<T, SH, kNB>, bytes);
     if (e == cudaSuccess)
       e = set_smem(k_trsm_ll<T, SH, kNB>, bytes);
@@ -1480,6 +1529,8 @@ ebv_status_t prepare_xview_kernels() {
   static const cudaError_t err = [] {
     const int bytes = (int)pair_smem_bytes<T, kNB>();
     cudaError_t e = set_smem(k_diag_factor<T, kNB, 4 * kNB, true>, (int)diagb_smem_bytes<T, kNB>());
+    if (e == cudaSuccess)
+      e = set_smem(k_diag_factor<T, kNB, 4 * kNB, true, !(sizeof(T) == 8)>, (int)diagb_smem_bytes<T, kNB>());
     if (e == cudaSuccess) e = set_smem(k_trsm_ru<T, float, kNB, true>, bytes);
     if (e == cudaSuccess) e = set_smem(k_trsm_ll<T, float, kNB, true>, bytes);
     if (e == cudaSuccess) e = set_smem(k_trsm_ru_strip<T, float, kNB, 16, true>, bytes);
