@@ -148,11 +148,14 @@ __global__ void __launch_bounds__(256) k_trsm_ll_subst(MatView<T, XV> A, int64_t
   }
 }
 
-// Side stream and events of the FP64 panels' look-ahead, one set per device,
-// made by the first factorisation on the device.
+// Side streams and events of the FP64 panels' overlaps, one set per device,
+// made by the first factorisation on the device: `side` takes the
+// look-ahead's trailing updates, `side2` each panel's U12 (concurrent with
+// its L21).
 struct BandPipe {
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, go = nullptr, join = nullptr, done[2] = {};
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t fork = nullptr, go = nullptr, join = nullptr, join2 = nullptr, dg = nullptr, u12 = nullptr,
+              done[2] = {};
   bool ready = false;
 };
 constexpr int kMaxPipeDevices = 64;
@@ -167,7 +170,8 @@ ebv_status_t band_pipe(BandPipe **out) {
   BandPipe &p = g_band_pipe[dev];
   if (!p.ready) {
     EBV_CU(cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking));
-    for (cudaEvent_t *e : {&p.fork, &p.go, &p.join, &p.done[0], &p.done[1]})
+    EBV_CU(cudaStreamCreateWithFlags(&p.side2, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&p.fork, &p.go, &p.join, &p.join2, &p.dg, &p.u12, &p.done[0], &p.done[1]})
       EBV_CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     p.ready = true;
   }
@@ -176,7 +180,10 @@ ebv_status_t band_pipe(BandPipe **out) {
 }
 
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
-bool g_band_lookahead = true; // FP64 panels: trailing update split for look-ahead (testing hook)
+// FP64 panels' overlaps (testing hook): 0 = serial; 1 = look-ahead for the
+// symmetric storages, U12 beside L21 for the general ones (default); 2 =
+// also look-ahead for the general band.
+int g_band_overlap = 1;
 bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
 // FP64 panels' diagonal blocks: the register-resident kernel (true) or the
 // blocked 16 x 16 sub-block kernel (testing hook)
@@ -252,11 +259,18 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
   // measured on the 512 x 512 Laplacian: 899 -> 843 ms, while the general
   // band's full updates made it slower, 933 -> 1009 ms).  The side stream
   // joins `s` here and `s` waits for it at the end.
-  BandPipe *pipe = nullptr;
-  if (sizeof(T) == 8 && sym && g_band_subst && g_band_lookahead && !cluster && n > 2 * kNB) {
-    EBV_TRY(band_pipe(&pipe));
-    EBV_CU(cudaEventRecord(pipe->fork, s));
-    EBV_CU(cudaStreamWaitEvent(pipe->side, pipe->fork, 0));
+  // General bands: each panel's U12 on a second side stream, concurrent with
+  // its L21 (both read only the diagonal block and their own entries).
+  const bool fp64_subst = sizeof(T) == 8 && g_band_subst && !cluster;
+  const bool ahead = fp64_subst && n > 2 * kNB && (sym ? g_band_overlap >= 1 : g_band_overlap >= 2);
+  const bool u12_side = fp64_subst && !sym && n > kNB && g_band_overlap >= 1;
+  BandPipe *pipe = nullptr, *bp = nullptr;
+  if (ahead || u12_side) {
+    EBV_TRY(band_pipe(&bp));
+    EBV_CU(cudaEventRecord(bp->fork, s));
+    if (ahead) EBV_CU(cudaStreamWaitEvent(bp->side, bp->fork, 0));
+    if (u12_side) EBV_CU(cudaStreamWaitEvent(bp->side2, bp->fork, 0));
+    if (ahead) pipe = bp;
   }
   for (int64_t c0 = 0; c0 < n; c0 += kNB) {
     const int w = (int)std::min<int64_t>(kNB, n - c0);
@@ -307,13 +321,25 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
                 <<<1, 4 * kNB, diagb_smem_bytes<T, kNB>(), s>>>(Araw, c0, w, info, nullptr);
           EBV_TRY(launch_ok());
         }
+        const bool u12_beside = u12_side && ce > cb;
+        if (u12_beside) {  // U12 on side2 after the diagonal block (and the rest-update of panel p-1)
+          EBV_CU(cudaEventRecord(bp->dg, s));
+          EBV_CU(cudaStreamWaitEvent(bp->side2, bp->dg, 0));
+          if (pipe && p >= 1) EBV_CU(cudaStreamWaitEvent(bp->side2, pipe->done[(p - 1) & 1], 0));
+          prof::Scope ps(bp->side2, prof::kTrsm, 1.0 * w * w * (ce - cb));
+          k_trsm_ll_subst<T, kNB><<<ceil_div(ce - cb, 8), 256, 0, bp->side2>>>(A, c0, w, cb, ce, env);
+          EBV_TRY(launch_ok());
+          EBV_CU(cudaEventRecord(bp->u12, bp->side2));
+        }
         if (re > rb) {
           prof::Scope ps(s, prof::kL21, 1.0 * (re - rb) * w * w);
           k_trsm_ru_subst<T, kNB><<<ceil_div(re - rb, 8), 256, 0, s>>>(A, c0, w, rb, re, env);
           EBV_TRY(launch_ok());
         }
         if (pipe && p >= 1) EBV_CU(cudaStreamWaitEvent(s, pipe->done[(p - 1) & 1], 0));
-        if (ce > cb && sym) {
+        if (u12_beside) {
+          EBV_CU(cudaStreamWaitEvent(s, bp->u12, 0));
+        } else if (ce > cb && sym) {
           if (!A.symlo) {  // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
             prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
             k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
@@ -390,6 +416,10 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
   if (pipe) {
     EBV_CU(cudaEventRecord(pipe->join, pipe->side));
     EBV_CU(cudaStreamWaitEvent(s, pipe->join, 0));
+  }
+  if (u12_side) {
+    EBV_CU(cudaEventRecord(bp->join2, bp->side2));
+    EBV_CU(cudaStreamWaitEvent(s, bp->join2, 0));
   }
   return EBV_OK;
 }
@@ -482,7 +512,7 @@ size_t band_factor_ws(int64_t n, int64_t kl, int64_t, ebv_prec_t prec) {
 }
 void set_band_envelope(bool on) { g_band_envelope = on; }
 void set_band_cluster(bool on) { g_band_cluster = on; }
-void set_band_lookahead(bool on) { g_band_lookahead = on; }
+void set_band_overlap(int mode) { g_band_overlap = mode; }
 void set_diag_lu(bool on) { g_diag_lu = on; }
 size_t band_solve_ws(int64_t n, int64_t nrhs, ebv_prec_t prec) {
   return solve_layout(n, nrhs, prec == EBV_FP64 ? 8 : 4).total;

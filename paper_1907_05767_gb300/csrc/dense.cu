@@ -294,10 +294,15 @@ struct Factorizer {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 64><<<ceil_div(N, 64), 256, smem, s>>>(A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
       } else if (sizeof(T) == 4 && A.ld % 4 == 0 && ((uintptr_t)A.base) % 16 == 0) {
         // binary32 with 16-byte rows: everything resident in shared memory
-        if constexpr (sizeof(T) == 4)
-          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks>
-              <<<ceil_div(N, kResCW), 256, trsm_res_smem_bytes<kNB, kTrsmMaxBlocks>(), s>>>(
-                  A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
+        if constexpr (sizeof(T) == 4) {
+          // At most one wave: a CTA keeps its copy of L11's tiles for every
+          // strip it takes (the copy is most of a strip's time).
+          constexpr size_t rsm = trsm_res_smem_bytes<kNB, kTrsmMaxBlocks>();
+          static const int wave = coop_capacity(k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks>, rsm);
+          const int strips = ceil_div(N, kResCW);
+          k_trsm_ll_resident<SH, kNB, kTrsmMaxBlocks><<<wave > 0 ? std::min(strips, wave) : strips, 256, rsm, s>>>(
+              A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
+        }
       } else if (N >= 32 * 148) {
         k_trsm_ll_multi<T, SH, kNB, kTrsmMaxBlocks, 32><<<ceil_div(N, 32), 256, smem, s>>>(A, r0, (int)h, cl, ch, leaf_inv(r0), sh);
       } else {

@@ -1361,19 +1361,12 @@ __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int6
   float *U = Lbase + (MAXB * (MAXB + 1) / 2) * NB * TS;    // MAXB blocks of 64 x CW
   float *red = U + MAXB * NB * US;                          // 4 partial 64 x CW sums
   auto ltile = [&](int j, int i) { return Lbase + (j * (j + 1) / 2 + i) * NB * TS; };  // i == j: the inverse
-  const int64_t c0 = c_begin + (int64_t)blockIdx.x * CW;
-  const int wc = (int)min64(CW, c_end - c0);
   const int nbk = ceil_div(h, NB);
-  // One batch of asynchronous copies: strip of A12, L_ji, L_jj^{-1}.
+  // One batch of asynchronous copies of L_ji and L_jj^{-1}, kept for every
+  // strip this CTA takes (strips s = blockIdx.x + gridDim.x t).
   for (int j = 0; j < nbk; ++j) {
     const int64_t rj = r0 + (int64_t)j * NB;
     const int hj = min(NB, h - j * NB);
-    float *Uj = U + j * NB * US;
-    for (int e = threadIdx.x; e < NB * (CW / 4); e += 256) {
-      const int k = e / (CW / 4), c = 4 * (e % (CW / 4));
-      const int nb = (k < hj) ? 4 * max(0, min(4, wc - c)) : 0;
-      cp_async16(Uj + k * US + c, nb ? A.base + (rj + k) * A.ld + c0 + c : A.base, nb);
-    }
     for (int i = 0; i < j; ++i) {
       float *Lt = ltile(j, i);
       const int64_t ri = r0 + (int64_t)i * NB;
@@ -1389,95 +1382,111 @@ __global__ void __launch_bounds__(256) k_trsm_ll_resident(MatView<float> A, int6
       cp_async16(Li + k * TS + c, linv + k * NB + c, 16);
     }
   }
-  cp_async_wait_all();
-  __syncthreads();
-  // Thread mapping of the split products: group q = tid / 64 takes a quarter
-  // of K; inside it thread t holds rows t/4 + 16a (a < 4), columns 4 (t % 4) .. +3.
-  const int q = threadIdx.x >> 6, t = threadIdx.x & 63;
-  const int pr = t >> 2, pc = 4 * (t & 3);
-  // Final mapping: thread tid holds row tid/4, columns 4 (tid % 4) .. +3.
-  const int fr = threadIdx.x >> 2, fc = 4 * (threadIdx.x & 3);
-  // out = sum over the np products P_m Q_m (P: 64 x 64, stride TS; Q: 64 x CW, stride US).
-  auto split_sum = [&](int np, auto P_of, auto Q_of, float (&out)[4]) {
-    float c[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) c[a][b] = 0.f;
-    const int kq = 16 * np;  // this group's share of the np * 64 terms
-    for (int kk = q * kq; kk < (q + 1) * kq; kk += 16) {
-      const float *P = P_of(kk >> 6);
-      const float *Q = Q_of(kk >> 6);
-      const int k0 = kk & 63;
-#pragma unroll
-      for (int k = k0; k < k0 + 16; k += 4) {  // four k per vector load of each P row
-        float4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4 *>(Q + (k + u) * US + pc);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float4 p4 = *reinterpret_cast<const float4 *>(P + (pr + 16 * a) * TS + k);
-          const float p[4] = {p4.x, p4.y, p4.z, p4.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            c[a][0] += p[u] * v[u].x;
-            c[a][1] += p[u] * v[u].y;
-            c[a][2] += p[u] * v[u].z;
-            c[a][3] += p[u] * v[u].w;
+  const int nstrips = ceil_div(c_end - c_begin, CW);
+  for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
+    const int64_t c0 = c_begin + (int64_t)strip * CW;
+    const int wc = (int)min64(CW, c_end - c0);
+    for (int j = 0; j < nbk; ++j) {  // the strip of A12 (with the L tiles on the first strip)
+      const int64_t rj = r0 + (int64_t)j * NB;
+      const int hj = min(NB, h - j * NB);
+      float *Uj = U + j * NB * US;
+      for (int e = threadIdx.x; e < NB * (CW / 4); e += 256) {
+        const int k = e / (CW / 4), c = 4 * (e % (CW / 4));
+        const int nb = (k < hj) ? 4 * max(0, min(4, wc - c)) : 0;
+        cp_async16(Uj + k * US + c, nb ? A.base + (rj + k) * A.ld + c0 + c : A.base, nb);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // Thread mapping of the split products: group q = tid / 64 takes a quarter
+    // of K; inside it thread t holds rows t/4 + 16a (a < 4), columns 4 (t % 4) .. +3.
+    const int q = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int pr = t >> 2, pc = 4 * (t & 3);
+    // Final mapping: thread tid holds row tid/4, columns 4 (tid % 4) .. +3.
+    const int fr = threadIdx.x >> 2, fc = 4 * (threadIdx.x & 3);
+    // out = sum over the np products P_m Q_m (P: 64 x 64, stride TS; Q: 64 x CW, stride US).
+    auto split_sum = [&](int np, auto P_of, auto Q_of, float (&out)[4]) {
+      float c[4][4];
+  #pragma unroll
+      for (int a = 0; a < 4; ++a)
+  #pragma unroll
+        for (int b = 0; b < 4; ++b) c[a][b] = 0.f;
+      const int kq = 16 * np;  // this group's share of the np * 64 terms
+      for (int kk = q * kq; kk < (q + 1) * kq; kk += 16) {
+        const float *P = P_of(kk >> 6);
+        const float *Q = Q_of(kk >> 6);
+        const int k0 = kk & 63;
+  #pragma unroll
+        for (int k = k0; k < k0 + 16; k += 4) {  // four k per vector load of each P row
+          float4 v[4];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4 *>(Q + (k + u) * US + pc);
+  #pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float4 p4 = *reinterpret_cast<const float4 *>(P + (pr + 16 * a) * TS + k);
+            const float p[4] = {p4.x, p4.y, p4.z, p4.w};
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              c[a][0] += p[u] * v[u].x;
+              c[a][1] += p[u] * v[u].y;
+              c[a][2] += p[u] * v[u].z;
+              c[a][3] += p[u] * v[u].w;
+            }
           }
         }
       }
+  #pragma unroll
+      for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4 *>(red + q * NB * US + (pr + 16 * a) * US + pc) =
+            make_float4(c[a][0], c[a][1], c[a][2], c[a][3]);
+      __syncthreads();
+  #pragma unroll
+      for (int b = 0; b < 4; ++b) out[b] = 0.f;
+  #pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const float4 v = *reinterpret_cast<const float4 *>(red + g * NB * US + fr * US + fc);
+        out[0] += v.x, out[1] += v.y, out[2] += v.z, out[3] += v.w;
+      }
+      __syncthreads();  // red is free again
+    };
+    for (int j = 0; j < nbk; ++j) {
+      float *Uj = U + j * NB * US;
+      float acc[4];
+      {
+        const float4 v = *reinterpret_cast<const float4 *>(Uj + fr * US + fc);
+        acc[0] = v.x, acc[1] = v.y, acc[2] = v.z, acc[3] = v.w;
+      }
+      if (j > 0) {  // acc = A_j - sum_{i<j} L_ji U_i
+        float sum[4];
+        split_sum(j, [&](int m) { return (const float *)ltile(j, m); }, [&](int m) { return (const float *)(U + m * NB * US); },
+                  sum);
+  #pragma unroll
+        for (int b = 0; b < 4; ++b) acc[b] -= sum[b];
+      }
+      *reinterpret_cast<float4 *>(Uj + fr * US + fc) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      __syncthreads();
+      float out[4];  // U_j = L_jj^{-1} acc
+      split_sum(1, [&](int) { return (const float *)ltile(j, j); }, [&](int) { return (const float *)Uj; }, out);
+      *reinterpret_cast<float4 *>(Uj + fr * US + fc) = make_float4(out[0], out[1], out[2], out[3]);
+      __syncthreads();
     }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-      *reinterpret_cast<float4 *>(red + q * NB * US + (pr + 16 * a) * US + pc) =
-          make_float4(c[a][0], c[a][1], c[a][2], c[a][3]);
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < 4; ++b) out[b] = 0.f;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const float4 v = *reinterpret_cast<const float4 *>(red + g * NB * US + fr * US + fc);
-      out[0] += v.x, out[1] += v.y, out[2] += v.z, out[3] += v.w;
-    }
-    __syncthreads();  // red is free again
-  };
-  for (int j = 0; j < nbk; ++j) {
-    float *Uj = U + j * NB * US;
-    float acc[4];
-    {
-      const float4 v = *reinterpret_cast<const float4 *>(Uj + fr * US + fc);
-      acc[0] = v.x, acc[1] = v.y, acc[2] = v.z, acc[3] = v.w;
-    }
-    if (j > 0) {  // acc = A_j - sum_{i<j} L_ji U_i
-      float sum[4];
-      split_sum(j, [&](int m) { return (const float *)ltile(j, m); }, [&](int m) { return (const float *)(U + m * NB * US); },
-                sum);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[b] -= sum[b];
-    }
-    *reinterpret_cast<float4 *>(Uj + fr * US + fc) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    __syncthreads();
-    float out[4];  // U_j = L_jj^{-1} acc
-    split_sum(1, [&](int) { return (const float *)ltile(j, j); }, [&](int) { return (const float *)Uj; }, out);
-    *reinterpret_cast<float4 *>(Uj + fr * US + fc) = make_float4(out[0], out[1], out[2], out[3]);
-    __syncthreads();
-  }
-  for (int j = 0; j < nbk; ++j) {
-    const int64_t rj = r0 + (int64_t)j * NB;
-    const int hj = min(NB, h - j * NB);
-    const float *Uj = U + j * NB * US;
-    for (int e = threadIdx.x; e < NB * CW; e += 256) {
-      const int k = e / CW, c = e % CW;
-      if (k < hj && c < wc) A.put(rj + k, c0 + c, Uj[k * US + c]);
-    }
-    if (sh.ut) {
-      const float s = sh.scale[1];
+    for (int j = 0; j < nbk; ++j) {
+      const int64_t rj = r0 + (int64_t)j * NB;
+      const int hj = min(NB, h - j * NB);
+      const float *Uj = U + j * NB * US;
       for (int e = threadIdx.x; e < NB * CW; e += 256) {
-        const int c = e / NB, k = e % NB;
-        if (k < hj && c < wc) sh.ut[(c0 + c) * sh.ld + rj + k] = from_float<SH>(Uj[k * US + c] * s);
+        const int k = e / CW, c = e % CW;
+        if (k < hj && c < wc) A.put(rj + k, c0 + c, Uj[k * US + c]);
+      }
+      if (sh.ut) {
+        const float s = sh.scale[1];
+        for (int e = threadIdx.x; e < NB * CW; e += 256) {
+          const int c = e / NB, k = e % NB;
+          if (k < hj && c < wc) sh.ut[(c0 + c) * sh.ld + rj + k] = from_float<SH>(Uj[k * US + c] * s);
+        }
       }
     }
+    __syncthreads();  // U and red are rewritten by the next strip
   }
 }
 

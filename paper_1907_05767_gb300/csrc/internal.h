@@ -36,7 +36,7 @@ void set_band_envelope(bool on);
 // Testing hook: true = band panels on thread-block clusters (default false).
 void set_band_cluster(bool on);
 // Testing hook: false = FP64 band panels without look-ahead (default true).
-void set_band_lookahead(bool on);
+void set_band_overlap(int mode);
 void set_diag_lu(bool on);
 // Dense FP64 factorisation of a small system as right-looking 64-column
 // panels (band.cu); orders up to kSmallDenseMaxN use it.
