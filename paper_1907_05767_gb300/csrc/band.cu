@@ -354,10 +354,10 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
           auto gemm = [&](int64_t n0, int64_t n1, cudaStream_t st) -> ebv_status_t {
             if (n1 <= n0) return EBV_OK;
             prof::Scope ps(st, prof::kSimtGemm, 2.0 * (re - rb) * (n1 - n0) * w);
+            constexpr int nt = (G::BM / G::TM) * (G::BN / G::TN);
             dim3 grid(ceil_div(n1 - n0, G::BN), ceil_div(re - rb, G::BM));
-            k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN>
-                <<<grid, (G::BM / G::TM) * (G::BN / G::TN), 0, st>>>(A, rb, n0, c0, re - rb, n1 - n0, w,
-                                                                     sym ? 1 : 0, env);
+            k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<grid, nt, 0, st>>>(A, rb, n0, c0, re - rb, n1 - n0, w,
+                                                                                    sym ? 1 : 0, env);
             return launch_ok();
           };
           const int64_t split = pipe ? std::min<int64_t>(ce, cb + kNB) : ce;

@@ -128,37 +128,85 @@ __device__ void warp_tri_inverses(BatchSmem<T, NB> &sm, int w, int warp, int lan
   __syncwarp();
 }
 
+// Products of an edge tile (it overhangs A22), FP64: only this warp's row
+// blocks q < qn (warp-uniform) and the column blocks u < UN (CTA-uniform)
+// that hold entries of A22, so no FP64 warp instruction (which costs the
+// pipe the same whatever its active lanes) is issued for entries outside it.
+template <int TT, int UN, typename T, int NB>
+__device__ __forceinline__ void edge_products(const BatchSmem<T, NB> &sm, int ty, int tx, int qn, T (&acc)[TT][TT]) {
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    if (q >= qn) break;
+#pragma unroll 4
+    for (int k = 0; k < NB; ++k) {
+      const T a = sm.As[k][ty + 16 * q];
+#pragma unroll
+      for (int u = 0; u < UN; ++u) acc[q][u] += a * sm.Bs[k][tx + 16 * u];
+    }
+  }
+}
+
 // A22 -= L21 U12 for the m x m trailing block (rows/cols k0+w..n-1) of one
 // system, K = w: TM x TM output tiles (TM = 64: a 4 x 4 register block per
-// thread; TM = 32: 2 x 2).  The K-slabs of L21 and U12 are read with
-// consecutive threads on consecutive addresses of a row (coalesced) and
-// stored transposed for L21; the tile of C is loaded into registers before
-// the slab products, so its latency overlaps them.
+// thread; TM = 32: 2 x 2), taken in row-major order.  The K-slabs of L21 and
+// U12 are read with consecutive threads on consecutive addresses of a row
+// (coalesced) and stored transposed for L21.  Binary32 is software-pipelined:
+// while a tile's products run, the next tile's C and both slabs are already
+// loading into registers, so each tile pays no global-memory round trip of
+// its own.
 template <typename T, int NB, int TM>
 __device__ void cta_trailing_update(BatchSmem<T, NB> &sm, T *A, int n, int k0, int w) {
-  constexpr int TT = TM / 16;  // outputs per thread along each dimension
+  constexpr int TT = TM / 16;          // outputs per thread along each dimension
+  constexpr int SL = NB * TM / BT;     // slab elements per thread (each of L21 and U12)
+  static_assert(SL * BT == NB * TM, "slab split");
   const int base = k0 + w, m = n - base;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  for (int ti = 0; ti < m; ti += TM) {
-    for (int tj = 0; tj < m; tj += TM) {
-      T c[TT][TT];
+  const int nt = (m + TM - 1) / TM, ntiles = nt * nt;
+  T cn[TT][TT], an[SL], bn[SL];  // the next tile's C and slabs
+  auto fetch = [&](int tile) {
+    const int ti = (tile / nt) * TM, tj = (tile % nt) * TM;
 #pragma unroll
-      for (int q = 0; q < TT; ++q) {
-        const int i = ti + ty + 16 * q;
+    for (int q = 0; q < TT; ++q) {
+      const int i = ti + ty + 16 * q;
 #pragma unroll
-        for (int u = 0; u < TT; ++u) {
-          const int j = tj + tx + 16 * u;
-          c[q][u] = (i < m && j < m) ? A[(int64_t)(base + i) * n + base + j] : T(0);
-        }
+      for (int u = 0; u < TT; ++u) {
+        const int j = tj + tx + 16 * u;
+        cn[q][u] = (i < m && j < m) ? A[(int64_t)(base + i) * n + base + j] : T(0);
       }
-      for (int e = threadIdx.x; e < NB * TM; e += BT) {
-        const int x = e / NB, k = e % NB;  // L21: row x of the tile, k along the row
-        sm.As[k][x] = (k < w && ti + x < m) ? A[(int64_t)(base + ti + x) * n + k0 + k] : T(0);
-        const int kb = e / TM, xb = e % TM;  // U12: row kb, xb along the row
-        sm.Bs[kb][xb] = (kb < w && tj + xb < m) ? A[(int64_t)(k0 + kb) * n + base + tj + xb] : T(0);
-      }
-      __syncthreads();
-      T acc[TT][TT] = {};
+    }
+#pragma unroll
+    for (int v = 0; v < SL; ++v) {
+      const int e = threadIdx.x + v * BT;
+      const int x = e / NB, k = e % NB;  // L21: row x of the tile, k along the row
+      an[v] = (k < w && ti + x < m) ? A[(int64_t)(base + ti + x) * n + k0 + k] : T(0);
+      const int kb = e / TM, xb = e % TM;  // U12: row kb, xb along the row
+      bn[v] = (kb < w && tj + xb < m) ? A[(int64_t)(k0 + kb) * n + base + tj + xb] : T(0);
+    }
+  };
+  // FP64 (its pipe, not latency, bounds it) fetches each tile when it starts:
+  // prefetching too would spill the doubles' registers.
+  constexpr bool ahead = sizeof(T) == 4;
+  if (ahead && ntiles > 0) fetch(0);
+  for (int tile = 0; tile < ntiles; ++tile) {
+    if (!ahead) fetch(tile);
+    const int ti = (tile / nt) * TM, tj = (tile % nt) * TM;
+    T c[TT][TT];
+#pragma unroll
+    for (int q = 0; q < TT; ++q)
+#pragma unroll
+      for (int u = 0; u < TT; ++u) c[q][u] = cn[q][u];
+#pragma unroll
+    for (int v = 0; v < SL; ++v) {
+      const int e = threadIdx.x + v * BT;
+      sm.As[e % NB][e / NB] = an[v];
+      sm.Bs[e / TM][e % TM] = bn[v];
+    }
+    __syncthreads();
+    if (ahead && tile + 1 < ntiles) fetch(tile + 1);  // in flight during the products below
+    T acc[TT][TT] = {};
+    // (binary32 takes the full-tile loop everywhere: the edge loop's extra
+    // shared-memory loads cost it more than the skipped FMAs save)
+    if (sizeof(T) == 4 || (ti + TM <= m && tj + TM <= m)) {
 #pragma unroll 8
       for (int k = 0; k < NB; ++k) {
         T ra[TT], rb[TT];
@@ -172,20 +220,46 @@ __device__ void cta_trailing_update(BatchSmem<T, NB> &sm, T *A, int n, int k0, i
 #pragma unroll
           for (int u = 0; u < TT; ++u) acc[q][u] += ra[q] * rb[u];
       }
-#pragma unroll
-      for (int q = 0; q < TT; ++q) {
-        const int i = ti + ty + 16 * q;
-        if (i >= m) continue;
-        T *row = A + (int64_t)(base + i) * n + base;
-#pragma unroll
-        for (int u = 0; u < TT; ++u) {
-          const int j = tj + tx + 16 * u;
-          if (j < m) row[j] = c[q][u] - acc[q][u];
-        }
-      }
-      __syncthreads();
+    } else {
+      const int qn = min(TT, max(0, (m - ti - (ty & ~1) + 15) / 16));  // this warp's rows: (ty & ~1) + {0, 1}
+      const int un = min(TT, (m - tj + 15) / 16);
+      if (un == 1) edge_products<TT, 1>(sm, ty, tx, qn, acc);
+      if constexpr (TT >= 2)
+        if (un == 2) edge_products<TT, 2>(sm, ty, tx, qn, acc);
+      if constexpr (TT >= 3)
+        if (un == 3) edge_products<TT, 3>(sm, ty, tx, qn, acc);
+      if constexpr (TT >= 4)
+        if (un == 4) edge_products<TT, 4>(sm, ty, tx, qn, acc);
     }
+#pragma unroll
+    for (int q = 0; q < TT; ++q) {
+      const int i = ti + ty + 16 * q;
+      if (i >= m) continue;
+      T *row = A + (int64_t)(base + i) * n + base;
+#pragma unroll
+      for (int u = 0; u < TT; ++u) {
+        const int j = tj + tx + 16 * u;
+        if (j < m) row[j] = c[q][u] - acc[q][u];
+      }
+    }
+    __syncthreads();
   }
+}
+
+// sum_{r < w} f[r] y[r][c] for one row f of a factor (global memory) and a
+// solved block y (shared memory): the row's w <= NB entries are loaded
+// together (unrolled to NB, predicated), so a row costs one memory round
+// trip, not w dependent ones.
+template <typename T, int NB>
+__device__ __forceinline__ T block_dot(const T *f, int w, const T (*y)[64 + 1], int c) {
+  T v[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) v[r] = r < w ? f[r] : T(0);
+  T s = T(0);
+#pragma unroll
+  for (int r = 0; r < NB; ++r)
+    if (r < w) s += v[r] * y[r][c];  // rows of y past w are not part of the block
+  return s;
 }
 
 // In-place LU (packed L\U) of one n x n system, then X = U^{-1} L^{-1} B.
@@ -209,16 +283,30 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
       const int i = e / w, j = e % w;
       A[(int64_t)(k0 + i) * n + k0 + j] = sm.D[i][j];
     }
-    // L21 = A21 U11^{-1} (Eq. 6a for every row below), 64-row tiles.
+    // L21 = A21 U11^{-1} (Eq. 6a for every row below), 64-row tiles, the
+    // next tile's entries loading into registers while one is multiplied.
+    constexpr int PT = 64 * NB / BT;  // tile entries per thread
+    T pf[PT];
+    auto fetch_l = [&](int t0) {
+      const int h = min(64, n - t0);
+#pragma unroll
+      for (int v = 0; v < PT; ++v) {
+        const int e = threadIdx.x + v * BT, r = e / NB, k = e % NB;
+        pf[v] = (r < h && k < w) ? A[(int64_t)(t0 + r) * n + k0 + k] : T(0);
+      }
+    };
     T(*tile)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(&sm.As[0][0]);  // 64 x NB fits in As + Bs
+    if (k0 + w < n) fetch_l(k0 + w);
     for (int t0 = k0 + w; t0 < n; t0 += 64) {
       const int h = min(64, n - t0);
       __syncthreads();
-      for (int e = threadIdx.x; e < 64 * NB; e += BT) {
-        const int r = e / NB, k = e % NB;
-        tile[r][k] = (r < h && k < w) ? A[(int64_t)(t0 + r) * n + k0 + k] : T(0);
+#pragma unroll
+      for (int v = 0; v < PT; ++v) {
+        const int e = threadIdx.x + v * BT;
+        tile[e / NB][e % NB] = pf[v];
       }
       __syncthreads();
+      if (t0 + 64 < n) fetch_l(t0 + 64);
       const int r = threadIdx.x >> 2, cq = threadIdx.x & 3;
       T out[NB / 4];
 #pragma unroll
@@ -234,15 +322,27 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
         for (int q = 0; q < NB / 4; ++q)
           if (cq + 4 * q < w) A[(int64_t)(t0 + r) * n + k0 + cq + 4 * q] = out[q];
     }
-    // U12 = L11^{-1} A12 (Eq. 6b for every column to the right), 64-column tiles.
+    // U12 = L11^{-1} A12 (Eq. 6b for every column to the right), 64-column
+    // tiles, prefetched the same way.
+    auto fetch_u = [&](int t0) {
+      const int h = min(64, n - t0);
+#pragma unroll
+      for (int v = 0; v < PT; ++v) {
+        const int e = threadIdx.x + v * BT, k = e / 64, c = e % 64;
+        pf[v] = (k < w && c < h) ? A[(int64_t)(k0 + k) * n + t0 + c] : T(0);
+      }
+    };
+    if (k0 + w < n) fetch_u(k0 + w);
     for (int t0 = k0 + w; t0 < n; t0 += 64) {
       const int h = min(64, n - t0);
       __syncthreads();
-      for (int e = threadIdx.x; e < NB * 64; e += BT) {
-        const int k = e / 64, c = e % 64;
-        sm.Bs[k][c] = (k < w && c < h) ? A[(int64_t)(k0 + k) * n + t0 + c] : T(0);
+#pragma unroll
+      for (int v = 0; v < PT; ++v) {
+        const int e = threadIdx.x + v * BT;
+        sm.Bs[e / 64][e % 64] = pf[v];
       }
       __syncthreads();
+      if (t0 + 64 < n) fetch_u(t0 + 64);
       const int c = threadIdx.x & 63, rg = threadIdx.x >> 6;
       T out[NB / 4];
 #pragma unroll
@@ -292,10 +392,7 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
     for (int e = threadIdx.x; e < w * nrhs; e += BT) B[(int64_t)k0 * nrhs + e] = Bs[e / nrhs][e % nrhs];
     for (int e = threadIdx.x; e < (n - k0 - w) * nrhs; e += BT) {
       const int i = k0 + w + e / nrhs, c = e % nrhs;
-      const T *li = A + (int64_t)i * n + k0;
-      T s = T(0);
-      for (int r = 0; r < w; ++r) s += li[r] * Bs[r][c];
-      B[(int64_t)i * nrhs + c] -= s;
+      B[(int64_t)i * nrhs + c] -= block_dot<T, NB>(A + (int64_t)i * n + k0, w, Bs, c);
     }
     __syncthreads();
   }
@@ -325,10 +422,7 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
     for (int e = threadIdx.x; e < w * nrhs; e += BT) B[(int64_t)k0 * nrhs + e] = Bs[e / nrhs][e % nrhs];
     for (int e = threadIdx.x; e < k0 * nrhs; e += BT) {
       const int i = e / nrhs, c = e % nrhs;
-      const T *ui = A + (int64_t)i * n + k0;
-      T s = T(0);
-      for (int r = 0; r < w; ++r) s += ui[r] * Bs[r][c];
-      B[(int64_t)i * nrhs + c] -= s;
+      B[(int64_t)i * nrhs + c] -= block_dot<T, NB>(A + (int64_t)i * n + k0, w, Bs, c);
     }
     __syncthreads();
   }

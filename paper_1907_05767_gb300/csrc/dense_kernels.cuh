@@ -1580,21 +1580,17 @@ __global__ void __launch_bounds__(256) k_sym_u12(MatView<T, XV> A, int64_t c0, i
 // steps):  A(m0+i, n0+j) -= sum_k A(m0+i, k0+k) * A(k0+k, n0+j).
 // Register-tiled: each thread owns a TM x TN block of C.
 // ---------------------------------------------------------------------------
-template <typename T, int BM, int BN, int BK, int TM, int TN, bool XV = false>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    k_gemm_nn(MatView<T, XV> A, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, int lower64 = 0,
-              Envelope env = {}) {
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool XV>
+__device__ __forceinline__ void gemm_nn_tile(MatView<T, XV> A, int64_t bm, int64_t bn, int64_t mend, int64_t nend,
+                                             int64_t k0, int64_t kend, int lower64, Envelope env,
+                                             T (*As)[BM + 1], T (*Bs)[BN + 1]) {
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
   const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
-  const int64_t bm = m0 + (int64_t)blockIdx.y * BM, bn = n0 + (int64_t)blockIdx.x * BN;
-  const int64_t mend = m0 + M, nend = n0 + N, kend = k0 + K;
   // lower64 (symmetric update): only the tiles of 64-blocks on or below the
   // diagonal (absolute block indices; BM, BN divide 64).
   if (lower64 && bn / 64 > bm / 64) return;
   // outside the envelope (BM, BN divide 64 and m0, n0 start 64-blocks): nothing to subtract
-  if (env.rows_empty(bm, k0 + K) || env.cols_empty(bn, k0 + K)) return;
+  if (env.rows_empty(bm, kend) || env.cols_empty(bn, kend)) return;
   T acc[TM][TN];
 #pragma unroll
   for (int a = 0; a < TM; ++a)
@@ -1639,6 +1635,16 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       }
     }
   }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool XV = false>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm_nn(MatView<T, XV> A, int64_t m0, int64_t n0, int64_t k0, int64_t M, int64_t N, int64_t K, int lower64 = 0,
+              Envelope env = {}) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  gemm_nn_tile<T, BM, BN, BK, TM, TN, XV>(A, m0 + (int64_t)blockIdx.y * BM, n0 + (int64_t)blockIdx.x * BN, m0 + M,
+                                          n0 + N, k0, k0 + K, lower64, env, As, Bs);
 }
 
 // ---------------------------------------------------------------------------
