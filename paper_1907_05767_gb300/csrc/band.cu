@@ -72,27 +72,28 @@ __global__ void __launch_bounds__(256) k_band_envelope(MatView<T, XV> A, int64_t
 }
 
 // L21 = A21 U11^{-1} by substitution (FP64 panels): one warp per row of
-// A21; lane l holds columns l and l+32 of the row.  Step j: the lane holding
+// A21, NW rows per CTA; lane l holds columns l and l+32 of the row.  Step j: the lane holding
 // column j forms l_ij = (a_ij - sum_{k<j} l_ik u_kj) / u_jj with the FP64
 // reciprocal and passes it by shuffle; every lane subtracts l_ij u_jc from
 // its later columns c (U11 and the reciprocals staged in shared memory).  The
 // 64-step chain per row needs no inverse of U11, so the diagonal-block kernel
 // only factors; rows run on many SMs.  Rows of 64-blocks outside the
 // envelope hold zeros and are skipped.
-template <typename T, int NB, bool XV>
-__global__ void __launch_bounds__(256) k_trsm_ru_subst(MatView<T, XV> A, int64_t c0, int w, int64_t rb, int64_t re,
-                                                       Envelope env) {
+template <typename T, int NB, int NW, bool XV>
+__global__ void __launch_bounds__(32 * NW) k_trsm_ru_subst(MatView<T, XV> A, int64_t c0, int w, int64_t rb,
+                                                           int64_t re, Envelope env) {
+  constexpr int NT = 32 * NW;
   __shared__ T Us[NB][NB + 1];
   __shared__ T rc[NB];
-  for (int e = threadIdx.x; e < NB * NB; e += 256) {
+  for (int e = threadIdx.x; e < NB * NB; e += NT) {
     const int k = e / NB, c = e % NB;
     Us[k][c] = (k < w && c < w && c >= k) ? A.get(c0 + k, c0 + c) : T(0);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < NB; k += 256) rc[k] = k < w ? pivot_rcp(Us[k][k]) : T(0);
+  for (int k = threadIdx.x; k < NB; k += NT) rc[k] = k < w ? pivot_rcp(Us[k][k]) : T(0);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t i = rb + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t i = rb + (int64_t)blockIdx.x * NW + (threadIdx.x >> 5);
   if (i >= re || env.rows_empty(i, c0 + w)) return;
   T a0 = lane < w ? A.get(i, c0 + lane) : T(0);
   T a1 = lane + 32 < w ? A.get(i, c0 + lane + 32) : T(0);
@@ -333,7 +334,14 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
         }
         if (re > rb) {
           prof::Scope ps(s, prof::kL21, 1.0 * (re - rb) * w * w);
-          k_trsm_ru_subst<T, kNB><<<ceil_div(re - rb, 8), 256, 0, s>>>(A, c0, w, rb, re, env);
+          // Symmetric storages: four rows per CTA, so one warp per SMSP keeps
+          // its FP64 pipe to itself (each row's chain issues three FP64 warp
+          // instructions per step; 512 x 512 Laplacian 621 -> 602 ms).  The
+          // general band keeps eight: its U12 runs beside on other SMs.
+          if (sym)
+            k_trsm_ru_subst<T, kNB, 4><<<ceil_div(re - rb, 4), 128, 0, s>>>(A, c0, w, rb, re, env);
+          else
+            k_trsm_ru_subst<T, kNB, 8><<<ceil_div(re - rb, 8), 256, 0, s>>>(A, c0, w, rb, re, env);
           EBV_TRY(launch_ok());
         }
         if (pipe && p >= 1) EBV_CU(cudaStreamWaitEvent(s, pipe->done[(p - 1) & 1], 0));
