@@ -88,9 +88,17 @@ __device__ __forceinline__ float to_float(__half x) { return __half2float(x); }
 // cycles per pivot step), so the FP64 form costs nothing extra on the chain.
 __device__ __forceinline__ double pivot_rcp(double p) { return 1.0 / p; }
 __device__ __forceinline__ float pivot_rcp(float p) { return (float)(1.0 / (double)p); }
-// A zero or non-finite pivot (tested in the working precision).
-template <typename T>
-__device__ __forceinline__ bool pivot_bad(T p) { return !(p != T(0)) || !isfinite(p); }
+// A zero or non-finite pivot (tested in the working precision), on the bit
+// pattern: zero of either sign, or the all-ones exponent of Inf / NaN (no
+// floating-point compare on the pivot chain).
+__device__ __forceinline__ bool pivot_bad(double p) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+  return (b << 1) == 0ull || ((b >> 52) & 0x7FFull) == 0x7FFull;
+}
+__device__ __forceinline__ bool pivot_bad(float p) {
+  const unsigned int b = __float_as_uint(p);
+  return (b << 1) == 0u || ((b >> 23) & 0xFFu) == 0xFFu;
+}
 
 // Record the first device-side failure in a status block (first writer wins).
 __device__ __forceinline__ void set_status(DevStatus *st, int code, int where) {

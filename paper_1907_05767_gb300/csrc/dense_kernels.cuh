@@ -428,9 +428,12 @@ __device__ __forceinline__ void warp_tri_inv16(const T *D, T *Z, int ld, int o, 
 template <typename T>
 __device__ __forceinline__ void lu_slot_update(T (&v)[4], T a, const T (&w)[4], bool live, bool rok, int tx, int k) {
   if (!live) return;
+  const int jb = (k + 1) >> 4;  // column blocks j < jb hold no column > k (warp-uniform)
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (16 * j + 15 > k && rok && tx + 16 * j > k) v[j] -= a * w[j];
+  for (int j = 0; j < 4; ++j) {
+    if (j < jb) continue;
+    if (rok && tx + 16 * j > k) v[j] -= a * w[j];
+  }
 }
 
 // Publish pivot row n of the register-resident diagonal block from the warp
