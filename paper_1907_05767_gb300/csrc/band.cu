@@ -182,9 +182,10 @@ ebv_status_t band_pipe(BandPipe **out) {
 
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
 // FP64 panels' overlaps (testing hook): 0 = serial; 1 = look-ahead for the
-// symmetric storages, U12 beside L21 for the general ones (default); 2 =
-// also look-ahead for the general band.
-int g_band_overlap = 1;
+// symmetric storages, U12 beside L21 for the general ones; 2 (default) =
+// also look-ahead for the general band (512 x 512 Laplacian, two runs: 639
+// and 640 ms against 649 and 650 without it).
+int g_band_overlap = 2;
 bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
 // FP64 panels' diagonal blocks: the register-resident kernel (true) or the
 // blocked 16 x 16 sub-block kernel (testing hook)
@@ -194,6 +195,21 @@ bool g_diag_lu = true;
 // against 1233 ms on clusters, so the cluster panels serve the lower-half
 // symmetric storage only, which needs them.
 bool g_band_cluster = false;
+
+// Symmetric band with both halves stored (EBV_BAND_SYM): the factorisation
+// runs on the lower half only (the lower-half view of the same array), then
+// this fills the upper half with U = D L^T, u_ij = d_i l_ji (Eq. 6a-b scale
+// both vectors by the same pivot), the one product the per-panel U12 kernel
+// formed.  One thread per stored entry i, j = i+1 .. i+kl; the writes of a
+// row are contiguous.
+template <typename T>
+__global__ void __launch_bounds__(256) k_band_fill_upper(T *ab, int64_t ldab, int64_t n, int64_t kl) {
+  const int64_t total = n * kl;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
+    const int64_t i = e / kl, t = e % kl + 1, j = i + t;
+    if (j < n) ab[i * ldab + kl + t] = ab[i * ldab + kl] * ab[j * ldab + kl - t];
+  }
+}
 
 // Binary32 working copy of the whole band array (mixed precisions): count
 // elements, grid-stride.  Slots outside the matrix are copied too and, as in
@@ -284,12 +300,7 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
         cluster = false;  // the device cannot run the cluster: one-CTA kernels from here on
       } else {
         EBV_TRY(st);
-        // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
-        if (ce > cb && sym && !A.symlo) {
-          prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
-          k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
-          EBV_TRY(launch_ok());
-        }
+        // (symmetric storages: U12 = D11 L21^T is implied, the lower-half view reads it so)
         if (re > rb && ce > cb) {
           prof::Scope ps(s, prof::kSimtGemm, 2.0 * (re - rb) * (ce - cb) * w);
           dim3 grid(ceil_div(ce - cb, G::BN), ceil_div(re - rb, G::BM));
@@ -345,15 +356,10 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
           EBV_TRY(launch_ok());
         }
         if (pipe && p >= 1) EBV_CU(cudaStreamWaitEvent(s, pipe->done[(p - 1) & 1], 0));
+        // (symmetric storages: U12 = D11 L21^T is implied, the lower-half view reads it so)
         if (u12_beside) {
           EBV_CU(cudaStreamWaitEvent(s, bp->u12, 0));
-        } else if (ce > cb && sym) {
-          if (!A.symlo) {  // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
-            prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
-            k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
-            EBV_TRY(launch_ok());
-          }
-        } else if (ce > cb) {
+        } else if (ce > cb && !sym) {
           prof::Scope ps(s, prof::kTrsm, 1.0 * w * w * (ce - cb));
           k_trsm_ll_subst<T, kNB><<<ceil_div(ce - cb, 8), 256, 0, s>>>(A, c0, w, cb, ce, env);
           EBV_TRY(launch_ok());
@@ -396,13 +402,8 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
         k_trsm_ru<T, float, kNB><<<ceil_div(re - rb, kNB), 256, smem, s>>>(A, c0, w, rb, re, inv, none, env);
       EBV_TRY(launch_ok());
     }
-    if (ce > cb && sym) {  // U12 = D11 L21^T (lower-half storage: implied, the view reads it so)
-      if (!A.symlo) {
-        prof::Scope ps(s, prof::kTrsm, 1.0 * w * (ce - cb));
-        k_sym_u12<T, kNB><<<ceil_div(ce - cb, kNB), 256, 0, s>>>(A, c0, w, cb, ce);
-        EBV_TRY(launch_ok());
-      }
-    } else if (ce > cb) {
+    // (symmetric storages: U12 = D11 L21^T is implied, the lower-half view reads it so)
+    if (ce > cb && !sym) {
       prof::Scope ps(s, prof::kTrsm, 2.0 * w * w * (ce - cb));
       if constexpr (sizeof(T) == 8)
         k_trsm_ll_multi<T, float, kNB, kTrsmMaxBlocks, 16>
@@ -555,10 +556,17 @@ ebv_status_t band_factor(const ebv_desc_t *d, ebv_prec_t prec, void *a, void *lo
                                   (float *)bcast, s);
     return EBV_ERR_UNSUPPORTED;
   }
-  // the factorisation in the view of the stored half or the whole band
-  auto run = [&](auto *p, auto *iv, auto *bc) {
-    return lower ? band_factor_t(symlo_view(p, d->ld, d->kl), d->n, info, iv, env, sym, bc, s)
-                 : band_factor_t(band_view(p, d->ld, d->kl, d->ku), d->n, info, iv, env, sym, bc, s);
+  // the factorisation in the view of the lower half (both symmetric
+  // storages) or of the whole band; EBV_BAND_SYM then gets its upper half
+  auto run = [&](auto *p, auto *iv, auto *bc) -> ebv_status_t {
+    if (!sym) return band_factor_t(band_view(p, d->ld, d->kl, d->ku), d->n, info, iv, env, false, bc, s);
+    EBV_TRY(band_factor_t(symlo_view(p, d->ld, d->kl), d->n, info, iv, env, true, bc, s));
+    if (lower || d->kl == 0) return EBV_OK;
+    using E = std::remove_pointer_t<decltype(p)>;
+    const int64_t total = d->n * d->kl;
+    k_band_fill_upper<E><<<(unsigned)std::min<int64_t>(8192, (total + 255) / 256), 256, 0, s>>>(p, d->ld, d->n,
+                                                                                               d->kl);
+    return launch_ok();
   };
   if (prec == EBV_FP64) return run((double *)a, (double *)inv, (double *)bcast);
   if (prec == EBV_FP32) return run((float *)a, (float *)inv, (float *)bcast);

@@ -1555,30 +1555,6 @@ ebv_status_t prepare_xview_kernels() {
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric band: U12 = D11 L21^T for the block row of the leaf at c0 (w
-// columns): u(c0+k, cb+j) = u_kk * l(cb+j, c0+k).  One CTA per 64 columns of
-// U12; the L21 block is read by rows and written transposed through shared
-// memory, so both sides are coalesced.
-// ---------------------------------------------------------------------------
-template <typename T, int NB, bool XV = false>
-__global__ void __launch_bounds__(256) k_sym_u12(MatView<T, XV> A, int64_t c0, int w, int64_t cb, int64_t ce) {
-  __shared__ T t[NB][NB + 1];
-  __shared__ T d[NB];
-  const int64_t j0 = cb + (int64_t)blockIdx.x * NB;
-  const int wj = (int)min64(NB, ce - j0);
-  for (int k = threadIdx.x; k < NB; k += 256) d[k] = k < w ? A.get(c0 + k, c0 + k) : T(0);
-  for (int e = threadIdx.x; e < NB * NB; e += 256) {
-    const int j = e / NB, k = e % NB;  // L21 row j, column k
-    t[j][k] = (j < wj && k < w) ? A.get(j0 + j, c0 + k) : T(0);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NB * NB; e += 256) {
-    const int k = e / NB, j = e % NB;  // U12 row k, column j
-    if (k < w && j < wj) A.put(c0 + k, j0 + j, d[k] * t[j][k]);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // SIMT trailing update in the working precision (Eq. 6c aggregated over K
 // steps):  A(m0+i, n0+j) -= sum_k A(m0+i, k0+k) * A(k0+k, n0+j).
 // Register-tiled: each thread owns a TM x TN block of C.
