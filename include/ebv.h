@@ -196,9 +196,9 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
  * FP64 factorisations of the band storages overlap work on two internal
- * side streams of the device (each panel's trailing update with the next
- * panel's diagonal block; for the general band also each panel's U12 with
- * its L21), forked from and joined back to `stream` inside
+ * side streams of the device (the symmetric storages: each panel's trailing
+ * update with the next panel's diagonal block; the general band: each
+ * panel's U12 with its L21), forked from and joined back to `stream` inside
  * the call (so the call stays stream-ordered and capturable); the first such
  * call on a device creates those streams and their events: make it before
  * any stream capture.
@@ -454,10 +454,10 @@ EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
  */
 EBV_API void ebv_debug_set_band_cluster(int32_t enable);
 /* Testing hook: the FP64 band panels' overlaps on internal side streams.
- * 0 = all serial; 1 = the symmetric storages' look-ahead (the next panel's
- * diagonal block under the rest of the trailing update) and, for the general
- * band, each panel's U12 beside its L21; 2 (default) = also the look-ahead
- * for the general band.  The same results in every mode.  Process-wide. */
+ * 0 = all serial; 1 (default) = the symmetric storages' look-ahead (the next
+ * panel's diagonal block under the rest of the trailing update) and, for the
+ * general band, each panel's U12 beside its L21; 2 = also the look-ahead for
+ * the general band.  The same results in every mode.  Process-wide. */
 EBV_API void ebv_debug_set_band_lookahead(int32_t mode);
 EBV_API void ebv_debug_set_cluster_panel(int32_t enable);
 /* Testing hook: 0 = the FP64 panels' 64 x 64 diagonal blocks (band storages,

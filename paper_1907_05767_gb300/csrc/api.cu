@@ -153,8 +153,8 @@ void ebv_debug_set_small_dense(int32_t panels) { set_small_dense_panels(panels !
 // Testing hook: 0 = FP64 panels' diagonal blocks on the blocked sub-block kernel.
 void ebv_debug_set_diag_lu(int32_t enable) { set_diag_lu(enable != 0); }
 
-// Testing hook: FP64 band panels' overlaps, 0 = serial, 1 = without the
-// general band's look-ahead, 2 = default (all).
+// Testing hook: FP64 band panels' overlaps, 0 = serial, 1 = default, 2 = also
+// the general band's look-ahead.
 void ebv_debug_set_band_lookahead(int32_t mode) { set_band_overlap(mode < 0 ? 0 : mode > 2 ? 2 : mode); }
 
 // Testing hook: 1 = band panels on thread-block clusters.

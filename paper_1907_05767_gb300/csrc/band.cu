@@ -181,11 +181,11 @@ ebv_status_t band_pipe(BandPipe **out) {
 }
 
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
-// FP64 panels' overlaps (testing hook): 0 = serial; 1 = look-ahead for the
-// symmetric storages, U12 beside L21 for the general ones; 2 (default) =
-// also look-ahead for the general band (512 x 512 Laplacian, two runs: 639
-// and 640 ms against 649 and 650 without it).
-int g_band_overlap = 2;
+// FP64 panels' overlaps (testing hook): 0 = serial; 1 (default) = look-ahead
+// for the symmetric storages, U12 beside L21 for the general ones; 2 = also
+// look-ahead for the general band (512 x 512 Laplacian 649 -> 640 ms, but the
+// variable band of the disc 705 -> 749 ms, so not the default).
+int g_band_overlap = 1;
 bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
 // FP64 panels' diagonal blocks: the register-resident kernel (true) or the
 // blocked 16 x 16 sub-block kernel (testing hook)
