@@ -91,3 +91,42 @@ def test_planted_dyadic_factors_exact(diag_kernel):
         f = ebv.factor(torch.from_numpy(a).to(DEV), "fp64")
         lu = f.lu.cpu().numpy()
         assert np.array_equal(np.tril(lu, -1), np.tril(lo, -1)) and np.array_equal(np.triu(lu), up), on
+
+
+def _with_bad_pivot(n, k, bad, seed):
+    a = synthetic.dense_dd(n, 0.5, seed)
+    a[k, :k] = 0.0
+    a[:k, k] = 0.0
+    a[k, k] = bad  # no earlier step touches a_kk: it reaches the elimination as is
+    return a
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf, 0.0])
+@pytest.mark.parametrize("prec,n", [("fp64", 200), ("fp64", 700), ("fp32", 200), ("fp32", 700), ("bf16", 700)])
+def test_nonfinite_pivot_reported_first(bad, prec, n):
+    # every path of the dense factorisation (panels and registers in FP64,
+    # the cluster or blocked binary32 leaves, the mixed precisions) reports the
+    # first zero / non-finite pivot; later pivots may be NaN too (it spreads)
+    k = 77
+    a = _with_bad_pivot(n, k, bad, 97_000 + n)
+    f = ebv.factor(torch.from_numpy(a).to(DEV), prec)
+    assert int(f.info.item()) == k + 1, (prec, n, bad)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_nonfinite_pivot_band_and_batched(bad):
+    n, kl, k = 600, 40, 333
+    a = _with_bad_pivot(n, k, bad, 98_000)
+    d = np.subtract.outer(np.arange(n), np.arange(n))
+    a[np.abs(d) > kl] = 0.0
+    ab = synthetic.dense_to_band(a, kl, kl)
+    f = ebv.band_factor(torch.from_numpy(ab).to(DEV), kl, kl, "fp64")
+    assert int(f.info.item()) == k + 1
+    batch = ebv.Batch([50, 120], [1, 1], "fp64")
+    for s, m in enumerate((50, 120)):
+        sysa = _with_bad_pivot(m, 31, bad, 98_100 + m) if s == 1 else synthetic.dense_dd(m, 0.5, 98_200)
+        batch.a_view(s).copy_(torch.from_numpy(sysa))
+        batch.b_view(s).copy_(torch.ones((m, 1), dtype=torch.float64))
+    batch.run()
+    info = batch.info.cpu().numpy()
+    assert info[0] == 0 and info[1] == 32
