@@ -273,11 +273,11 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
   Araw.symraw = true;
   // FP64 look-ahead for the symmetric storages (whose trailing updates, the
   // block-lower half only, leave the diagonal block's SM its FP64 units;
-  // measured on the 512 x 512 Laplacian: 899 -> 843 ms, while the general
-  // band's full updates made it slower, 933 -> 1009 ms).  The side stream
-  // joins `s` here and `s` waits for it at the end.
-  // General bands: each panel's U12 on a second side stream, concurrent with
-  // its L21 (both read only the diagonal block and their own entries).
+  // 512 x 512 Laplacian 638 -> 577 ms; for the general band it is optional,
+  // g_band_overlap).  General bands: each panel's U12 on a second side
+  // stream, concurrent with its L21 (both read only the diagonal block and
+  // their own entries).  The side streams fork from `s` here and `s` waits
+  // for them at the end.
   const bool fp64_subst = sizeof(T) == 8 && g_band_subst && !cluster;
   const bool ahead = fp64_subst && n > 2 * kNB && (sym ? g_band_overlap >= 1 : g_band_overlap >= 2);
   const bool u12_side = fp64_subst && !sym && n > kNB && g_band_overlap >= 1;
@@ -316,7 +316,7 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
       if (g_band_subst) {
         // FP64: the diagonal block factored alone (no inverses: two thirds
         // of its FP64 work), then L21 and U12 by substitution over many SMs.
-        // Look-ahead (symmetric storages): the trailing update is split into
+        // Look-ahead: the trailing update is split into
         // the next panel's 64 columns (on `s`, the critical path) and the
         // rest (on the side stream, overlapping the next diagonal block,
         // which runs on one SM).  Panel p's diagonal block and L21 wait for
