@@ -27,7 +27,7 @@ namespace {  // internal linkage: every translation unit gets its own kernels
 // row-major with width 64(b+1) - plo[b], from base + poffL[b]; column block
 // c keeps rows pup[c] .. 64c-1 (its part above the diagonal block),
 // row-major with width 64, from base + poffU[c].  Entries outside read as 0
-// and are never written; kl / ku bound the profile (the drivers' windows).
+// and are never written; kl / ku bound the profile (the host loops' windows).
 template <typename T, bool XV = false>
 struct MatView {
   T *base;

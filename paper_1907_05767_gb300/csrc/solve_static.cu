@@ -36,7 +36,7 @@ constexpr int kMaxDevices = 64;
 // module on the device: after cudaDeviceReset the primary context, and the
 // module in it, are made anew, and a caller may make a context of its own
 // current on the same device.  So the address is cached per device together
-// with the driver's unique ID of the context it was looked up in, and looked
+// with the CUDA driver's unique ID of the context it was looked up in, and looked
 // up again whenever the current context's ID differs.
 struct Slot {
   unsigned long long ctx_id = 0;  // 0: nothing cached
