@@ -67,33 +67,34 @@ struct BatchSmem {
   int bad;           // first failing pivot of the system (0-based), or INT32_MAX
 };
 
-// Unblocked Doolittle of the w x w block D (w <= NB <= 32) by warp 0.  Lane
-// (p, g) owns the column pair {p, NB-1-p} and the rows g, g+NG, ...; the pair
-// holds one long and one short column, so all lanes do the same number of
-// updates over the elimination (Eq. 7).  Multipliers use the pivot
-// reciprocal (one division per pivot).
+// Unblocked Doolittle of the w x w block D (w <= NB) by the whole CTA.
+// Thread (p, g) owns the column pair {p, NB-1-p} and the rows g, g+NG, ...;
+// the pair holds one long and one short column, so all threads do the same
+// number of updates over the elimination (Eq. 7).  Multipliers use the pivot
+// reciprocal (one division per pivot, thread 0); three barriers per step.
 template <typename T, int NB>
-__device__ void warp_diag_factor(BatchSmem<T, NB> &sm, int w, int k0, int lane) {
-  constexpr int NP = NB / 2, NG = 32 / NP;
-  const int p = lane % NP, g = lane / NP;
+__device__ void cta_diag_factor(BatchSmem<T, NB> &sm, int w, int k0) {
+  constexpr int NP = NB / 2, NG = BT / NP;
+  const int p = threadIdx.x % NP, g = threadIdx.x / NP;
   const int c0 = p, c1 = NB - 1 - p;
   for (int r = 0; r < w; ++r) {
-    if (lane == 0) {
+    __syncthreads();  // the block is staged / step r-1's updates are in
+    if (threadIdx.x == 0) {
       const T pv = sm.D[r][r];
       sm.rcp[r] = pivot_rcp(pv);
       if (pivot_bad(pv) && sm.bad > k0 + r) sm.bad = k0 + r;
     }
-    __syncwarp();
+    __syncthreads();
     const T rc = sm.rcp[r];
-    for (int i = r + 1 + lane; i < w; i += 32) sm.D[i][r] *= rc;  // Eq. 6a
-    __syncwarp();
+    for (int i = r + 1 + threadIdx.x; i < w; i += BT) sm.D[i][r] *= rc;  // Eq. 6a
+    __syncthreads();
     for (int i = r + 1 + g; i < w; i += NG) {  // Eq. 6c on the owned entries
       const T l = sm.D[i][r];
       if (c0 > r && c0 < w) sm.D[i][c0] -= l * sm.D[r][c0];
       if (c1 > r && c1 < w && c1 != c0) sm.D[i][c1] -= l * sm.D[r][c1];
     }
-    __syncwarp();
   }
+  __syncthreads();
 }
 
 // Inverses of both triangles of the factored block (identity beyond w), one
@@ -275,8 +276,7 @@ __device__ void cta_lu_solve(BatchSmem<T, NB> &sm, int n, T *A, T *B, int nrhs, 
       sm.D[i][j] = (i < w && j < w) ? A[(int64_t)(k0 + i) * n + k0 + j] : (i == j ? T(1) : T(0));
     }
     __syncthreads();
-    if (warp == 0) warp_diag_factor<T, NB>(sm, w, k0, lane);
-    __syncthreads();
+    cta_diag_factor<T, NB>(sm, w, k0);
     warp_tri_inverses<T, NB>(sm, w, warp, lane);
     __syncthreads();
     for (int e = threadIdx.x; e < w * w; e += BT) {
