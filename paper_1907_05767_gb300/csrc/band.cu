@@ -33,6 +33,16 @@ template <>
 struct BandGemm<double> {
   static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2;
 };
+// FP64 windows of fewer than four 32 x 32 tiles per SM (a band's): 16 x 16
+// tiles, one output per thread.  An FP64 warp instruction costs the pipe the
+// same whatever the tile, so the DFMA time is fixed and the small tiles only
+// balance the SMs (a 512 x 512 window: 1024 tiles over 152 SMs against 256 of
+// 32 x 32, two per SM on most and one on the rest; 512 x 512 Laplacian
+// 649 -> 621 ms).  Wide windows (dense symmetric) keep 32 x 32: there the
+// extra shared-memory loads of the small tiles cost more (1320 -> 1371 ms).
+struct BandGemmNarrow {
+  static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1;
+};
 template <>
 struct BandGemm<float> {
   static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
@@ -271,6 +281,13 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
   // lower-half symmetric storage that view reads a_ji above the diagonal.
   MatView<T, XV> Araw = A;
   Araw.symraw = true;
+  static const int sm_count = [] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 0;
+    return sms;
+  }();
   // FP64 look-ahead for the symmetric storages (whose trailing updates, the
   // block-lower half only, leave the diagonal block's SM its FP64 units;
   // 512 x 512 Laplacian 638 -> 577 ms; for the general band it is optional,
@@ -368,6 +385,16 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
           auto gemm = [&](int64_t n0, int64_t n1, cudaStream_t st) -> ebv_status_t {
             if (n1 <= n0) return EBV_OK;
             prof::Scope ps(st, prof::kSimtGemm, 2.0 * (re - rb) * (n1 - n0) * w);
+            if constexpr (sizeof(T) == 8) {
+              using H = BandGemmNarrow;
+              if ((int64_t)ceil_div(n1 - n0, G::BN) * ceil_div(re - rb, G::BM) < 4 * sm_count) {
+                dim3 grid(ceil_div(n1 - n0, H::BN), ceil_div(re - rb, H::BM));
+                k_gemm_nn<T, H::BM, H::BN, H::BK, H::TM, H::TN>
+                    <<<grid, (H::BM / H::TM) * (H::BN / H::TN), 0, st>>>(A, rb, n0, c0, re - rb, n1 - n0, w,
+                                                                         sym ? 1 : 0, env);
+                return launch_ok();
+              }
+            }
             constexpr int nt = (G::BM / G::TM) * (G::BN / G::TN);
             dim3 grid(ceil_div(n1 - n0, G::BN), ceil_div(re - rb, G::BM));
             k_gemm_nn<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<grid, nt, 0, st>>>(A, rb, n0, c0, re - rb, n1 - n0, w,
