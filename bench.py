@@ -667,12 +667,12 @@ def _config_band(args, dev):
     ebv.lib().ebv_debug_set_diag_lu(0)
     ms_diag_blocked = _dev_ms(c1, 3, 2)
     ebv.lib().ebv_debug_set_diag_lu(1)
-    # every panel's kernels serial, and with the general band's look-ahead too
+    # every panel's kernels serial, and without the general band's look-ahead
     ebv.lib().ebv_debug_set_band_lookahead(0)
     ms_serial = _dev_ms(c1, 3, 2)
-    ebv.lib().ebv_debug_set_band_lookahead(2)
-    ms_general_lookahead = _dev_ms(c1, 3, 2)
     ebv.lib().ebv_debug_set_band_lookahead(1)
+    ms_no_lookahead = _dev_ms(c1, 3, 2)
+    ebv.lib().ebv_debug_set_band_lookahead(2)
     # per kernel class (CUDA events around every launch; classes on the
     # look-ahead's side stream overlap the others)
     ebv.profile(True)
@@ -688,7 +688,7 @@ def _config_band(args, dev):
     g = args.band_grid
     out.append({"config": f"band FP64 Laplacian {g}x{g} (n={n}, kl=ku={kl}), 8 RHS", "ms": ms,
                 "ms_cluster_panels": ms_cluster, "ms_blocked_diag_kernel": ms_diag_blocked,
-                "ms_serial_panels": ms_serial, "ms_with_lookahead": ms_general_lookahead,
+                "ms_serial_panels": ms_serial, "ms_without_lookahead": ms_no_lookahead,
                 "class_ms_profiled_run": classes,
                 "solves_per_s": 1e3 / ms, "gflops": flops / (ms / 1e3) / 1e9,
                 "err_vs_x_true": float(np.abs(xs - x_true).max() / np.abs(x_true).max()),
@@ -706,7 +706,7 @@ def _config_band(args, dev):
 
     ebv.lib().ebv_debug_set_band_lookahead(0)
     ms_sym_no_lookahead = _dev_ms(c1s, 3, 2)
-    ebv.lib().ebv_debug_set_band_lookahead(1)
+    ebv.lib().ebv_debug_set_band_lookahead(2)
     ms = _dev_ms(c1s, 3, 2)
     xs = x.cpu().numpy()
     r = oracle.band_residual(ab, kl, ku, xs, b)[rows]

@@ -454,9 +454,9 @@ EBV_API void ebv_debug_set_lowp_gemm(int32_t mode);
  */
 EBV_API void ebv_debug_set_band_cluster(int32_t enable);
 /* Testing hook: the FP64 band panels' overlaps on internal side streams.
- * 0 = all serial; 1 (default) = the symmetric storages' look-ahead (the next
- * panel's diagonal block under the rest of the trailing update) and, for the
- * general band, each panel's U12 beside its L21; 2 = also the look-ahead for
+ * 0 = all serial; 1 = the symmetric storages' look-ahead (the next panel's
+ * diagonal block under the rest of the trailing update) and, for the general
+ * band, each panel's U12 beside its L21; 2 (default) = also the look-ahead for
  * the general band.  The same results in every mode.  Process-wide. */
 EBV_API void ebv_debug_set_band_lookahead(int32_t mode);
 EBV_API void ebv_debug_set_cluster_panel(int32_t enable);

@@ -191,11 +191,11 @@ ebv_status_t band_pipe(BandPipe **out) {
 }
 
 bool g_band_envelope = true;  // testing hook: false = every CTA of the band window works
-// FP64 panels' overlaps (testing hook): 0 = serial; 1 (default) = look-ahead
-// for the symmetric storages, U12 beside L21 for the general ones; 2 = also
-// look-ahead for the general band (512 x 512 Laplacian 649 -> 640 ms, but the
-// variable band of the disc 705 -> 749 ms, so not the default).
-int g_band_overlap = 1;
+// FP64 panels' overlaps (testing hook): 0 = serial; 1 = look-ahead for the
+// symmetric storages, U12 beside L21 for the general ones; 2 (default) = also
+// look-ahead for the general band (with the 16 x 16 window tiles: 512 x 512
+// Laplacian 620 -> 603 ms, the disc's variable band 650 -> 621 ms).
+int g_band_overlap = 2;
 bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or inverse tile products
 // FP64 panels' diagonal blocks: the register-resident kernel (true) or the
 // blocked 16 x 16 sub-block kernel (testing hook)
@@ -290,13 +290,15 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
   }();
   // FP64 look-ahead for the symmetric storages (whose trailing updates, the
   // block-lower half only, leave the diagonal block's SM its FP64 units;
-  // 512 x 512 Laplacian 638 -> 577 ms; for the general band it is optional,
+  // 512 x 512 Laplacian 638 -> 577 ms) and the general band (620 -> 603 ms;
   // g_band_overlap).  General bands: each panel's U12 on a second side
   // stream, concurrent with its L21 (both read only the diagonal block and
   // their own entries).  The side streams fork from `s` here and `s` waits
   // for them at the end.
   const bool fp64_subst = sizeof(T) == 8 && g_band_subst && !cluster;
-  const bool ahead = fp64_subst && n > 2 * kNB && (sym ? g_band_overlap >= 1 : g_band_overlap >= 2);
+  // (Four panels or fewer, the small dense systems: the general look-ahead's
+  // events cost more than it hides, n = 256 0.522 -> 0.529 ms.)
+  const bool ahead = fp64_subst && n > 2 * kNB && (sym ? g_band_overlap >= 1 : g_band_overlap >= 2 && n > 4 * kNB);
   const bool u12_side = fp64_subst && !sym && n > kNB && g_band_overlap >= 1;
   BandPipe *pipe = nullptr, *bp = nullptr;
   if (ahead || u12_side) {

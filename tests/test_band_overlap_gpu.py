@@ -24,7 +24,7 @@ DEV = "cuda"
 def overlap_mode():
     lib = ebv.lib()
     yield lambda m: lib.ebv_debug_set_band_lookahead(m)
-    lib.ebv_debug_set_band_lookahead(1)
+    lib.ebv_debug_set_band_lookahead(2)
 
 
 def _band(n, kl, ku, seed):
