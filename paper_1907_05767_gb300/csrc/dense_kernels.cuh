@@ -1350,6 +1350,15 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int byt
                "l"(gmem), "r"(bytes)
                : "memory");
 }
+// One element's asynchronous copy (4 or 8 bytes, naturally aligned); bytes 0
+// zero-fills it.
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T *smem, const T *gmem, int bytes) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "n"((int)sizeof(T)), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }

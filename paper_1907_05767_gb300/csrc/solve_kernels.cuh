@@ -149,8 +149,11 @@ __device__ __forceinline__ bool xw_wait(const unsigned long long *p, uint32_t ta
 // one 64 x 64 x RC product -> X_t stored.
 // The factor tiles F(t, s) and the coupling tile stream through an NS-stage
 // shared-memory ring filled by 16-byte cp.async (16-byte chunks XOR-swizzled
-// by row, so the fold's column reads hit distinct banks); band views and
-// unaligned rows fill the ring with plain loads instead.  Published entries
+// by row, so the fold's column reads hit distinct banks); band rows (not
+// 16-byte aligned) by one-element cp.async, so the next tile's copy is in
+// flight during the current fold instead of on the chain (the band's factors
+// outgrow L2: one HBM round trip per serial load); views with computed
+// entries by plain loads, all issued before the first store.  Published entries
 // of an earlier block are taken with one attempt each; only if one is
 // missing does thread 0 poll for the block (one poller per CTA at the front
 // of the chain) before every thread waits for its own.  At the last step
@@ -254,10 +257,28 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T, XV> F, int64
         cp_async16(dst + ring_idx<T, NB>(r, c * E), valid ? F.base + (i0 + r) * F.ld + j0 + c * E : F.base,
                    valid * (int)sizeof(T));
       }
-    } else {
+    } else if constexpr (!XV) {
+      // band rows (and dense rows of an odd ld): entry (i, j) at base + i ld + j
+      // inside the band, contiguous along a row but not 16-byte aligned; one
+      // element per copy, zero-filled outside the band and the matrix
       for (int e = threadIdx.x; e < NB * NB; e += NT) {
         const int r = e / NB, k = e % NB;
-        dst[ring_idx<T, NB>(r, k)] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
+        const int64_t i = i0 + r, j = j0 + k;
+        const bool ok = r < hi && k < hj && F.in(i, j);
+        cp_async_el(dst + ring_idx<T, NB>(r, k), ok ? F.base + i * F.ld + j : F.base, ok ? (int)sizeof(T) : 0);
+      }
+    } else {
+      // views with computed entries: every load of the tile in flight before the first store
+      T v[NB * NB / NT];
+#pragma unroll
+      for (int q = 0; q < NB * NB / NT; ++q) {
+        const int e = threadIdx.x + NT * q, r = e / NB, k = e % NB;
+        v[q] = (r < hi && k < hj) ? F.get(i0 + r, j0 + k) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < NB * NB / NT; ++q) {
+        const int e = threadIdx.x + NT * q;
+        dst[ring_idx<T, NB>(e / NB, e % NB)] = v[q];
       }
     }
   };
