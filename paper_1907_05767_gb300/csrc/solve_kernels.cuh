@@ -370,6 +370,11 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T, XV> F, int64
 #pragma unroll
     for (int q = 0; q < OPT; ++q) Ac[tr + PASS * q][tc] += acc[q];  // this thread's own entries
     __syncthreads();
+    // D_t^{-1} is triangular (Di: lower for L, upper for U, zero diagonal):
+    // a group of four columns k .. k+3 is skipped for pass q when it holds
+    // no entry of any of the warp's rows (warp-uniform; an FP64 warp
+    // instruction costs its pipe slot whatever its lanes do).
+    const int wr0 = (threadIdx.x & ~31) / RC, wr1 = (threadIdx.x | 31) / RC;  // the warp's tr range
     T y[OPT];
 #pragma unroll
     for (int q = 0; q < OPT; ++q) y[q] = T(0);
@@ -380,6 +385,7 @@ __global__ void __launch_bounds__(256, MINB) k_trsv_left(MatView<T, XV> F, int64
       for (int u = 0; u < 4; ++u) x[u] = Ac[k + u][tc];
 #pragma unroll
       for (int q = 0; q < OPT; ++q) {
+        if (UPPER ? k + 3 <= wr0 + PASS * q : k >= wr1 + PASS * q) continue;
         const T *d = &Di[tr + PASS * q][k];
         T f[4];
         if constexpr (sizeof(T) == 4) {
