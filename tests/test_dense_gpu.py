@@ -140,6 +140,36 @@ def test_padded_leading_dimension():
     assert relerr(x.cpu().numpy(), oracle.solve(lu_ref, b)) <= 1e-11
 
 
+@pytest.mark.parametrize("prec,ld", [("fp64", 701), ("fp32", 703)])
+def test_unaligned_leading_dimension(prec, ld):
+    """Rows of an odd leading dimension are not 16-byte aligned: the block
+    substitution copies their tiles element by element (n = 700, above the
+    one-CTA small-system solve)."""
+    n, nrhs = 700, 3
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    a = synthetic.dense_dd(n, 0.9, 33)
+    x_true = synthetic.planted_x(n, nrhs, 33)
+    b = synthetic.rhs_for(a, x_true)
+    big = torch.zeros((n, ld), dtype=dt, device=DEV)
+    big[:, :n] = torch.from_numpy(a).to(dt)
+    big[:, n:] = 7.0  # must stay untouched
+    info = ebv.ebv_factor(big, prec)
+    assert int(info.item()) == 0
+    assert torch.all(big[:, n:] == 7.0)
+    lu_ref, _ = oracle.lu(a)
+    x = torch.from_numpy(b).to(DEV).to(dt).clone()  # the right-hand sides in the factors' precision
+    ebv.ebv_solve(big, x, prec, ld=ld)
+    assert torch.all(big[:, n:] == 7.0)
+    xs = x.cpu().numpy().astype(np.float64)
+    if prec == "fp64":
+        assert np.abs(big[:, :n].cpu().numpy() - lu_ref).max() <= 1e-13
+        assert relerr(xs, oracle.solve(lu_ref, b)) <= 1e-11
+    else:
+        assert np.abs(big[:, :n].cpu().numpy().astype(np.float64) - lu_ref).max() <= 5e-5
+        assert relerr(xs, oracle.solve(lu_ref, b)) <= 1e-4
+        assert backward_error(a, xs, b) <= 1e-5
+
+
 @pytest.mark.parametrize("n,k", [(10, 4), (100, 70), (300, 1)])
 def test_zero_pivot_reported(n, k):
     a = synthetic.dense_dd(n, 0.5, 41)
