@@ -200,10 +200,10 @@ bool g_band_subst = true;     // FP64 panels: substitution L21 / U12 (true) or i
 // FP64 panels' diagonal blocks: the register-resident kernel (true) or the
 // blocked 16 x 16 sub-block kernel (testing hook)
 bool g_diag_lu = true;
-// General bands: one-CTA diagonal blocks (false) or cluster panels (true).
-// Measured on the 512 x 512 Laplacian, factor + solve: 1113 ms one-CTA
-// against 1233 ms on clusters, so the cluster panels serve the lower-half
-// symmetric storage only, which needs them.
+// Band panels: the diagonal block on one CTA with L21 / U12 as separate
+// launches (false, every storage) or one thread-block-cluster launch per
+// panel (true, a testing hook).  Measured on the 512 x 512 Laplacian, factor
+// + solve: 565 ms against 1147 ms on clusters.
 bool g_band_cluster = false;
 
 // Symmetric band with both halves stored (EBV_BAND_SYM): the factorisation
@@ -271,10 +271,8 @@ ebv_status_t band_factor_t(MatView<T, XV> A, int64_t n, int32_t *info, T *inv, i
     env.up = env_up;
   }
   // Panels on a thread-block cluster (diagonal block, L21 and U12 in one
-  // launch) for the lower-half symmetric storage, which needs them; the
-  // other band storages keep the one-CTA diagonal-block kernels, measured
-  // faster on the 512 x 512 Laplacian (1119 ms against 1504 ms per
-  // factor + solve).
+  // launch) only when the testing hook asks for them, for the band views
+  // (not the profile or dense views).
   bool cluster = !A.plo && A.kl < kDenseBand && g_band_cluster && cluster_panel_enabled() &&
                  cluster_panel_fits(sizeof(T) == 8, kNB, std::min<int64_t>(n, kNB + A.kl), sym ? 0 : A.ku);
   // The diagonal-block kernel reads its still unfactored block; in the
