@@ -195,10 +195,12 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  *             non-finite pivot.  Always written.
  *   ws        device workspace of ws_bytes >= ebv_workspace_size(desc, prec, 0),
  *             256-byte aligned (may be NULL when that size is 0).
- * FP64 factorisations of the band storages overlap work on two internal
- * side streams of the device (the symmetric storages: each panel's trailing
- * update with the next panel's diagonal block; the general band: each
- * panel's U12 with its L21), forked from and joined back to `stream` inside
+ * FP64 factorisations that run as 64-column panels (the band, symmetric and
+ * profile storages, and dense systems of order <= 256) overlap work on two
+ * internal side streams of the device: the rest of each panel's trailing
+ * update beside the next panel's diagonal block (symmetric storages past two
+ * panels, the others past four) and, without symmetry, each panel's U12
+ * beside its L21.  They are forked from and joined back to `stream` inside
  * the call (so the call stays stream-ordered and capturable); the first such
  * call on a device creates those streams and their events: make it before
  * any stream capture.
