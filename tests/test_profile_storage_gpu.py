@@ -7,7 +7,8 @@ element by element, 1e-13; X 1e-11 relative; backward error 1e-14; FP32
 factors 5e-5), on an irregular-domain Laplacian, a random profile and a
 narrow band with a few wide rows (where the profile stores far less than
 the band).  The packer itself is checked on the host: the buffer unpacks
-to the input matrix exactly.
+to the input matrix exactly, through the package's decoder and through the
+layout the C header documents (tight envelope, byte count, binary32 values).
 """
 import numpy as np
 import pytest
@@ -68,6 +69,59 @@ def test_packer_round_trip(name, ab, kl, ku):
     assert np.array_equal(synthetic.band_to_dense(back, klp, kup), synthetic.band_to_dense(ab, kl, ku))
     if name == "wide_rows":  # a few wide rows: the profile stores far less than the widest band
         assert buf.nbytes < 0.25 * ab.nbytes
+
+
+def _decode_as_documented(buf, n, es):
+    """The profile buffer read from the layout the C header states, without
+    the package's own decoder: int32 lo[nb], int32 up[nb], int64 offL[nb],
+    int64 offU[nb], values from byte align256(24 nb); row block b keeps
+    columns lo[b] .. 64b+63 of its rows, column block c rows up[c] .. 64c-1
+    of its 64 columns, both row-major.  Returns (dense A, stored mask, lo, up)."""
+    nb = (n + 63) // 64
+    raw = buf.tobytes()
+    lo = np.frombuffer(raw, np.int32, nb, 0)
+    up = np.frombuffer(raw, np.int32, nb, 4 * nb)
+    offl = np.frombuffer(raw, np.int64, nb, 8 * nb)
+    offu = np.frombuffer(raw, np.int64, nb, 16 * nb)
+    v0 = -(-24 * nb // 256) * 256
+    vals = np.frombuffer(raw[v0:], np.float64 if es == 8 else np.float32).astype(np.float64)
+    a = np.zeros((n, n))
+    stored = np.zeros((n, n), dtype=bool)
+    for b in range(nb):
+        w = 64 * (b + 1) - lo[b]
+        for i in range(64 * b, min(n, 64 * b + 64)):
+            cols = np.arange(lo[b], min(n, 64 * b + 64))
+            a[i, cols] = vals[offl[b] + (i - 64 * b) * w + (cols - lo[b])]
+            stored[i, cols] = True
+        cols = np.arange(64 * b, min(n, 64 * b + 64))
+        for i in range(up[b], 64 * b):
+            a[i, cols] = vals[offu[b] + (i - up[b]) * 64 + (cols - 64 * b)]
+            stored[i, cols] = True
+    return a, stored, lo, up
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,ab,kl,ku", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_packer_layout_as_documented(name, ab, kl, ku, prec):
+    n = ab.shape[0]
+    es = 8 if prec == "fp64" else 4
+    buf, klp, kup = ebv.ebv_profile_from_band(ab, kl, ku, prec)
+    a = synthetic.band_to_dense(ab, kl, ku)
+    got, stored, lo, up = _decode_as_documented(buf, n, es)
+    want = a if es == 8 else a.astype(np.float32).astype(np.float64)
+    assert np.array_equal(got, np.where(stored, want, 0.0))
+    assert not np.any(a[~stored])  # every non-zero lies inside the profile
+    nb = (n + 63) // 64
+    for b in range(nb):  # the envelope is tight: its first row / column holds a non-zero
+        r0, r1 = 64 * b, min(n, 64 * b + 64)
+        assert lo[b] == r0 or np.any(a[r0:r1, lo[b]])
+        assert not np.any(a[r0:r1, :lo[b]])
+        assert up[b] == r0 or np.any(a[up[b], r0:r1])
+        assert not np.any(a[:up[b], r0:r1])
+    assert klp == min(n - 1, max(min(n, 64 * b + 64) - 1 - lo[b] for b in range(nb)))
+    assert kup == min(n - 1, max(min(n, 64 * b + 64) - 1 - up[b] for b in range(nb)))
+    count = sum(64 * (64 * (b + 1) - lo[b]) + 64 * (64 * b - up[b]) for b in range(nb))
+    assert buf.nbytes == -(-24 * nb // 256) * 256 + es * count
 
 
 @pytest.mark.gpu
