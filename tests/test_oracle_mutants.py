@@ -1,7 +1,7 @@
 """Planted mistakes in the oracle must each fail at least one pin (CPU only).
 
 Every mutant is a one-token change to a copy of oracle/ebv_oracle.c (a dropped
-term, a wrong sign, a shifted or transposed index), compiled with gcc into a
+term, a wrong sign, a shifted or transposed index, a window one short), compiled with gcc into a
 temporary library and run against the pins.
 """
 import os
@@ -39,6 +39,20 @@ MUTANTS = {
     "adjoint_grad_a_sign": ("grad_a[IDX(i, j, ldga)] = -s;", "grad_a[IDX(i, j, ldga)] = s;"),
     "adjoint_grad_a_transposed": ("s += grad_b[IDX(i, c, ldx)] * x[IDX(j, c, ldx)];",
                                   "s += grad_b[IDX(j, c, ldx)] * x[IDX(i, c, ldx)];"),
+    "band_pivot_multiply": ("const double lik = AB(i, k) / p;", "const double lik = AB(i, k) * p;"),
+    "band_update_sign": ("for (int64_t j = k + 1; j <= jend; ++j) AB(i, j) -= lik * AB(k, j);",
+                         "for (int64_t j = k + 1; j <= jend; ++j) AB(i, j) += lik * AB(k, j);"),
+    "band_update_transposed": ("for (int64_t j = k + 1; j <= jend; ++j) AB(i, j) -= lik * AB(k, j);",
+                               "for (int64_t j = k + 1; j <= jend; ++j) AB(i, j) -= lik * AB(j, k);"),
+    "band_info_off_by_one": ("if (info == 0 && (p == 0.0 || !isfinite(p))) info = k + 1;\n    const int64_t iend",
+                             "if (info == 0 && (p == 0.0 || !isfinite(p))) info = k;\n    const int64_t iend"),
+    "band_backward_window": ("const int64_t j1 = (i + ku < n - 1) ? i + ku : n - 1;\n      for (int64_t j = i + 1; j <= j1; ++j) s -= AB(i, j)",
+                             "const int64_t j1 = (i + ku - 1 < n - 1) ? i + ku - 1 : n - 1;\n      for (int64_t j = i + 1; j <= j1; ++j) s -= AB(i, j)"),
+    "band_backward_no_divide": ("b[IDX(i, c, ldb)] = s / AB(i, i);", "b[IDX(i, c, ldb)] = s;"),
+    "band_residual_window": ("for (int64_t j = j0; j <= j1; ++j) {\n        const double aij",
+                             "for (int64_t j = j0; j < j1; ++j) {\n        const double aij"),
+    "band_residual_drops_product_error": ("comp += pe + se;\n      }\n      r[IDX(i, c, ldr)]",
+                                          "comp += se;\n      }\n      r[IDX(i, c, ldr)]"),
     "residual_drops_product_error": ("comp += pe + se;\n      }\n      r[IDX(t, c, ldr)]",
                                      "comp += se;\n      }\n      r[IDX(t, c, ldr)]"),
     "inverse_gauss_sign": ("for (int64_t j = 0; j < n; ++j) x[IDX(i, j, ldx)] -= lik * x[IDX(k, j, ldx)];",
