@@ -38,6 +38,11 @@
  *   - Device-side waits inside the library's kernels are bounded; on expiry a
  *     kernel sets EBV_ERR_TIMEOUT in its status word and returns.
  *   - Calls are reentrant; concurrent calls must use distinct workspaces.
+ *   - One device per process: the library prepares each kernel once per
+ *     process, on the device current at its first use (shared-memory limits,
+ *     occupancy and SM counts), as one process per GPU does.  On another
+ *     device those settings are missing and a launch that needs them fails
+ *     (EBV_ERR_CUDA).
  */
 #ifndef EBV_H_
 #define EBV_H_
