@@ -104,14 +104,17 @@ def _rank(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_two_ranks_split_the_batch_and_gather_in_system_order(lib):
-    world, port = 2, _free_port()
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_split_the_batch_and_gather_in_system_order(lib, world):
+    port = _free_port()
     out = mp.Manager().dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     ns, _ = synthetic.config3_sizes()
-    assert out[0][0] and out[1][0]
-    i0, i1 = set(out[0][1]), set(out[1][1])
-    assert not (i0 & i1) and (i0 | i1) == set(range(len(ns)))  # every system exactly once
-    assert out[0][2] == out[1][2] == [1000 + s for s in range(len(ns))]
+    assert all(out[r][0] for r in range(world))
+    shares = [set(out[r][1]) for r in range(world)]
+    assert sum(len(x) for x in shares) == len(ns)  # every system exactly once
+    assert set().union(*shares) == set(range(len(ns)))
+    want = [1000 + s for s in range(len(ns))]
+    assert all(out[r][2] == want for r in range(world))
     c = out[0][3]
     assert max(c) / min(c) < 1.01
