@@ -57,22 +57,30 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
+    INTERVAL_MS = 100
+
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
         self.thread = None
 
-    def start(self):
+    def start(self, first_sample_s: float = 3.0):
+        """Start sampling; returns once the first sample is in (at most
+        first_sample_s seconds), so the timed region that follows is covered
+        from its start."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.INTERVAL_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        deadline = time.monotonic() + first_sample_s
+        while not self.lines and self.proc.poll() is None and time.monotonic() < deadline:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -106,7 +114,7 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": self.INTERVAL_MS}
 
 
 # ----------------------------------------------------------------------------
@@ -1150,7 +1158,7 @@ def run_reference(args):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ebv", choices=["ebv", "reference"])
     p.add_argument("--n", type=int, default=N_FULL)

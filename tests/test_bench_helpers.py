@@ -70,3 +70,35 @@ def test_roofline_fractions():
     assert bench.active_launches("residual", {"iters": 2}) == 3
     assert bench.active_launches("trsv", {"iters": 2}) == 6
     assert bench.active_launches("panel", {"iters": 2}) is None
+
+
+def _fake_smi(tmp_path, line, delay="0.05"):
+    """A stand-in nvidia-smi that prints `line` every `delay` seconds until killed."""
+    d = tmp_path / "bin"
+    d.mkdir()
+    f = d / "nvidia-smi"
+    f.write_text(f"#!/bin/sh\nwhile true; do echo '{line}'; sleep {delay}; done\n")
+    f.chmod(0o755)
+    return str(d)
+
+
+def test_clock_sampler_reads_clocks_and_reasons(tmp_path, monkeypatch):
+    path = _fake_smi(tmp_path, "2070, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active")
+    monkeypatch.setenv("PATH", path + os.pathsep + os.environ.get("PATH", ""))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.lines, "start() returns once the first sample is in"
+    import time
+    time.sleep(0.2)
+    c = s.stop()
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["samples"] >= 2 and c["interval_ms"] == bench.ClockSampler.INTERVAL_MS
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    empty = tmp_path / "empty"
+    empty.mkdir()
+    monkeypatch.setenv("PATH", str(empty))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
