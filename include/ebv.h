@@ -298,7 +298,12 @@ EBV_API ebv_status_t ebv_batch_partition(int64_t batch, const int32_t *n_host, c
  * *bytes_needed receives the buffer size, *kl_out / *ku_out the bounds to
  * pass in the descriptor.  out == NULL only computes those; otherwise out
  * (host, out_bytes >= *bytes_needed, 256-byte aligned for the device copy)
- * receives the buffer, which the caller copies to the device as is.
+ * receives the buffer, which the caller copies to the device as is.  Any of
+ * bytes_needed, kl_out, ku_out may be NULL.  Host only, no device call.
+ * EBV_ERR_ARG for n < 1, kl or ku outside 0..n-1, ldab < kl+ku+1 or a null
+ * ab; EBV_ERR_UNSUPPORTED for another prec; EBV_ERR_WORKSPACE when out_bytes
+ * is short.  (The profile of the sparse matrices of the paper's Table 1,
+ * read as uneven bands.)
  */
 EBV_API ebv_status_t ebv_profile_from_band(int64_t n, int64_t kl, int64_t ku, const double *ab, int64_t ldab,
                                            ebv_prec_t prec, void *out, size_t out_bytes, size_t *bytes_needed,
