@@ -214,6 +214,12 @@ EBV_API size_t ebv_workspace_size(const ebv_desc_t *desc, ebv_prec_t prec, int64
  * (a profile, or skyline, matrix stored in its widest band) costs the work of
  * its profile: the factorisation first finds each 64-block's envelope and
  * skips the tiles outside it (see ebv_debug_set_band_envelope).
+ * Returns EBV_ERR_ARG for an invalid descriptor or precision, a null or
+ * misaligned pointer (a, info_dev, lowp for the mixed precisions, ws; the
+ * profile buffer 256-byte aligned); EBV_ERR_UNSUPPORTED for the mixed
+ * precisions with EBV_PROFILE or EBV_DENSE_SYM; EBV_ERR_WORKSPACE for a
+ * missing or short ws; EBV_ERR_CUDA when a launch fails.  All but the last
+ * are returned before anything is enqueued.
  */
 EBV_API ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a, void *lowp,
                         int32_t *info_dev, void *ws, size_t ws_bytes, ebv_stream_t stream);
@@ -236,6 +242,13 @@ EBV_API ebv_status_t ebv_factor(const ebv_desc_t *desc, ebv_prec_t prec, void *a
  *   report_dev device ebv_refine_report_t, written when refine != NULL (may be
  *             NULL otherwise).
  *   ws        workspace of ws_bytes >= ebv_workspace_size(desc, prec, nrhs).
+ * Returns EBV_ERR_ARG for an invalid descriptor or precision, nrhs outside
+ * 0..2^20, ldb < nrhs, a null or misaligned pointer, or refine with a
+ * negative or NaN tol or max_iter outside 0..1000; EBV_ERR_UNSUPPORTED for
+ * refine with EBV_FP32 (refinement returns FP64 solutions) and for the mixed
+ * precisions with EBV_PROFILE or EBV_DENSE_SYM; EBV_ERR_WORKSPACE for a
+ * missing or short ws; EBV_ERR_CUDA when a launch fails.  The outcome of the
+ * refinement is in report_dev (EBV_ERR_NOT_CONVERGED there), on the device.
  */
 EBV_API ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const void *lu, const double *a_orig,
                        void *b, int64_t nrhs, int64_t ldb, const ebv_refine_t *refine,
