@@ -279,9 +279,13 @@ EBV_API ebv_status_t ebv_solve(const ebv_desc_t *desc, ebv_prec_t prec, const vo
  *   matrix (leading dimension n), overwritten by its packed factors;
  *   b_ptrs_dev[s] to its n x nrhs right-hand sides (leading dimension nrhs),
  *   overwritten by X.  prec is EBV_FP64 or EBV_FP32 (all matrices alike).
- *   info_dev[s] receives the system's pivot status.  ws: workspace of at least
- *   ebv_batch_workspace_size(batch) bytes (a work counter and a status word).
- *   All arrays named _dev are device memory.
+ *   info_dev[s] receives the system's pivot status (-1 for an order or count
+ *   outside those ranges, found on the device).  ws: workspace of at least
+ *   ebv_batch_workspace_size(batch) bytes (a work counter and a status word),
+ *   256-byte aligned.  All arrays named _dev are device memory.  Returns
+ *   EBV_ERR_ARG for batch outside 0..2^28-1, a precision other than those
+ *   two or a null array; EBV_ERR_WORKSPACE for a missing, misaligned or short
+ *   ws; EBV_ERR_CUDA when the launch fails (batch 0 returns EBV_OK at once).
  */
 EBV_API int64_t ebv_batch_schedule_len(int64_t batch);
 EBV_API size_t ebv_batch_workspace_size(int64_t batch);
@@ -335,7 +339,11 @@ EBV_API ebv_status_t ebv_factor_solve_batched(int64_t batch, const int32_t *n_de
  * id per order to best_variant_host.  ms_host (host, nullable, count *
  * EBV_BATCH_VARIANTS entries) receives the times, -1 for variants not
  * offered in `prec`.  scratch_dev must hold ebv_batch_autotune_scratch(max
- * order, reps, prec) bytes.  Synchronises the stream (it measures time).
+ * order, reps, prec) bytes, 256-byte aligned.  Synchronises the stream (it
+ * measures time).  EBV_ERR_ARG for null orders or best_variant_host, count or
+ * reps < 1, an order outside 1..4096 or another precision than EBV_FP64 /
+ * EBV_FP32; EBV_ERR_WORKSPACE for a missing, misaligned or short scratch;
+ * ebv_batch_autotune_scratch returns 0 for invalid arguments.
  */
 #define EBV_BATCH_VARIANTS 6
 EBV_API size_t ebv_batch_autotune_scratch(int32_t max_n, int32_t reps, ebv_prec_t prec);
